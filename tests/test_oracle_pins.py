@@ -1,0 +1,481 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: an
+independent library routine (scipy rotations, Triton's Philox), a textbook
+closed form (pendulum, two-link planar arm), an invariant (energy, the power
+identity of Coriolis terms, symmetry and definiteness of M, shift and
+permutation invariance of Eq. 4), or a limit of the method (lambda -> 0 and
+lambda -> infinity of Eq. 4).  The three dynamics formulations (RNEA+CRBA,
+ABA, Eq. 8) also pin one another.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+from scipy.spatial.transform import Rotation as Rot
+
+import oracle
+from paper_2609_02020_b300 import synth
+
+RNG = np.random.default_rng(12345)
+
+
+# ---------------------------------------------------------------------------
+# helpers: hand-built robots
+
+def planar_robot(lengths, masses, lcs, Izz, armature=0.0, damping=0.0, gravity=(0, -9.81, 0)):
+    """Planar chain: every joint turns about z, links along x, gravity in-plane."""
+    n = len(lengths)
+    jx = np.zeros((n, 3))
+    for i in range(1, n):
+        jx[i, 0] = lengths[i - 1]
+    com = np.zeros((n, 3))
+    com[:, 0] = lcs
+    inertia = np.zeros((n, 6))
+    inertia[:, 0] = 0.01
+    inertia[:, 1] = np.asarray(Izz) + 0.01
+    inertia[:, 2] = Izz
+    d = dict(n=n, joint_xyz=jx, joint_rpy=np.zeros((n, 3)), axis=np.tile([0, 0, 1.0], (n, 1)),
+             com=com, mass=np.asarray(masses, float), inertia=inertia,
+             armature=np.full(n, float(armature)), damping=np.full(n, float(damping)),
+             ee_xyz=np.array([lengths[-1], 0.0, 0.0]),
+             q_min=np.full(n, -3.0), q_max=np.full(n, 3.0), qd_max=np.full(n, 5.0),
+             tau_max=np.full(n, 50.0), gravity=np.asarray(gravity, float))
+    return d
+
+
+def random_robot(seed, armature=0.0, damping=0.0, general=True):
+    """Seeded 7-joint arm; with general=True also random fixed rotations,
+    random axes and full inertia tensors (off-diagonal terms)."""
+    g = np.random.default_rng(seed)
+    d = synth.arm(seed, armature=armature, damping=damping)
+    if general:
+        n = d["n"]
+        d["joint_rpy"] = g.uniform(-1, 1, (n, 3))
+        ax = g.normal(size=(n, 3))
+        d["axis"] = ax / np.linalg.norm(ax, axis=1, keepdims=True)
+        d["joint_xyz"] = d["joint_xyz"] + g.uniform(-0.05, 0.05, (n, 3))
+        d["com"] = d["com"] + g.uniform(-0.03, 0.03, (n, 3))
+        inertia = []
+        for i in range(n):
+            A = g.normal(size=(3, 3)) * 0.02
+            Ic = A @ A.T + np.diag(d["inertia"][i, :3])
+            inertia.append([Ic[0, 0], Ic[1, 1], Ic[2, 2], Ic[0, 1], Ic[0, 2], Ic[1, 2]])
+        d["inertia"] = np.array(inertia)
+    return d
+
+
+def R_of(d):
+    return oracle.make_robot(d)
+
+
+# ---------------------------------------------------------------------------
+# Philox and the normals (Eq. 2's noise)
+
+def test_philox_matches_triton_implementation():
+    """Triton's Philox4x32-10 (run by its CPU interpreter) is an independent
+    implementation of the same published generator."""
+    os.environ["TRITON_INTERPRET"] = "1"
+    try:
+        import torch
+        import triton
+        import triton.language as tl
+    except Exception as e:  # pragma: no cover
+        pytest.skip(f"triton unavailable: {e}")
+
+    @triton.jit
+    def kern(out, ctr, seed, N: tl.constexpr):
+        offs = tl.arange(0, N)
+        c0 = tl.load(ctr + offs * 4 + 0)
+        c1 = tl.load(ctr + offs * 4 + 1)
+        c2 = tl.load(ctr + offs * 4 + 2)
+        c3 = tl.load(ctr + offs * 4 + 3)
+        a, b, c, d = tl.philox(seed, c0, c1, c2, c3)
+        tl.store(out + offs * 4 + 0, a)
+        tl.store(out + offs * 4 + 1, b)
+        tl.store(out + offs * 4 + 2, c)
+        tl.store(out + offs * 4 + 3, d)
+
+    g = np.random.default_rng(7)
+    for seed in [0xC0FFEE, 0x123456789ABCDEF, 0, 2**63 - 1]:
+        ctr = g.integers(0, 2**32, (16, 4), dtype=np.uint64).astype(np.uint32)
+        ctr[0] = 0
+        ctr[1] = [2**32 - 1] * 4
+        o = torch.zeros(64, dtype=torch.uint32)
+        try:
+            kern[(1,)](o, torch.from_numpy(ctr.reshape(-1).copy()), seed, 16)
+        except Exception as e:  # pragma: no cover
+            pytest.skip(f"triton interpreter failed: {e}")
+        ref = o.numpy().reshape(16, 4)
+        key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+        for i in range(16):
+            got = oracle.philox4x32_10(ctr[i], key)
+            assert np.array_equal(got, ref[i]), (seed, i, got, ref[i])
+
+
+def test_normals_are_standard_gaussian():
+    z = np.array([oracle.normals(7, it, k, t) for it in range(2) for k in range(2500)
+                  for t in range(4)]).ravel()
+    n = z.size  # 160000
+    assert abs(z.mean()) < 4.0 / math.sqrt(n)
+    assert abs(z.var() - 1.0) < 4.0 * math.sqrt(2.0 / n)
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    # pairs from one Box-Muller call are uncorrelated
+    zz = z.reshape(-1, 2)
+    assert abs(np.corrcoef(zz[:, 0], zz[:, 1])[0, 1]) < 4.0 / math.sqrt(zz.shape[0])
+
+
+def test_normals_depend_on_every_counter_word():
+    base = oracle.normals(1, 2, 3, 4)
+    for args in [(2, 2, 3, 4), (1, 3, 3, 4), (1, 2, 4, 4), (1, 2, 3, 5), (1, 2**32 + 2, 3, 4),
+                 (2**32 + 1, 2, 3, 4)]:
+        assert np.all(oracle.normals(*args) != base)
+
+
+# ---------------------------------------------------------------------------
+# rotations and the log map of Eq. 11
+
+def test_rotation_helpers_match_scipy():
+    for _ in range(20):
+        rpy = RNG.uniform(-3, 3, 3)
+        ref = Rot.from_euler("xyz", rpy).as_matrix()  # extrinsic x, y, z = Rz Ry Rx
+        assert np.allclose(oracle.rpy_matrix(rpy), ref, atol=1e-14)
+        a = RNG.normal(size=3)
+        a /= np.linalg.norm(a)
+        q = RNG.uniform(-4, 4)
+        assert np.allclose(oracle.axis_angle(a, q), Rot.from_rotvec(a * q).as_matrix(), atol=1e-14)
+        qt = RNG.normal(size=4)
+        ref = Rot.from_quat([qt[1], qt[2], qt[3], qt[0]]).as_matrix()
+        assert np.allclose(oracle.quat_matrix(qt), ref, atol=1e-14)
+
+
+@pytest.mark.parametrize("angle", [0.0, 1e-9, 1e-4, 1.0, 2.5, math.pi - 1e-3, math.pi - 1e-9])
+def test_so3_log_recovers_axis_angle(angle):
+    for _ in range(5):
+        a = RNG.normal(size=3)
+        a /= np.linalg.norm(a)
+        R = Rot.from_rotvec(a * angle).as_matrix()
+        r = oracle.so3_log(R)
+        assert abs(np.linalg.norm(r) - angle) < 1e-7
+        if angle > 1e-6:
+            # near pi the sign of the axis is not unique
+            assert min(np.linalg.norm(r - a * angle), np.linalg.norm(r + a * angle)) < 5e-6
+        ref = Rot.from_matrix(R).as_rotvec()
+        if angle < math.pi - 1e-2:
+            assert np.allclose(r, ref, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# kinematics (Fig. 1)
+
+def test_fk_planar_closed_form():
+    L = [0.3, 0.25, 0.2]
+    d = planar_robot(L, [1, 1, 1], [0.1, 0.1, 0.1], [0.01, 0.01, 0.01])
+    rb = R_of(d)
+    for _ in range(10):
+        q = RNG.uniform(-3, 3, 3)
+        c = np.cumsum(q)
+        p = np.array([np.sum(np.array(L) * np.cos(c)), np.sum(np.array(L) * np.sin(c)), 0.0])
+        _, _, Re, pe = oracle.fk(rb, q)
+        assert np.allclose(pe, p, atol=1e-14)
+        assert np.allclose(Re, Rot.from_rotvec([0, 0, c[-1]]).as_matrix(), atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_jacobian_matches_finite_differences(seed):
+    d = random_robot(seed)
+    rb = R_of(d)
+    q = RNG.uniform(-2, 2, 7)
+    J = oracle.jacobian(rb, q)
+    eps = 1e-6
+    for j in range(7):
+        dq = np.zeros(7)
+        dq[j] = eps
+        _, _, Rp, pp = oracle.fk(rb, q + dq)
+        _, _, Rm, pm = oracle.fk(rb, q - dq)
+        assert np.allclose(J[:3, j], (pp - pm) / (2 * eps), atol=1e-8)
+        w = Rot.from_matrix(Rp @ Rm.T).as_rotvec() / (2 * eps)
+        assert np.allclose(J[3:, j], w, atol=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# dynamics (Eq. 5, 6, 8)
+
+def test_two_link_planar_textbook():
+    l1, l2, m1, m2, lc1, lc2, I1, I2, g = 0.5, 0.4, 2.0, 1.5, 0.2, 0.15, 0.05, 0.03, 9.81
+    rb = R_of(planar_robot([l1, l2], [m1, m2], [lc1, lc2], [I1, I2]))
+    for _ in range(10):
+        q, qd, qdd = RNG.uniform(-3, 3, 2), RNG.uniform(-2, 2, 2), RNG.uniform(-5, 5, 2)
+        c2, s2 = math.cos(q[1]), math.sin(q[1])
+        M = np.array([[m1 * lc1 ** 2 + m2 * (l1 ** 2 + lc2 ** 2 + 2 * l1 * lc2 * c2) + I1 + I2,
+                       m2 * (lc2 ** 2 + l1 * lc2 * c2) + I2],
+                      [m2 * (lc2 ** 2 + l1 * lc2 * c2) + I2, m2 * lc2 ** 2 + I2]])
+        hc = np.array([-m2 * l1 * lc2 * s2 * (2 * qd[0] * qd[1] + qd[1] ** 2),
+                       m2 * l1 * lc2 * s2 * qd[0] ** 2])
+        gv = np.array([(m1 * lc1 + m2 * l1) * g * math.cos(q[0]) + m2 * lc2 * g * math.cos(q[0] + q[1]),
+                       m2 * lc2 * g * math.cos(q[0] + q[1])])
+        tau = M @ qdd + hc + gv
+        assert np.allclose(oracle.rnea(rb, q, qd, qdd), tau, atol=1e-12)
+        assert np.allclose(oracle.crba(rb, q), M, atol=1e-13)
+        assert np.allclose(oracle.mass_eq8(rb, q), M, atol=1e-13)
+        assert np.allclose(oracle.aba(rb, q, qd, tau), qdd, atol=1e-11)
+
+
+def test_pendulum_forward_dynamics_closed_form():
+    m, lc, I, a, b, g = 1.7, 0.3, 0.02, 0.05, 0.1, 9.81
+    rb = R_of(planar_robot([0.5], [m], [lc], [I], armature=a, damping=b))
+    for _ in range(20):
+        q, qd, tau = RNG.uniform(-3, 3), RNG.uniform(-3, 3), RNG.uniform(-5, 5)
+        ref = (tau - m * g * lc * math.cos(q) - b * qd) / (I + m * lc ** 2 + a)
+        for method in (oracle.METHOD_CRBA, oracle.METHOD_ABA, oracle.METHOD_EQ8):
+            got = oracle.forward_dynamics(rb, [q], [qd], [tau], method)[0]
+            assert abs(got - ref) < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_three_dynamics_formulations_agree(seed):
+    d = random_robot(seed, armature=0.1, damping=0.1)
+    rb = R_of(d)
+    q, qd = RNG.uniform(-2.5, 2.5, 7), RNG.normal(0, 1, 7)
+    tau = RNG.normal(0, 5, 7)
+    M = oracle.crba(rb, q) + np.diag(d["armature"])
+    M8 = oracle.mass_eq8(rb, q)
+    assert np.allclose(M, M.T, atol=1e-14)
+    assert np.allclose(M, M8, atol=1e-12)
+    assert np.linalg.eigvalsh(M).min() > 0
+    a0 = oracle.forward_dynamics(rb, q, qd, tau, oracle.METHOD_CRBA)
+    a1 = oracle.forward_dynamics(rb, q, qd, tau, oracle.METHOD_ABA)
+    a2 = oracle.forward_dynamics(rb, q, qd, tau, oracle.METHOD_EQ8)
+    assert np.allclose(a0, a1, atol=1e-10) and np.allclose(a0, a2, atol=1e-10)
+    # round trip: RNEA of ABA's acceleration returns the torque
+    rt = oracle.rnea(rb, q, qd, a1) + d["armature"] * a1 + d["damping"] * qd
+    assert np.allclose(rt, tau, atol=1e-10)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_gravity_compensation_holds_still(seed):
+    d = random_robot(seed)
+    rb = R_of(d)
+    q = RNG.uniform(-2.5, 2.5, 7)
+    g = oracle.rnea(rb, q, np.zeros(7), np.zeros(7))
+    for method in (oracle.METHOD_CRBA, oracle.METHOD_ABA, oracle.METHOD_EQ8):
+        assert np.abs(oracle.forward_dynamics(rb, q, np.zeros(7), g, method)).max() < 1e-11
+
+
+def _energy(rb, d, q, qd):
+    M = oracle.crba(rb, q)
+    c = oracle.com_positions(rb, q)
+    V = -np.sum(np.asarray(d["mass"]) * (c @ np.asarray(d["gravity"])))
+    return 0.5 * qd @ M @ qd + V
+
+
+def test_energy_conserved_without_torque_or_damping():
+    d = random_robot(3, armature=0.0, damping=0.0)
+    rb = R_of(d)
+    q, qd = RNG.uniform(-1.5, 1.5, 7), RNG.normal(0, 0.5, 7)
+    zero = np.zeros(7)
+
+    def f(x):
+        return np.concatenate([x[7:], oracle.aba(rb, x[:7], x[7:], zero)])
+
+    x = np.concatenate([q, qd])
+    E0 = _energy(rb, d, q, qd)
+    h = 2e-4
+    for _ in range(2500):  # 0.5 s of RK4
+        k1 = f(x)
+        k2 = f(x + 0.5 * h * k1)
+        k3 = f(x + 0.5 * h * k2)
+        k4 = f(x + h * k3)
+        x = x + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    E1 = _energy(rb, d, x[:7], x[7:])
+    assert abs(E1 - E0) < 1e-7 * max(1.0, abs(E0))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_coriolis_power_identity(seed):
+    """With g = 0: qd^T C(q,qd) qd = 1/2 qd^T Mdot qd (Mdot along qd)."""
+    d = random_robot(seed)
+    d["gravity"] = np.zeros(3)
+    rb = R_of(d)
+    q, qd = RNG.uniform(-2, 2, 7), RNG.normal(0, 1, 7)
+    eps = 1e-6
+    Mdot = (oracle.crba(rb, q + eps * qd) - oracle.crba(rb, q - eps * qd)) / (2 * eps)
+    lhs = qd @ oracle.rnea(rb, q, qd, np.zeros(7))
+    assert abs(lhs - 0.5 * qd @ Mdot @ qd) < 1e-7 * max(1.0, abs(lhs))
+
+
+# ---------------------------------------------------------------------------
+# contact (Eq. 5's tau_ext) and costs (Eq. 9-14)
+
+def test_contact_force_and_torque_closed_form():
+    l, k, c = 0.5, 2000.0, 50.0
+    d = planar_robot([l], [1.0], [0.25], [0.02])
+    rb = R_of(d)
+    cost = oracle.make_cost(dict(w_pos=np.zeros(3), w_ori=np.zeros(3), contact=1,
+                                 k_contact=k, d_contact=c))
+    plane = np.array([0.0, 1.0, 0.0, 0.01])  # free space is y >= 0.01
+    for q, qd in [(0.0, 0.0), (0.0, -0.1), (0.01, 0.3), (-0.2, 0.0), (0.5, 0.0), (0.0, 1.0)]:
+        py = l * math.sin(q)
+        delta = 0.01 - py
+        vy = l * math.cos(q) * qd
+        f = max(0.0, k * delta - c * vy) if delta > 0 else 0.0
+        got_f, tex = oracle.contact(rb, cost, plane, [q], [qd])
+        assert abs(got_f - f) < 1e-12
+        assert abs(tex[0] - f * l * math.cos(q)) < 1e-12
+
+
+def test_joint_cost_hinges_by_hand():
+    d = planar_robot([0.5, 0.5], [1, 1], [0.2, 0.2], [0.01, 0.01])
+    d["q_min"] = np.array([-1.0, -1.0])
+    d["q_max"] = np.array([1.0, 1.0])
+    d["qd_max"] = np.array([2.0, 2.0])
+    d["tau_max"] = np.array([10.0, 10.0])
+    rb = R_of(d)
+    cost = oracle.make_cost(dict(w_pos=np.zeros(3), w_ori=np.zeros(3), w_qlim=3.0, w_qdlim=5.0,
+                                 w_tau=7.0, w_posture=0.5, q_posture=[0.1, -0.2]))
+    q, qd, v = [1.5, -0.5], [-2.5, 1.0], [12.0, -9.0]
+    ref = 3.0 * 0.25 + 5.0 * 0.25 + 7.0 * 4.0 + 0.5 * (1.4 ** 2 + 0.3 ** 2)
+    assert abs(oracle.joint_cost(rb, cost, q, qd, v) - ref) < 1e-12
+
+
+def test_motion_cost_weighted_norms():
+    cost = oracle.make_cost(dict(w_pos=[1.0, 2.0, 3.0], w_ori=[4.0, 5.0, 6.0]))
+    rv = np.array([0.3, -0.2, 0.5])
+    Rd = Rot.from_rotvec([0.1, 0.7, -0.4])
+    Re = (Rd * Rot.from_rotvec(rv)).as_matrix()  # R_des^T R_ee = exp(rv)
+    qd_ = Rd.as_quat()
+    goal = np.array([0.1, 0.2, 0.3, qd_[3], qd_[0], qd_[1], qd_[2]])
+    pe = np.array([0.4, -0.1, 0.0])
+    ref = 1 * 0.09 + 2 * 0.09 + 3 * 0.09 + 4 * 0.09 + 5 * 0.04 + 6 * 0.25
+    assert abs(oracle.motion_cost(cost, goal, pe, Re) - ref) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# MPPI update (Eq. 4) and the shift
+
+def _upd(S, noise, plan, lam):
+    return oracle.mppi_update(np.asarray(S, float), noise, plan, lam)
+
+
+def test_update_single_and_pair_closed_form():
+    T, n = 3, 2
+    plan = RNG.normal(size=(T, n))
+    noise = RNG.normal(size=(2, T, n))
+    rc, us, nxt, st = _upd([5.0], noise[:1], plan, 1.0)
+    assert rc == 0 and np.allclose(us, plan + noise[0], atol=1e-15)
+    rc, us, nxt, st = _upd([1.0, 1.7], noise, plan, 0.5)
+    w2 = math.exp(-0.7 / 0.5)
+    assert np.allclose(us, plan + (noise[0] + w2 * noise[1]) / (1 + w2), atol=1e-15)
+    assert np.allclose(nxt[:-1], us[1:]) and np.allclose(nxt[-1], us[-1])
+    assert abs(st[0] - 1.0) < 1e-15 and abs(st[1] - (1 + w2)) < 1e-15
+
+
+def test_update_lambda_limits():
+    K, T, n = 64, 4, 7
+    plan = RNG.normal(size=(T, n))
+    noise = RNG.normal(size=(K, T, n))
+    S = RNG.uniform(0, 10, K)
+    _, us, _, _ = _upd(S, noise, plan, 1e12)
+    assert np.allclose(us, plan + noise.mean(axis=0), atol=1e-9)
+    _, us, _, st = _upd(S, noise, plan, 1e-12)
+    assert np.allclose(us, plan + noise[np.argmin(S)], atol=1e-15)
+    assert abs(st[2] - 1.0) < 1e-12
+
+
+def test_update_shift_and_permutation_invariance():
+    K, T, n = 50, 5, 7
+    plan = RNG.normal(size=(T, n))
+    noise = RNG.normal(size=(K, T, n))
+    S = RNG.uniform(0, 3, K)
+    _, u0, _, _ = _upd(S, noise, plan, 0.7)
+    _, u1, _, _ = _upd(S + 1234.5, noise, plan, 0.7)
+    p = RNG.permutation(K)
+    _, u2, _, _ = _upd(S[p], noise[p], plan, 0.7)
+    assert np.allclose(u0, u1, atol=1e-12) and np.allclose(u0, u2, atol=1e-13)
+
+
+def test_update_nonfinite_costs():
+    K, T, n = 10, 3, 7
+    plan = RNG.normal(size=(T, n))
+    noise = RNG.normal(size=(K, T, n))
+    S = RNG.uniform(0, 3, K)
+    S2 = S.copy()
+    S2[[2, 5]] = [np.nan, np.inf]
+    keep = [i for i in range(K) if i not in (2, 5)]
+    rc, us, _, st = _upd(S2, noise, plan, 1.0)
+    _, ref, _, _ = _upd(S[keep], noise[keep], plan, 1.0)
+    assert rc == 0 and np.allclose(us, ref, atol=1e-15) and st[3] == 2
+    rc, us, nxt, st = _upd(np.full(K, np.nan), noise, plan, 1.0)
+    assert rc == 1 and np.array_equal(us, plan) and np.array_equal(nxt, plan)
+
+
+# ---------------------------------------------------------------------------
+# rollout (Eq. 1-3, 5-7)
+
+def test_pendulum_rollout_closed_form():
+    """sigma = 0: the rollout is the semi-implicit Euler recursion of the
+    pendulum's closed-form dynamics, charged on x_{t+1} (Eq. 3, 7)."""
+    m, lc, I, a, b, l, g = 1.2, 0.25, 0.03, 0.05, 0.1, 0.5, 9.81
+    d = planar_robot([l], [m], [lc], [I], armature=a, damping=b)
+    d["q_min"], d["q_max"], d["qd_max"], d["tau_max"] = [-0.2], [0.2], [0.5], [1.0]
+    rb = R_of(d)
+    wq, wr = np.array([2.0, 3.0, 0.0]), np.array([0.0, 0.0, 0.7])
+    cd = dict(w_pos=wq, w_ori=wr, w_qlim=1.5, w_qdlim=2.5, w_tau=0.3, w_posture=0.2,
+              q_posture=[0.1])
+    cost = oracle.make_cost(cd)
+    qg = 0.4
+    goal = np.array([0.3, 0.1, 0.0, math.cos(qg / 2), 0.0, 0.0, math.sin(qg / 2)])
+    T, dt = 12, 0.01
+    plan = RNG.normal(0, 2, (T, 1))
+    q, qd, S = 0.05, -0.3, 0.0
+    for t in range(T):
+        v = plan[t, 0]
+        qdd = (v - m * g * lc * math.cos(q) - b * qd) / (I + m * lc ** 2 + a)
+        qd += qdd * dt
+        q += qd * dt
+        p = np.array([l * math.cos(q), l * math.sin(q)])
+        S += wq[0] * (goal[0] - p[0]) ** 2 + wq[1] * (goal[1] - p[1]) ** 2
+        S += wr[2] * (q - qg) ** 2
+        S += 1.5 * (max(0, q - 0.2) ** 2 + max(0, -0.2 - q) ** 2)
+        S += 2.5 * max(0, abs(qd) - 0.5) ** 2 + 0.2 * (q - 0.1) ** 2 + 0.3 * max(0, abs(v) - 1) ** 2
+    got = oracle.rollout(rb, cost, dt, T, [0.0], 1, 0, 0, [0.05], [-0.3], goal, synth.NO_PLANE, plan)
+    assert abs(got - S) < 1e-12 * max(1, abs(S))
+
+
+def test_rollout_noise_is_sigma_times_normals():
+    d = synth.arm(0)
+    rb = R_of(d)
+    cost = oracle.make_cost(synth.cost_free_space())
+    q, qd = synth.state(5, d)
+    T = 4
+    sig = np.linspace(0.5, 3.5, 7)
+    _, nz = oracle.rollout(rb, cost, 0.01, T, sig, 99, 3, 17, q, qd, synth.goal(5, d),
+                           synth.NO_PLANE, np.zeros((T, 7)), want_noise=True)
+    for t in range(T):
+        assert np.array_equal(nz[t], sig * oracle.normals(99, 3, 17, t)[:7])
+
+
+def test_step_equals_rollouts_plus_update_and_threads_agree():
+    d = synth.arm(1)
+    rb = R_of(d)
+    cost = oracle.make_cost(synth.cost_contact())
+    q, qd = synth.state(1001, d)
+    pe = oracle.fk(rb, q)[3]
+    plane = synth.plane_through(pe[2])
+    goal = synth.goal(1001, d)
+    T, K = 6, 40
+    plan = RNG.normal(0, 1, (T, 7))
+    sig = np.full(7, 2.0)
+    o1 = oracle.mppi_step(rb, cost, 0.01, T, K, 1.0, sig, 5, 2, q, qd, goal, plane, plan,
+                          nthreads=1, want_noise=True)
+    o4 = oracle.mppi_step(rb, cost, 0.01, T, K, 1.0, sig, 5, 2, q, qd, goal, plane, plan,
+                          nthreads=4, want_noise=True)
+    assert np.array_equal(o1["S"], o4["S"]) and np.array_equal(o1["ustar"], o4["ustar"])
+    for k in range(K):
+        S, nz = oracle.rollout(rb, cost, 0.01, T, sig, 5, 2, k, q, qd, goal, plane, plan,
+                               want_noise=True)
+        assert S == o1["S"][k] and np.array_equal(nz, o1["noise"][k])
+    _, us, _, _ = oracle.mppi_update(o1["S"], o1["noise"], plan, 1.0)
+    assert np.array_equal(us, o1["ustar"])
