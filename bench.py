@@ -1,0 +1,335 @@
+"""Benchmark: rollout-steps/s and MPPI update latency, 7-DoF arm, K=16384, T=18.
+
+One step = one full MPPI update (K rollouts of T steps with dynamics, contact
+and costs, then the Eq. 4 update and the shift) of a seeded 7-joint arm with
+plane contact, dt = 0.01 s.  Prints one JSON line on rank 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`value` times the update on device-resident inputs with CUDA events on the
+library's stream, L2 flushed between steps; `e2e` times the public host call
+mppi_step (inputs copied from pinned host memory, tau0 and the plan read back)
+with a host clock.  `--impl reference` times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.  With N > 1 (torchrun) every
+rank solves its own independent problem (replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rollout-steps/s and MPPI update p50/p99 ms, 7-DoF K=16384 T=18, vs plain"
+UNIT = "rollout-steps/s"
+K_DEFAULT, T_DEFAULT, DT = 16384, 18, 0.01
+SIGMA, LAMBDA, SEED = 2.0, 1.0, 0xC0FFEE
+L2_FLUSH_BYTES = 256 << 20  # twice the 126 MB L2
+
+# FP32 floating-point operations the rollout kernel executes per rollout-step
+# (FADD + FMUL + 2 x FFMA, plus MUFU as 1), counted by ncu on the rollout
+# kernel (smsp__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on) and
+# divided by K*T; the derivation is in the design notes.
+FLOP_PER_ROLLOUT_STEP = None
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--K", type=int, default=K_DEFAULT)
+    ap.add_argument("--T", type=int, default=T_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(rank: int):
+    from paper_2609_02020_b300 import synth
+    arm = synth.arm(rank)
+    q, qd = synth.state(1000 + rank, arm)
+    goal = synth.goal(1000 + rank, arm)
+    return arm, synth.cost_contact(), q, qd, goal
+
+
+def config_dict(K, T, n):
+    return {"workload": f"7-DoF seeded arm, one MPPI update with plane contact, K={K} T={T} "
+                        f"dt={DT} s, sigma={SIGMA} N m, lambda={LAMBDA}",
+            "K": K, "T": T, "dt": DT, "robots": "synthetic 7-joint arms (seeded)",
+            "l2": "flushed between timed steps", "parallelism": f"replicas x{n}"}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the host cores
+
+def cpu_baseline(K_sample: int, T: int, reps: int = 2):
+    import oracle
+    from paper_2609_02020_b300 import synth
+    arm, cost, q, qd, goal = workload(0)
+    rb, oc = oracle.make_robot(arm), oracle.make_cost(cost)
+    pe = oracle.fk(rb, q)[3]
+    plane = synth.plane_through(pe[2])
+    cores = os.cpu_count() or 1
+    nth = min(cores, oracle.max_threads())
+    plan = np.zeros((T, 7))
+    t0 = time.perf_counter()
+    for r in range(reps):
+        oracle.mppi_step(rb, oc, DT, T, K_sample, LAMBDA, np.full(7, SIGMA), SEED, r, q, qd, goal,
+                         plane, plan, nthreads=nth)
+    dt = time.perf_counter() - t0
+    return {"value": K_sample * T * reps / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": f"{reps} full FP64 updates at K={K_sample}, T={T} (same arm, contact "
+                      f"cost), OpenMP over samples on {nth} threads",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    K, T = args.K, args.T
+    K_sample = min(K, 2048)
+    import oracle
+    from paper_2609_02020_b300 import synth
+    arm, cost, q, qd, goal = workload(0)
+    rb, oc = oracle.make_robot(arm), oracle.make_cost(cost)
+    plane = synth.plane_through(oracle.fk(rb, q)[3][2])
+    nth = min(os.cpu_count() or 1, oracle.max_threads())
+    plan = np.zeros((T, 7))
+    for w in range(args.warmup):
+        oracle.mppi_step(rb, oc, DT, T, K_sample, LAMBDA, np.full(7, SIGMA), SEED, w, q, qd, goal,
+                         plane, plan, nthreads=nth)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.mppi_step(rb, oc, DT, T, K_sample, LAMBDA, np.full(7, SIGMA), SEED, s, q, qd, goal,
+                         plane, plan, nthreads=nth)
+        times.append(time.perf_counter() - t0)
+    times = np.array(times)
+    val = K_sample * T / times.mean()
+    scale = K / K_sample
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(times.mean() * 1e3 * scale), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(K, T, 1),
+            "p50_ms": float(np.percentile(times, 50) * 1e3 * scale),
+            "p99_ms": float(np.percentile(times, 99) * 1e3 * scale),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": nth, "kind": "oracle",
+                             "sample": f"each step one FP64 update at K={K_sample} of the K={K} "
+                                       f"workload (latencies scaled by {scale:g})"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2609_02020_b300 import mppi, synth
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    K, T = args.K, args.T
+    arm, cost, q, qd, goal = workload(rank)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctl = mppi.MPPI(arm, cost, dt=DT, T=T, K=K, lam=LAMBDA, sigma=SIGMA, seed=SEED + rank,
+                    stream=stream)
+    pose = ctl.ee_pose(q)
+    plane = synth.plane_through(float(pose[2]))
+    d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, plane), device="cuda")
+    d_tau = torch.zeros(7, device="cuda")
+    d_plan = torch.zeros(T, 7, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # --- device-resident timed region --------------------------------------
+    for _ in range(args.warmup):
+        ctl.step_device(d_in, d_tau, d_plan)
+    assert ctl.sync() == 0
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(dev) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            ctl.step_device(d_in, d_tau, d_plan)
+            ends[i].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    rc = ctl.sync()
+    if rc != 0:
+        raise RuntimeError(f"update failed with status {rc}")
+    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    mean_ms = float(step_ms.mean())
+    launches = 2 * args.steps  # rollout_kernel + update_kernel per update
+
+    # --- per-kernel times for the roofline (events on the library stream) ---
+    ms_roll, ms_upd = ctl.time_kernels(d_in, 50)
+
+    # --- end to end through the public host call ----------------------------
+    q32 = np.asarray(q, np.float32)
+    qd32 = np.asarray(qd, np.float32)
+    g32 = np.asarray(goal, np.float32)
+    p32 = np.asarray(plane, np.float32)
+    for _ in range(args.warmup):
+        ctl.step(q32, qd32, g32, p32)
+    barrier()
+    e2e_ms = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ctl.step(q32, qd32, g32, p32)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    barrier()
+    e2e_ms = np.array(e2e_ms)
+
+    # --- aggregate over ranks -------------------------------------------------
+    total_ms = float(step_ms.sum())
+    e2e_total = float(e2e_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms, e2e_total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, e2e_total = float(t[0]), float(t[1])
+    units = K * T * args.steps * world
+    value = units / (total_ms * 1e-3)
+    e2e_value = units / (e2e_total * 1e-3)
+
+    if rank != 0:
+        ctl.close()
+        return
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or 2032.0
+    peak_max = SM_COUNT * FP32_LANES_PER_SM * 2 * 2032e6 / 1e12
+    roof = None
+    if FLOP_PER_ROLLOUT_STEP:
+        achieved = FLOP_PER_ROLLOUT_STEP * K * T / (ms_roll * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
+                "frac": achieved / peak_max, "traffic": ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH,
+                "kernel": "rollout_kernel", "kernel_ms": ms_roll,
+                "peak_note": "FP32 peak of 148 SMs x 128 lanes x 2 FLOP at the 2032 MHz "
+                             "maximum SM clock (derived; no measured FP32 peak)"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(K, T, world),
+            "p50_ms": float(np.percentile(step_ms, 50)),
+            "p99_ms": float(np.percentile(step_ms, 99)),
+            "update_hz": 1e3 / mean_ms,
+            "kernels_ms": {"rollout_kernel": ms_roll, "update_kernel": ms_upd},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 25 * 4,
+                    "d2h_bytes_per_step": (16 + T * 7) * 4,
+                    "p50_ms": float(np.percentile(e2e_ms, 50)),
+                    "p99_ms": float(np.percentile(e2e_ms, 99)),
+                    "api": "mppi_step (host buffers, CUDA graph replay)"},
+            "roofline": roof,
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "wall_s": t_wall}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(min(K, 4096), T)
+    ctl.close()
+    print(json.dumps(line), flush=True)
+
+
+ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

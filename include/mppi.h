@@ -1,0 +1,224 @@
+/*
+ * mppi.h - C ABI of the B300 (sm_103a) torque-sampling MPPI library.
+ *
+ * One update of Model Predictive Path Integral control for a 7-joint
+ * torque-controlled serial arm, as set out in "Real-Time Dynamics-Based
+ * Torque-Sampling MPPI for Compliant and Force Aware Manipulation":
+ *   - K noisy torque sequences v_{k,t} = u_t + dtau_{k,t}, dtau ~ N(0, Sigma)
+ *     (Eq. 2, Sec. III-A);
+ *   - each rolled out over T steps through the rigid-body dynamics
+ *     M qdd + h = tau + tau_ext (Eq. 5), qdd = M^-1 (v + tau_ext - h) (Eq. 6),
+ *     and the Euler update qd += qdd dt, q += qd dt (Eq. 7), with M and h
+ *     rebuilt at every step (Sec. III-A);
+ *   - trajectory cost S_k = phi(x_T) + sum_t l(x_{t+1}, v_t) (Eq. 3) with
+ *     l = C_motion + C_force + C_joint (Eq. 9-12, 14);
+ *   - weights w_k = exp(-(S_k - S_min)/lambda) and the update
+ *     u*_t = u_t + sum_k w_k dtau_{k,t} / sum_k w_k (Eq. 4a-4b);
+ *   - u*_0 is applied and the plan shifted by one step to warm-start the next
+ *     update (Sec. II, last paragraph).
+ *
+ * Everything per update runs in CUDA kernels on the GPU: the library owns the
+ * device buffers it allocates in mppi_create and frees them in mppi_destroy.
+ * All entry points return MPPI_OK (0) or a negative MPPI_ERR_* code; the
+ * message of the last failure on a handle is available from mppi_last_error
+ * (and from mppi_last_error(NULL) for failures of mppi_create).  On any error
+ * the nominal plan is left as it was.  A handle may be used by one host thread
+ * at a time; distinct handles are independent.
+ *
+ * Conventions shared by every entry point:
+ *   - joint vectors are 7 floats in joint order; plans are row-major [T][7]
+ *     (N m);
+ *   - goal = (p_des x, y, z [m], unit quaternion w, x, y, z of R_des);
+ *   - plane = (n_x, n_y, n_z, d): unit normal n, free space is n . p >= d;
+ *     ignored when the cost's contact flag is 0;
+ *   - noise: Philox4x32-10 (Salmon et al., SC'11) with key (seed_lo, seed_hi)
+ *     and counter (k, 2t + c, iter_lo, iter_hi), c in {0, 1}; each output
+ *     word x gives u = ((x >> 8) + 0.5) / 2^24, pairs (u1, u2) give the
+ *     Box-Muller normals sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2); call c=0
+ *     supplies joints 0-3 and c=1 joints 4-6; dtau_{k,t,j} = sigma_j z_j.
+ *     A step is therefore reproducible from (seed, iter, plan, inputs).
+ *   - iter starts at 0 and increases by one after every successful update.
+ */
+#ifndef MPPI_H
+#define MPPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MPPI_API __attribute__((visibility("default")))
+#else
+#define MPPI_API
+#endif
+
+#define MPPI_NJ 7 /* joints of the arm; the library supports exactly 7 */
+
+/* status codes */
+#define MPPI_OK 0
+#define MPPI_ERR_INVALID_ARG (-1) /* a pointer, size or parameter is invalid   */
+#define MPPI_ERR_OOM (-2)         /* a device or pinned-host allocation failed */
+#define MPPI_ERR_CUDA (-3)        /* a CUDA runtime call failed                */
+#define MPPI_ERR_TIMEOUT (-4)     /* a bounded device wait ran out             */
+#define MPPI_ERR_NONFINITE (-5)   /* no sample had a finite cost; plan kept    */
+
+/* Arm description (Fig. 1: joint transforms, CoM offsets, masses, inertias
+ * held by every rollout).  Frames follow the usual URDF chain: link i's frame
+ * is its parent's frame translated by joint_xyz[i], rotated by
+ * Rz(yaw) Ry(pitch) Rx(roll) of joint_rpy[i], then rotated by q_i about the
+ * unit vector axis[i].  The caller owns the record; mppi_create copies it. */
+typedef struct mppi_robot {
+  int n;                      /* must be MPPI_NJ                               */
+  double joint_xyz[7][3];     /* joint i origin in the parent link frame [m]   */
+  double joint_rpy[7][3];     /* fixed rotation parent -> joint frame [rad]    */
+  double axis[7][3];          /* unit joint axis in the joint frame            */
+  double com[7][3];           /* CoM of link i in link i's frame [m]           */
+  double mass[7];             /* [kg], > 0                                     */
+  double inertia[7][6];       /* I^G about the CoM, link frame: xx yy zz xy xz yz */
+  double armature[7];         /* diag(a) of Eq. 8 [kg m^2], >= 0               */
+  double damping[7];          /* viscous joint damping [N m s/rad], >= 0       */
+  double ee_xyz[3];           /* end-effector point in link 7's frame [m]      */
+  double q_min[7], q_max[7];  /* joint position limits [rad]                   */
+  double qd_max[7];           /* joint speed limits [rad/s]                    */
+  double tau_max[7];          /* torque limits [N m]                           */
+  double gravity[3];          /* world gravity [m/s^2]                         */
+} mppi_robot;
+
+/* Running cost l(x_{t+1}, v_t) = C_motion + C_force + C_joint (Eq. 9-12, 14):
+ *   C_motion = sum_a w_pos[a] (p_des - p_ee)_a^2 + sum_a w_ori[a] r_a^2,
+ *              r = log(R_des^T R_ee) as a rotation vector (Eq. 11);
+ *   C_force  = w_force (f_des - f)^2 + w_reg f^2 on the contact normal force
+ *              f (Eq. 12), only when contact != 0;
+ *   C_joint  = w_qlim sum_j [max(0, q_j - q_max_j)^2 + max(0, q_min_j - q_j)^2]
+ *            + w_qdlim sum_j max(0, |qd_j| - qd_max_j)^2
+ *            + w_posture sum_j (q_j - q_posture_j)^2
+ *            + w_tau sum_j max(0, |v_j| - tau_max_j)^2;
+ *   phi(x_T) = w_terminal C_motion(x_T).
+ * Contact (contact != 0): penetration delta = d - n . p_ee; when delta > 0,
+ * f = max(0, k_contact delta - d_contact n . v_ee), else 0; the wrench
+ * (f n, 0) enters the dynamics as tau_ext = J^T F_ext (Eq. 5). */
+typedef struct mppi_cost {
+  double w_pos[3], w_ori[3];
+  double w_force, f_des, w_reg;
+  double w_qlim, w_qdlim, w_tau, w_posture;
+  double q_posture[7];
+  double w_terminal;
+  int contact;
+  double k_contact, d_contact;
+} mppi_cost;
+
+/* Problem sizes and sampler parameters (Eq. 2-4). */
+typedef struct mppi_config {
+  double dt;        /* integration step [s], > 0                            */
+  int T;            /* horizon steps, 1..MPPI_T_MAX                          */
+  int K;            /* samples, 1..MPPI_K_MAX                                */
+  double lambda;    /* temperature, > 0                                      */
+  double sigma[7];  /* noise standard deviation per joint [N m], >= 0        */
+  uint64_t seed;    /* Philox key                                            */
+  int reduce_fp64;  /* 0: FP32 weight reduction; 1: FP64 accumulators       */
+  int use_graph;    /* 1: mppi_step replays a captured CUDA graph            */
+} mppi_config;
+
+#define MPPI_T_MAX 256
+#define MPPI_K_MAX (1 << 22)
+
+typedef struct mppi_s* mppi_t;
+
+/* Create a controller.  Validates every parameter (MPPI_ERR_INVALID_ARG),
+ * allocates the device buffers (noise [T*7][K], costs [K], plans, staging;
+ * MPPI_ERR_OOM on failure) on the current CUDA device.  `stream` is a
+ * cudaStream_t on which all work of this handle is queued; NULL makes the
+ * library create its own non-blocking stream.  The initial plan is zero and
+ * iter is 0.  On success *out receives the handle. */
+MPPI_API int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_config* cfg,
+                void* stream, mppi_t* out);
+
+/* Release every resource of the handle (NULL is accepted). */
+MPPI_API int mppi_destroy(mppi_t h);
+
+/* One MPPI update from host memory: copies (q, qd, goal, plane) to the
+ * device, runs the rollouts and the update, and returns tau0 = u*_0 (7
+ * floats) and, when plan_out is not NULL, the shifted plan [T][7] that the
+ * next update samples around.  Blocks until the result is in host memory.
+ * Returns MPPI_ERR_NONFINITE (plan unchanged, iter unchanged) when no sample
+ * has a finite cost. */
+MPPI_API int mppi_step(mppi_t h, const float q[7], const float qd[7], const float goal[7],
+              const float plane[4], float tau0_out[7], float* plan_out);
+
+/* One MPPI update from device memory, queued on the handle's stream without
+ * waiting.  d_in: 25 device floats (q[7], qd[7], goal[7], plane[4]).
+ * d_tau0 (7 floats) and d_plan ([T][7]) receive u*_0 and the shifted plan
+ * when not NULL.  The status of the update is read by mppi_sync. */
+MPPI_API int mppi_step_device(mppi_t h, const float* d_in, float* d_tau0, float* d_plan);
+
+/* Wait for the handle's queued work; returns the status of the last update
+ * (MPPI_OK or MPPI_ERR_NONFINITE) or MPPI_ERR_CUDA. */
+MPPI_API int mppi_sync(mppi_t h);
+
+/* Per-sample costs S_k of the last update (K floats, host memory). */
+MPPI_API int mppi_get_costs(mppi_t h, float* S_out);
+
+/* Noise dtau of the last update as stored by the rollouts: host array of
+ * T*7*K floats laid out [t*7 + j][k]. */
+MPPI_API int mppi_get_noise(mppi_t h, float* noise_out);
+
+/* u* of the last update before the shift ([T][7], host memory). */
+MPPI_API int mppi_get_updated_plan(mppi_t h, float* u_out);
+
+/* Statistics of the last update: S_min, sum of weights Z, effective sample
+ * size 1/sum(wbar^2), number of non-finite costs. */
+MPPI_API int mppi_get_stats(mppi_t h, double stats[4]);
+
+/* Nominal plan the next update samples around ([T][7], host memory). */
+MPPI_API int mppi_set_plan(mppi_t h, const float* u);
+MPPI_API int mppi_get_plan(mppi_t h, float* u);
+
+/* Update counter used in the Philox counter (for checkpoint / resume). */
+MPPI_API int mppi_set_iter(mppi_t h, uint64_t iter);
+MPPI_API int mppi_get_iter(mppi_t h, uint64_t* iter);
+
+/* Rollouts only (Eq. 1-3, 5-7) for the plan held by the handle and the
+ * inputs at d_in (as in mppi_step_device): writes S [K] to d_S and, when not
+ * NULL, the noise [T*7][K] to d_noise.  Does not change the plan or iter. */
+MPPI_API int mppi_rollout_device(mppi_t h, const float* d_in, float* d_S, float* d_noise);
+
+/* Update only (Eq. 4a-4b and the shift) from caller-supplied device arrays:
+ * costs d_S [K], noise d_noise [T*7][K], nominal plan d_plan [T][7]; writes
+ * u* to d_ustar and the shifted plan to d_plan_next ([T][7] each).  Uses the
+ * handle's K, T, lambda and reduction precision; does not touch its plan. */
+MPPI_API int mppi_update_device(mppi_t h, const float* d_S, const float* d_noise, const float* d_plan,
+                       float* d_ustar, float* d_plan_next);
+
+/* End-effector pose (p xyz, quaternion wxyz) at joint angles q, computed on
+ * the device by the rollouts' own kinematics (host arrays). */
+MPPI_API int mppi_ee_pose(mppi_t h, const float q[7], float pose_out[7]);
+
+/* Device time of the two kernels of one update, averaged over `iters`
+ * updates from the inputs at d_in (CUDA events on the handle's stream).  The
+ * plan and iter are restored afterwards. */
+MPPI_API int mppi_time_kernels(mppi_t h, const float* d_in, int iters, float* ms_rollout,
+                      float* ms_update);
+
+/* The raw Philox4x32-10 words behind the noise (Eq. 2) of update `iter`,
+ * step t, samples k0 .. k0+count-1, computed by the rollouts' own device
+ * generator with the handle's seed: out (host) receives count x 8 words,
+ * [k][call*4 + word].  count must be in 1..1024.  For bit-exact checks of
+ * the integer stream. */
+MPPI_API int mppi_noise_words(mppi_t h, uint64_t iter, uint32_t k0, int count, uint32_t t,
+                              uint32_t* out);
+
+/* Message of the last failure on h, or of the last mppi_create failure of the
+ * calling thread when h is NULL.  Never NULL. */
+MPPI_API const char* mppi_last_error(mppi_t h);
+
+/* Library version string. */
+MPPI_API const char* mppi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPPI_H */

@@ -1,0 +1,399 @@
+// Device-side building blocks of one torque-sampling MPPI rollout (sm_103a).
+//
+// One thread owns one sample k and walks it through the horizon with every
+// quantity in registers: the 7 links are unrolled at compile time, so all
+// per-link arrays below are register arrays, never local memory.
+//
+// Formulation (world frame, Plucker coordinates about the world origin):
+//   joint i's motion axis  S_i = (z_i, p_i x z_i)   [angular; linear at O]
+//   link velocity          V_i = V_{i-1} + S_i qd_i
+//   bias acceleration      A_i = A_{i-1} + V_{i-1} x S_i qd_i,  A_0 = (0, -g)
+//   link force             F_i = I_i A_i + V_i x* (I_i V_i)
+//   bias torque            h_i = S_i . sum_{l>=i} F_l + b_i qd_i
+//   inertia (CRBA)         M_ji = S_j . (I^c_i S_i), I^c_i = sum_{l>=i} I_l,
+//                          plus diag(a) (Eq. 8's armature)
+// so M(q) and h(q, qd) of Eq. 5 are rebuilt at every step as the paper
+// requires (Sec. III-A), and Eq. 6 is solved with an LDL^T factorisation.
+// A spatial inertia about O is (m, h = m c, I_O = Ibar + m(|c|^2 1 - c c^T)),
+// Ibar = R I^G R^T (the rotated link inertia of Eq. 8).
+#pragma once
+#include <cstdint>
+
+namespace mppi_dev {
+
+constexpr int NJ = 7;
+
+// Link constants in the kernel's link frames (z = joint axis); the host
+// rotates the caller's description into these frames once, at create time.
+struct LinkK {
+  float F[9];   // parent kernel frame -> this joint's frame before Rz(q), row-major
+  float r[3];   // joint origin in the parent kernel frame
+  float c[3];   // CoM in this link's kernel frame
+  float I[6];   // inertia about the CoM, kernel frame: xx yy zz xy xz yz
+  float m, arm, damp;
+};
+
+struct RobotK {
+  LinkK L[NJ];
+  float ee[3];    // end-effector point in the last kernel frame
+  float Qee[9];   // last kernel frame -> end-effector (caller's link) frame
+  float qmin[NJ], qmax[NJ], qdmax[NJ], taumax[NJ];
+  float g[3];
+};
+
+struct CostK {
+  float wpos[3], wori[3];
+  float wforce, fdes, wreg;
+  float wqlim, wqdlim, wtau, wpost;
+  float qpost[NJ];
+  float wterm;
+  int contact;
+  float kc, dc;
+};
+
+struct ProbK {
+  RobotK rb;
+  CostK cost;
+  float dt, lambda;
+  float sigma[NJ];
+  int T, K;
+  uint32_t key0, key1;
+};
+
+// Per-step inputs in device memory: q, qd, goal (p, quat wxyz), plane (n, d).
+constexpr int IN_FLOATS = 25;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller normals
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// u = ((x >> 8) + 0.5) 2^-24 is exact in FP32, so both sides of any
+// comparison see the same uniforms.
+__device__ __forceinline__ float u24(uint32_t x) {
+  return (static_cast<float>(x >> 8) + 0.5f) * 5.9604644775390625e-8f;
+}
+
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
+  const float r = sqrtf(-2.0f * logf(u24(a)));
+  float s, c;
+  sincospif(2.0f * u24(b), &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+// The 8 normals of (sample k, step t, update iter); joints use z[0..6].
+__device__ __forceinline__ void normals8(uint32_t k0, uint32_t k1, uint64_t iter, uint32_t k,
+                                         uint32_t t, float z[8]) {
+#pragma unroll
+  for (uint32_t call = 0; call < 2; ++call) {
+    uint32_t c[4] = {k, 2u * t + call, static_cast<uint32_t>(iter),
+                     static_cast<uint32_t>(iter >> 32)};
+    philox4x32_10(c, k0, k1);
+    box_muller(c[0], c[1], z[4 * call + 0], z[4 * call + 1]);
+    box_muller(c[2], c[3], z[4 * call + 2], z[4 * call + 3]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// small vector helpers
+
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
+  return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+// y = R x, R row-major 3x3
+__device__ __forceinline__ void mv3(const float R[9], const float x[3], float y[3]) {
+  y[0] = fmaf(R[0], x[0], fmaf(R[1], x[1], R[2] * x[2]));
+  y[1] = fmaf(R[3], x[0], fmaf(R[4], x[1], R[5] * x[2]));
+  y[2] = fmaf(R[6], x[0], fmaf(R[7], x[1], R[8] * x[2]));
+}
+// C = A B (3x3 row-major)
+__device__ __forceinline__ void mm3(const float A[9], const float B[9], float Cm[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Cm[3 * i + j] = fmaf(A[3 * i], B[j], fmaf(A[3 * i + 1], B[3 + j], A[3 * i + 2] * B[6 + j]));
+}
+
+// Spatial inertia about O applied to a motion vector (w, v):
+// H = I_O w + h x v,  L = m v - h x w.   In = (m, h0..2, Ixx Iyy Izz Ixy Ixz Iyz)
+__device__ __forceinline__ void inertia_apply(const float In[10], const float w[3],
+                                              const float v[3], float H[3], float L[3]) {
+  const float m = In[0];
+  const float h[3] = {In[1], In[2], In[3]};
+  float hv[3], hw[3];
+  cross3(h, v, hv);
+  cross3(h, w, hw);
+  H[0] = fmaf(In[4], w[0], fmaf(In[7], w[1], fmaf(In[8], w[2], hv[0])));
+  H[1] = fmaf(In[7], w[0], fmaf(In[5], w[1], fmaf(In[9], w[2], hv[1])));
+  H[2] = fmaf(In[8], w[0], fmaf(In[9], w[1], fmaf(In[6], w[2], hv[2])));
+  L[0] = fmaf(m, v[0], -hw[0]);
+  L[1] = fmaf(m, v[1], -hw[1]);
+  L[2] = fmaf(m, v[2], -hw[2]);
+}
+
+// Per-link results of the forward sweep kept for the backward sweep.
+struct LinkState {
+  float z[3];   // joint axis (world)
+  float w[3];   // p_i x z_i (linear part of S_i)
+  float F[6];   // RNEA link force (moment about O; force)
+  float In[10]; // spatial inertia about O
+};
+
+struct EEState {
+  float p[3];   // end-effector position
+  float R[9];   // end-effector orientation (row-major)
+  float v[3];   // end-effector linear velocity
+};
+
+// Forward sweep at state (q, qd): kinematics (Fig. 1), RNEA forward
+// recursion with qdd = 0, end-effector pose and velocity.
+__device__ __forceinline__ void forward_sweep(const RobotK& rb, const float q[NJ],
+                                              const float qd[NJ], LinkState ls[NJ], EEState& ee) {
+  float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+  float p[3] = {0.f, 0.f, 0.f};
+  float Vw[3] = {0.f, 0.f, 0.f}, Vv[3] = {0.f, 0.f, 0.f};
+  float Aw[3] = {0.f, 0.f, 0.f}, Av[3] = {-rb.g[0], -rb.g[1], -rb.g[2]};
+#pragma unroll
+  for (int i = 0; i < NJ; ++i) {
+    const LinkK& L = rb.L[i];
+    float d[3];
+    mv3(R, L.r, d);
+    p[0] += d[0]; p[1] += d[1]; p[2] += d[2];
+    float RF[9];
+    mm3(R, L.F, RF);
+    float s, c;
+    sincospif(q[i] * 0.318309886183790672f, &s, &c);
+    // R = RF * Rz(q): columns 0 and 1 rotate, column 2 is the joint axis
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float c0 = RF[3 * r], c1 = RF[3 * r + 1];
+      R[3 * r] = fmaf(c, c0, s * c1);
+      R[3 * r + 1] = fmaf(c, c1, -s * c0);
+      R[3 * r + 2] = RF[3 * r + 2];
+    }
+    LinkState& S = ls[i];
+    S.z[0] = R[2]; S.z[1] = R[5]; S.z[2] = R[8];
+    cross3(p, S.z, S.w);
+
+    // spatial inertia of link i about O
+    float cw[3];
+    mv3(R, L.c, cw);
+    cw[0] += p[0]; cw[1] += p[1]; cw[2] += p[2];
+    // Ibar = R I R^T via T = R I (I symmetric)
+    float Tm[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      Tm[3 * r + 0] = fmaf(R[3 * r], L.I[0], fmaf(R[3 * r + 1], L.I[3], R[3 * r + 2] * L.I[4]));
+      Tm[3 * r + 1] = fmaf(R[3 * r], L.I[3], fmaf(R[3 * r + 1], L.I[1], R[3 * r + 2] * L.I[5]));
+      Tm[3 * r + 2] = fmaf(R[3 * r], L.I[4], fmaf(R[3 * r + 1], L.I[5], R[3 * r + 2] * L.I[2]));
+    }
+    const float m = L.m;
+    const float cc = dot3(cw, cw);
+    float* In = S.In;
+    In[0] = m;
+    In[1] = m * cw[0]; In[2] = m * cw[1]; In[3] = m * cw[2];
+    In[4] = fmaf(Tm[0], R[0], fmaf(Tm[1], R[1], Tm[2] * R[2])) + m * (cc - cw[0] * cw[0]);
+    In[5] = fmaf(Tm[3], R[3], fmaf(Tm[4], R[4], Tm[5] * R[5])) + m * (cc - cw[1] * cw[1]);
+    In[6] = fmaf(Tm[6], R[6], fmaf(Tm[7], R[7], Tm[8] * R[8])) + m * (cc - cw[2] * cw[2]);
+    In[7] = fmaf(Tm[0], R[3], fmaf(Tm[1], R[4], Tm[2] * R[5])) - m * cw[0] * cw[1];
+    In[8] = fmaf(Tm[0], R[6], fmaf(Tm[1], R[7], Tm[2] * R[8])) - m * cw[0] * cw[2];
+    In[9] = fmaf(Tm[3], R[6], fmaf(Tm[4], R[7], Tm[5] * R[8])) - m * cw[1] * cw[2];
+
+    // velocity and bias acceleration
+    const float jw[3] = {S.z[0] * qd[i], S.z[1] * qd[i], S.z[2] * qd[i]};
+    const float jv[3] = {S.w[0] * qd[i], S.w[1] * qd[i], S.w[2] * qd[i]};
+    float t0[3], t1[3], t2[3];
+    cross3(Vw, jw, t0);  // (V x S qd) angular
+    cross3(Vw, jv, t1);
+    cross3(Vv, jw, t2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Aw[a] += t0[a];
+      Av[a] += t1[a] + t2[a];
+      Vw[a] += jw[a];
+      Vv[a] += jv[a];
+    }
+    // F = I A + V x* (I V)
+    float HA[3], LA[3], HV[3], LV[3];
+    inertia_apply(In, Aw, Av, HA, LA);
+    inertia_apply(In, Vw, Vv, HV, LV);
+    float a0[3], a1[3], a2[3];
+    cross3(Vw, HV, a0);
+    cross3(Vv, LV, a1);
+    cross3(Vw, LV, a2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      S.F[a] = HA[a] + a0[a] + a1[a];
+      S.F[3 + a] = LA[a] + a2[a];
+    }
+  }
+  float de[3];
+  mv3(R, rb.ee, de);
+  ee.p[0] = p[0] + de[0]; ee.p[1] = p[1] + de[1]; ee.p[2] = p[2] + de[2];
+  mm3(R, rb.Qee, ee.R);
+  float wp[3];
+  cross3(Vw, ee.p, wp);
+  ee.v[0] = Vv[0] + wp[0]; ee.v[1] = Vv[1] + wp[1]; ee.v[2] = Vv[2] + wp[2];
+}
+
+// Backward sweep: bias torque h (incl. damping) and the joint-space inertia
+// M (lower triangle, packed row-major: M[i(i+1)/2 + j], j <= i) incl. armature.
+__device__ __forceinline__ void backward_sweep(const RobotK& rb, const float qd[NJ],
+                                               const LinkState ls[NJ], float h[NJ],
+                                               float M[NJ * (NJ + 1) / 2]) {
+  float Fs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float Ic[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = NJ - 1; i >= 0; --i) {
+    const LinkState& S = ls[i];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) Fs[a] += S.F[a];
+#pragma unroll
+    for (int a = 0; a < 10; ++a) Ic[a] += S.In[a];
+    h[i] = fmaf(rb.L[i].damp, qd[i],
+                dot3(S.z, Fs) + fmaf(S.w[0], Fs[3], fmaf(S.w[1], Fs[4], S.w[2] * Fs[5])));
+    float H[3], Lm[3];
+    inertia_apply(Ic, S.z, S.w, H, Lm);
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      const LinkState& Sj = ls[j];
+      M[i * (i + 1) / 2 + j] = dot3(Sj.z, H) + dot3(Sj.w, Lm);
+    }
+    M[i * (i + 1) / 2 + i] += rb.L[i].arm;
+  }
+}
+
+// Solve M x = b with M symmetric positive definite (packed lower triangle),
+// by LDL^T.  Overwrites M with the factors.  Every loop has a constant trip
+// count (bounds are guards) so that the factorisation unrolls completely and
+// M stays in registers.
+__device__ __forceinline__ void ldlt_solve(float M[NJ * (NJ + 1) / 2], const float b[NJ],
+                                           float x[NJ]) {
+  float D[NJ], invD[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    // column j: D_j = M_jj - sum_k L_jk^2 D_k ; L_ij = (M_ij - sum_k L_ik L_jk D_k) / D_j
+    float LD[NJ];  // L_jk D_k
+    float d = M[j * (j + 1) / 2 + j];
+#pragma unroll
+    for (int k = 0; k < NJ; ++k) {
+      if (k < j) {
+        const float Ljk = M[j * (j + 1) / 2 + k];
+        LD[k] = Ljk * D[k];
+        d = fmaf(-Ljk, LD[k], d);
+      }
+    }
+    D[j] = d;
+    invD[j] = 1.0f / d;
+#pragma unroll
+    for (int i = 0; i < NJ; ++i) {
+      if (i > j) {
+        float s = M[i * (i + 1) / 2 + j];
+#pragma unroll
+        for (int k = 0; k < NJ; ++k)
+          if (k < j) s = fmaf(-M[i * (i + 1) / 2 + k], LD[k], s);
+        M[i * (i + 1) / 2 + j] = s * invD[j];
+      }
+    }
+  }
+  float y[NJ];
+#pragma unroll
+  for (int i = 0; i < NJ; ++i) {
+    float s = b[i];
+#pragma unroll
+    for (int k = 0; k < NJ; ++k)
+      if (k < i) s = fmaf(-M[i * (i + 1) / 2 + k], y[k], s);
+    y[i] = s;
+  }
+#pragma unroll
+  for (int ii = 0; ii < NJ; ++ii) {
+    const int i = NJ - 1 - ii;
+    float s = y[i] * invD[i];
+#pragma unroll
+    for (int k = 0; k < NJ; ++k)
+      if (k > i) s = fmaf(-M[k * (k + 1) / 2 + i], x[k], s);
+    x[i] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// costs (Eq. 9-12, 14)
+
+__device__ __forceinline__ float hinge2(float x) { return x > 0.f ? x * x : 0.f; }
+
+// goal rotation matrix from the (normalised) quaternion wxyz
+__device__ __forceinline__ void quat_to_R(const float qt[4], float R[9]) {
+  const float n = rsqrtf(qt[0] * qt[0] + qt[1] * qt[1] + qt[2] * qt[2] + qt[3] * qt[3]);
+  const float w = qt[0] * n, x = qt[1] * n, y = qt[2] * n, z = qt[3] * n;
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// C_motion (Eq. 11): weighted squared position error plus weighted squared
+// rotation vector of R_des^T R_ee.
+__device__ __forceinline__ float motion_cost(const CostK& c, const float pdes[3],
+                                             const float Rd[9], const EEState& ee) {
+  // E = Rd^T Re: E_ab = sum_r Rd[r][a] Re[r][b]
+  auto E = [&](int a, int b) {
+    return fmaf(Rd[a], ee.R[b], fmaf(Rd[3 + a], ee.R[3 + b], Rd[6 + a] * ee.R[6 + b]));
+  };
+  const float vx = E(2, 1) - E(1, 2), vy = E(0, 2) - E(2, 0), vz = E(1, 0) - E(0, 1);
+  const float tr = E(0, 0) + E(1, 1) + E(2, 2);
+  const float s2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+  const float s = 0.5f * sqrtf(s2);
+  const float cth = 0.5f * (tr - 1.f);
+  const float th = atan2f(s, cth);
+  float r0, r1, r2;
+  if (s > 1e-4f) {
+    const float k = th / (2.f * s);
+    r0 = k * vx; r1 = k * vy; r2 = k * vz;
+  } else if (cth > 0.f) {
+    r0 = 0.5f * vx; r1 = 0.5f * vy; r2 = 0.5f * vz;
+  } else {
+    // theta near pi: axis from the symmetric part B = (E + E^T)/2 - cos(th) 1
+    const float B00 = E(0, 0) - cth, B11 = E(1, 1) - cth, B22 = E(2, 2) - cth;
+    const float B01 = 0.5f * (E(0, 1) + E(1, 0)), B02 = 0.5f * (E(0, 2) + E(2, 0)),
+                B12 = 0.5f * (E(1, 2) + E(2, 1));
+    float a0, a1, a2;
+    if (B00 >= B11 && B00 >= B22) { a0 = B00; a1 = B01; a2 = B02; }
+    else if (B11 >= B22) { a0 = B01; a1 = B11; a2 = B12; }
+    else { a0 = B02; a1 = B12; a2 = B22; }
+    const float inv = rsqrtf(fmaf(a0, a0, fmaf(a1, a1, a2 * a2)));
+    a0 *= inv; a1 *= inv; a2 *= inv;
+    if (fmaf(a0, vx, fmaf(a1, vy, a2 * vz)) < 0.f) { a0 = -a0; a1 = -a1; a2 = -a2; }
+    r0 = th * a0; r1 = th * a1; r2 = th * a2;
+  }
+  const float ex = pdes[0] - ee.p[0], ey = pdes[1] - ee.p[1], ez = pdes[2] - ee.p[2];
+  float cst = c.wpos[0] * ex * ex + c.wpos[1] * ey * ey + c.wpos[2] * ez * ez;
+  cst += c.wori[0] * r0 * r0 + c.wori[1] * r1 * r1 + c.wori[2] * r2 * r2;
+  return cst;
+}
+
+// Plane contact normal force at the end-effector (0 without contact).
+__device__ __forceinline__ float contact_force(const CostK& c, const float plane[4],
+                                               const EEState& ee) {
+  const float delta = plane[3] - dot3(plane, ee.p);
+  if (!(delta > 0.f)) return 0.f;
+  const float vn = dot3(plane, ee.v);
+  return fmaxf(0.f, fmaf(c.kc, delta, -c.dc * vn));
+}
+
+}  // namespace mppi_dev

@@ -1,0 +1,275 @@
+// Kernels of one MPPI update (sm_103a):
+//   rollout_kernel  - Eq. 1-3 with Eq. 5-7 and the running cost of Eq. 9-14,
+//                     one thread per sample;
+//   update_kernel   - Eq. 4a-4b and the warm-start shift, one block per plan
+//                     entry (t, j), each block reducing over all K samples.
+#pragma once
+#include <cfloat>
+#include <cstdint>
+
+#include "mppi_device.cuh"
+
+namespace mppi_dev {
+
+constexpr int T_MAX = 256;
+constexpr int ROLLOUT_BLOCK = 128;
+constexpr int UPDATE_BLOCK = 256;
+
+// Offsets in the per-handle output record (floats): tau0, status, stats.
+constexpr int OUT_TAU0 = 0;
+constexpr int OUT_STATUS = 7;   // written as an int: 0 ok, 1 no finite cost
+constexpr int OUT_STATS = 8;    // S_min, Z, n_eff, n_nonfinite
+constexpr int OUT_PLAN = 16;    // shifted plan [T][7]
+
+// One rollout per thread.  plan: [T][7] nominal torques; in: IN_FLOATS
+// inputs; iter: update counter (device); S: [K] costs; noise: [T*7][K].
+template <bool STORE_NOISE>
+__global__ void __launch_bounds__(ROLLOUT_BLOCK)
+rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
+               const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
+               float* __restrict__ S, float* __restrict__ noise) {
+  __shared__ float s_plan[T_MAX * NJ];
+  __shared__ float s_in[IN_FLOATS];
+  const int T = P.T, K = P.K;
+  for (int i = threadIdx.x; i < T * NJ; i += blockDim.x) s_plan[i] = plan[i];
+  if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
+  __syncthreads();
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const uint64_t iter = *iter_p;
+
+  float q[NJ], qd[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    q[j] = s_in[j];
+    qd[j] = s_in[NJ + j];
+  }
+  const float pdes[3] = {s_in[14], s_in[15], s_in[16]};
+  float Rd[9];
+  {
+    const float qt[4] = {s_in[17], s_in[18], s_in[19], s_in[20]};
+    quat_to_R(qt, Rd);
+  }
+  const float plane[4] = {s_in[21], s_in[22], s_in[23], s_in[24]};
+  const CostK& C = P.cost;
+  const bool contact = C.contact != 0;
+
+  LinkState ls[NJ];
+  EEState ee;
+  forward_sweep(P.rb, q, qd, ls, ee);
+  float f = contact ? contact_force(C, plane, ee) : 0.f;
+  double Sacc = 0.0;
+
+  for (int t = 0; t < T; ++t) {
+    // Eq. 2: v = u + dtau
+    float z[8];
+    normals8(P.key0, P.key1, iter, static_cast<uint32_t>(k), static_cast<uint32_t>(t), z);
+    float v[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const float du = P.sigma[j] * z[j];
+      if (STORE_NOISE) noise[static_cast<size_t>(t * NJ + j) * K + k] = du;
+      v[j] = s_plan[t * NJ + j] + du;
+    }
+    // Eq. 5-6: qdd = M^-1 (v + J^T F_ext - h)
+    float h[NJ], M[NJ * (NJ + 1) / 2];
+    backward_sweep(P.rb, qd, ls, h, M);
+    float rhs[NJ];
+    if (contact && f > 0.f) {
+      const float Fc[3] = {f * plane[0], f * plane[1], f * plane[2]};
+      float pxF[3];
+      cross3(ee.p, Fc, pxF);
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) rhs[j] = v[j] + dot3(ls[j].z, pxF) + dot3(ls[j].w, Fc) - h[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) rhs[j] = v[j] - h[j];
+    }
+    float qdd[NJ];
+    ldlt_solve(M, rhs, qdd);
+    // Eq. 7: semi-implicit Euler
+    const float dt = P.dt;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      qd[j] = fmaf(qdd[j], dt, qd[j]);
+      q[j] = fmaf(qd[j], dt, q[j]);
+    }
+    // kinematics and RNEA forward sweep at x_{t+1} (reused by step t+1)
+    forward_sweep(P.rb, q, qd, ls, ee);
+    // running cost l(x_{t+1}, v_t), Eq. 9-14
+    float cst = motion_cost(C, pdes, Rd, ee);
+    if (contact) {
+      f = contact_force(C, plane, ee);
+      const float e = C.fdes - f;
+      cst += C.wforce * e * e + C.wreg * f * f;
+    }
+    float cj = 0.f;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      cj += C.wqlim * (hinge2(q[j] - P.rb.qmax[j]) + hinge2(P.rb.qmin[j] - q[j]));
+      cj += C.wqdlim * hinge2(fabsf(qd[j]) - P.rb.qdmax[j]);
+      const float e = q[j] - C.qpost[j];
+      cj += C.wpost * e * e;
+      cj += C.wtau * hinge2(fabsf(v[j]) - P.rb.taumax[j]);
+    }
+    Sacc += static_cast<double>(cst) + static_cast<double>(cj);
+  }
+  if (C.wterm != 0.f) Sacc += static_cast<double>(C.wterm * motion_cost(C, pdes, Rd, ee));
+  S[k] = static_cast<float>(Sacc);
+}
+
+// ---------------------------------------------------------------------------
+// block reductions
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ float warp_min(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ float block_min(float x, float* sm) {
+  x = warp_min(x);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sm[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    x = lane < BLOCK / 32 ? sm[lane] : INFINITY;
+    x = warp_min(x);
+    if (lane == 0) sm[0] = x;
+  }
+  __syncthreads();
+  const float r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+template <int BLOCK, typename V>
+__device__ __forceinline__ void block_sum3(V& a, V& b, V& c, V* sm) {
+  a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { sm[3 * w] = a; sm[3 * w + 1] = b; sm[3 * w + 2] = c; }
+  __syncthreads();
+  if (w == 0) {
+    a = lane < BLOCK / 32 ? sm[3 * lane] : V(0);
+    b = lane < BLOCK / 32 ? sm[3 * lane + 1] : V(0);
+    c = lane < BLOCK / 32 ? sm[3 * lane + 2] : V(0);
+    a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+  }
+}
+
+__device__ __forceinline__ float acc_exp(float x) { return expf(x); }
+__device__ __forceinline__ double acc_exp(double x) { return exp(x); }
+
+// Eq. 4a-4b for plan entry e = blockIdx.x = t*7 + j, and the shift.
+// Costs that are not finite get weight 0; if none is finite the plan is kept
+// (u* = u, next plan = u) and status 1 is reported.  out (may be null):
+// tau0, status, stats and a copy of the shifted plan (OUT_* offsets).
+template <typename Acc>
+__global__ void __launch_bounds__(UPDATE_BLOCK)
+update_kernel(int K, int T, float lambda, const float* __restrict__ S,
+              const float* __restrict__ noise, const float* __restrict__ plan,
+              float* __restrict__ ustar, float* __restrict__ plan_next, float* __restrict__ out,
+              unsigned long long* __restrict__ iter_p) {
+  __shared__ float sm_f[32];
+  __shared__ Acc sm_a[3 * 32];
+  const int e = blockIdx.x;
+  float m = INFINITY;
+  int bad = 0;
+  for (int k = threadIdx.x; k < K; k += UPDATE_BLOCK) {
+    const float s = S[k];
+    if (isfinite(s)) m = fminf(m, s);
+    else ++bad;
+  }
+  m = block_min<UPDATE_BLOCK>(m, sm_f);
+  const bool ok = isfinite(m);
+  Acc z = Acc(0), z2 = Acc(0), nacc = Acc(0);
+  if (ok) {
+    const Acc inv_l = Acc(1) / static_cast<Acc>(lambda);
+    const float* nrow = noise + static_cast<size_t>(e) * K;
+    for (int k = threadIdx.x; k < K; k += UPDATE_BLOCK) {
+      const float s = S[k];
+      const Acc w = isfinite(s) ? acc_exp((static_cast<Acc>(m) - static_cast<Acc>(s)) * inv_l)
+                                : Acc(0);
+      z += w;
+      z2 += w * w;
+      nacc += w * static_cast<Acc>(nrow[k]);
+    }
+  }
+  block_sum3<UPDATE_BLOCK>(z, z2, nacc, sm_a);
+  Acc nbad = Acc(0), d1 = Acc(0), d2 = Acc(0);
+  if (e == 0) {
+    nbad = static_cast<Acc>(bad);
+    __syncthreads();
+    block_sum3<UPDATE_BLOCK>(nbad, d1, d2, sm_a);
+  }
+  if (threadIdx.x != 0) return;
+  const float u = plan[e];
+  const int t = e / NJ;
+  float us;
+  if (ok) {
+    us = static_cast<float>(static_cast<Acc>(u) + nacc / z);
+    if (t >= 1) plan_next[e - NJ] = us;
+    if (t == T - 1) plan_next[e] = us;
+    if (out) {
+      if (t >= 1) out[OUT_PLAN + e - NJ] = us;
+      if (t == T - 1) out[OUT_PLAN + e] = us;
+    }
+  } else {
+    us = u;
+    plan_next[e] = u;
+    if (out) out[OUT_PLAN + e] = u;
+  }
+  ustar[e] = us;
+  if (out && e < NJ) out[OUT_TAU0 + e] = us;
+  if (e == 0) {
+    if (out) {
+      reinterpret_cast<int*>(out)[OUT_STATUS] = ok ? 0 : 1;
+      out[OUT_STATS + 0] = m;
+      out[OUT_STATS + 1] = static_cast<float>(z);
+      out[OUT_STATS + 2] = ok ? static_cast<float>(z * z / z2) : 0.f;
+      out[OUT_STATS + 3] = static_cast<float>(nbad);
+    }
+    if (iter_p && ok) *iter_p += 1ull;
+  }
+}
+
+// Raw Philox words of (iter, t) for samples k0 + i, i < count: out[8 i + 4 call + w].
+__global__ void noise_words_kernel(uint32_t key0, uint32_t key1, uint64_t iter, uint32_t k0,
+                                   int count, uint32_t t, uint32_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+#pragma unroll
+  for (uint32_t call = 0; call < 2; ++call) {
+    uint32_t c[4] = {k0 + static_cast<uint32_t>(i), 2u * t + call, static_cast<uint32_t>(iter),
+                     static_cast<uint32_t>(iter >> 32)};
+    philox4x32_10(c, key0, key1);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) out[8 * i + 4 * call + w] = c[w];
+  }
+}
+
+// End-effector pose at q (one thread): p (3) and R (9, row-major).
+__global__ void ee_pose_kernel(const __grid_constant__ ProbK P, const float* __restrict__ q_in,
+                               float* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float q[NJ], qd[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    q[j] = q_in[j];
+    qd[j] = 0.f;
+  }
+  LinkState ls[NJ];
+  EEState ee;
+  forward_sweep(P.rb, q, qd, ls, ee);
+  for (int a = 0; a < 3; ++a) out[a] = ee.p[a];
+  for (int a = 0; a < 9; ++a) out[3 + a] = ee.R[a];
+}
+
+}  // namespace mppi_dev

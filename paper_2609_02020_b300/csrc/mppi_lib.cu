@@ -1,0 +1,636 @@
+// Host side of the C ABI declared in include/mppi.h: parameter checking, the
+// one-time conversion of the arm into the kernels' link frames, device buffer
+// ownership, kernel launches and CUDA-graph replay of one update.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "mppi.h"
+#include "mppi_kernels.cuh"
+
+using namespace mppi_dev;
+
+#define MPPI_VERSION_STR "paper_2609_02020_b300 mppi 1.0 (sm_103a)"
+
+struct mppi_s {
+  ProbK P;
+  int reduce_fp64 = 0;
+  int use_graph = 1;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // device buffers
+  float* d_plan[2] = {nullptr, nullptr};  // ping-pong nominal plans [T][7]
+  float* d_ustar = nullptr;               // u* before the shift [T][7]
+  float* d_S = nullptr;                   // costs [K]
+  float* d_noise = nullptr;               // noise [T*7][K]
+  float* d_in = nullptr;                  // staged inputs (IN_FLOATS)
+  float* d_out = nullptr;                 // tau0 / status / stats / plan
+  float* d_scratch_plan = nullptr;        // [2][T][7] for timing runs
+  float* d_misc = nullptr;                // 32 floats for small helper kernels
+  uint32_t* d_words = nullptr;            // 8 x 1024 words for mppi_noise_words
+  unsigned long long* d_iter = nullptr;
+  // pinned host staging
+  float* h_in = nullptr;
+  float* h_out = nullptr;
+  int cur = 0;  // index of the current nominal plan
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::string err;
+  int out_floats = 0;
+};
+
+static thread_local std::string g_create_err;
+
+static int fail(mppi_s* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(h, call)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail((h), e_ == cudaErrorMemoryAllocation ? MPPI_ERR_OOM : MPPI_ERR_CUDA, \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// arm conversion (double precision, once per handle)
+
+namespace {
+
+struct M3 {
+  double a[3][3];
+};
+
+M3 m3_identity() {
+  M3 r{};
+  r.a[0][0] = r.a[1][1] = r.a[2][2] = 1.0;
+  return r;
+}
+M3 m3_mul(const M3& A, const M3& B) {
+  M3 C{};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k) C.a[i][j] += A.a[i][k] * B.a[k][j];
+  return C;
+}
+M3 m3_t(const M3& A) {
+  M3 B{};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) B.a[i][j] = A.a[j][i];
+  return B;
+}
+void m3_v(const M3& A, const double x[3], double y[3]) {
+  for (int i = 0; i < 3; ++i) y[i] = A.a[i][0] * x[0] + A.a[i][1] * x[1] + A.a[i][2] * x[2];
+}
+// fixed joint rotation from roll, pitch, yaw: Rz(yaw) Ry(pitch) Rx(roll)
+M3 from_rpy(const double rpy[3]) {
+  const double sr = std::sin(rpy[0]), cr = std::cos(rpy[0]);
+  const double sp = std::sin(rpy[1]), cp = std::cos(rpy[1]);
+  const double sy = std::sin(rpy[2]), cy = std::cos(rpy[2]);
+  M3 R{};
+  R.a[0][0] = cy * cp; R.a[0][1] = cy * sp * sr - sy * cr; R.a[0][2] = cy * sp * cr + sy * sr;
+  R.a[1][0] = sy * cp; R.a[1][1] = sy * sp * sr + cy * cr; R.a[1][2] = sy * sp * cr - cy * sr;
+  R.a[2][0] = -sp;     R.a[2][1] = cp * sr;                R.a[2][2] = cp * cr;
+  return R;
+}
+// a rotation P with P e_z = a (a unit)
+M3 z_to_axis(const double a[3]) {
+  const double c = a[2];
+  if (c > 1.0 - 1e-12) return m3_identity();
+  if (c < -1.0 + 1e-12) {
+    M3 R{};
+    R.a[0][0] = 1.0; R.a[1][1] = -1.0; R.a[2][2] = -1.0;
+    return R;
+  }
+  // axis k = e_z x a / |e_z x a|, angle acos(c)
+  double k[3] = {-a[1], a[0], 0.0};
+  const double s = std::sqrt(k[0] * k[0] + k[1] * k[1]);
+  k[0] /= s; k[1] /= s;
+  const double C = 1.0 - c;
+  M3 R{};
+  const double K[3][3] = {{0, -k[2], k[1]}, {k[2], 0, -k[0]}, {-k[1], k[0], 0}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) R.a[i][j] = (i == j ? c : 0.0) + s * K[i][j] + C * k[i] * k[j];
+  return R;
+}
+
+bool finite_all(const double* x, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, ProbK* P,
+            std::string* why) {
+  if (rb->n != MPPI_NJ) { *why = "robot.n must be 7"; return -1; }
+  if (!(cfg->dt > 0.0) || !std::isfinite(cfg->dt)) { *why = "dt must be > 0"; return -1; }
+  if (cfg->T < 1 || cfg->T > MPPI_T_MAX) { *why = "T must be in 1..256"; return -1; }
+  if (cfg->K < 1 || cfg->K > MPPI_K_MAX) { *why = "K must be in 1..2^22"; return -1; }
+  if (!(cfg->lambda > 0.0) || !std::isfinite(cfg->lambda)) { *why = "lambda must be > 0"; return -1; }
+  for (int j = 0; j < 7; ++j)
+    if (!(cfg->sigma[j] >= 0.0) || !std::isfinite(cfg->sigma[j])) { *why = "sigma must be >= 0"; return -1; }
+  const double* flat = &rb->joint_xyz[0][0];
+  const int nflat = static_cast<int>((reinterpret_cast<const char*>(&rb->gravity[3]) -
+                                      reinterpret_cast<const char*>(flat)) / sizeof(double));
+  if (!finite_all(flat, nflat)) { *why = "robot parameters must be finite"; return -1; }
+  for (int j = 0; j < 7; ++j) {
+    if (!(rb->mass[j] > 0.0)) { *why = "masses must be > 0"; return -1; }
+    if (rb->armature[j] < 0.0 || rb->damping[j] < 0.0) { *why = "armature and damping must be >= 0"; return -1; }
+    const double* a = rb->axis[j];
+    const double na = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    if (std::fabs(na - 1.0) > 1e-6) { *why = "joint axes must be unit vectors"; return -1; }
+    if (!(rb->q_min[j] <= rb->q_max[j])) { *why = "q_min must be <= q_max"; return -1; }
+  }
+  const double* cflat = &c->w_pos[0];
+  if (!finite_all(cflat, 3 + 3 + 3 + 4 + 7 + 1)) { *why = "cost weights must be finite"; return -1; }
+  if (c->contact && (!std::isfinite(c->k_contact) || !std::isfinite(c->d_contact) ||
+                     c->k_contact < 0.0 || c->d_contact < 0.0)) {
+    *why = "contact stiffness and damping must be finite and >= 0";
+    return -1;
+  }
+
+  std::memset(P, 0, sizeof(*P));
+  M3 Pprev = m3_identity();
+  for (int i = 0; i < 7; ++i) {
+    const double* a = rb->axis[i];
+    const double an = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double au[3] = {a[0] / an, a[1] / an, a[2] / an};
+    const M3 Pi = z_to_axis(au);
+    const M3 E = from_rpy(rb->joint_rpy[i]);
+    const M3 F = m3_mul(m3_mul(m3_t(Pprev), E), Pi);
+    LinkK& L = P->rb.L[i];
+    for (int r = 0; r < 3; ++r)
+      for (int s = 0; s < 3; ++s) L.F[3 * r + s] = static_cast<float>(F.a[r][s]);
+    double rk[3], ck[3];
+    m3_v(m3_t(Pprev), rb->joint_xyz[i], rk);
+    m3_v(m3_t(Pi), rb->com[i], ck);
+    for (int r = 0; r < 3; ++r) {
+      L.r[r] = static_cast<float>(rk[r]);
+      L.c[r] = static_cast<float>(ck[r]);
+    }
+    const double* t = rb->inertia[i];
+    M3 Ig{};
+    Ig.a[0][0] = t[0]; Ig.a[1][1] = t[1]; Ig.a[2][2] = t[2];
+    Ig.a[0][1] = Ig.a[1][0] = t[3];
+    Ig.a[0][2] = Ig.a[2][0] = t[4];
+    Ig.a[1][2] = Ig.a[2][1] = t[5];
+    const M3 Ik = m3_mul(m3_mul(m3_t(Pi), Ig), Pi);
+    L.I[0] = static_cast<float>(Ik.a[0][0]);
+    L.I[1] = static_cast<float>(Ik.a[1][1]);
+    L.I[2] = static_cast<float>(Ik.a[2][2]);
+    L.I[3] = static_cast<float>(Ik.a[0][1]);
+    L.I[4] = static_cast<float>(Ik.a[0][2]);
+    L.I[5] = static_cast<float>(Ik.a[1][2]);
+    L.m = static_cast<float>(rb->mass[i]);
+    L.arm = static_cast<float>(rb->armature[i]);
+    L.damp = static_cast<float>(rb->damping[i]);
+    Pprev = Pi;
+  }
+  double ek[3];
+  m3_v(m3_t(Pprev), rb->ee_xyz, ek);
+  const M3 Q = m3_t(Pprev);
+  for (int r = 0; r < 3; ++r) {
+    P->rb.ee[r] = static_cast<float>(ek[r]);
+    P->rb.g[r] = static_cast<float>(rb->gravity[r]);
+    for (int s = 0; s < 3; ++s) P->rb.Qee[3 * r + s] = static_cast<float>(Q.a[r][s]);
+  }
+  for (int j = 0; j < 7; ++j) {
+    P->rb.qmin[j] = static_cast<float>(rb->q_min[j]);
+    P->rb.qmax[j] = static_cast<float>(rb->q_max[j]);
+    P->rb.qdmax[j] = static_cast<float>(rb->qd_max[j]);
+    P->rb.taumax[j] = static_cast<float>(rb->tau_max[j]);
+  }
+  CostK& k = P->cost;
+  for (int a = 0; a < 3; ++a) {
+    k.wpos[a] = static_cast<float>(c->w_pos[a]);
+    k.wori[a] = static_cast<float>(c->w_ori[a]);
+  }
+  k.wforce = static_cast<float>(c->w_force);
+  k.fdes = static_cast<float>(c->f_des);
+  k.wreg = static_cast<float>(c->w_reg);
+  k.wqlim = static_cast<float>(c->w_qlim);
+  k.wqdlim = static_cast<float>(c->w_qdlim);
+  k.wtau = static_cast<float>(c->w_tau);
+  k.wpost = static_cast<float>(c->w_posture);
+  for (int j = 0; j < 7; ++j) k.qpost[j] = static_cast<float>(c->q_posture[j]);
+  k.wterm = static_cast<float>(c->w_terminal);
+  k.contact = c->contact ? 1 : 0;
+  k.kc = static_cast<float>(c->k_contact);
+  k.dc = static_cast<float>(c->d_contact);
+  P->dt = static_cast<float>(cfg->dt);
+  P->lambda = static_cast<float>(cfg->lambda);
+  for (int j = 0; j < 7; ++j) P->sigma[j] = static_cast<float>(cfg->sigma[j]);
+  P->T = cfg->T;
+  P->K = cfg->K;
+  P->key0 = static_cast<uint32_t>(cfg->seed);
+  P->key1 = static_cast<uint32_t>(cfg->seed >> 32);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// launches
+
+cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float* S, float* noise) {
+  const int grid = (h->P.K + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
+  if (noise)
+    rollout_kernel<true><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S, noise);
+  else
+    rollout_kernel<false><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const float* plan,
+                          float* ustar, float* plan_next, float* out, unsigned long long* iter) {
+  const int grid = h->P.T * NJ;
+  if (h->reduce_fp64)
+    update_kernel<double><<<grid, UPDATE_BLOCK, 0, h->stream>>>(h->P.K, h->P.T, h->P.lambda, S,
+                                                                noise, plan, ustar, plan_next, out, iter);
+  else
+    update_kernel<float><<<grid, UPDATE_BLOCK, 0, h->stream>>>(h->P.K, h->P.T, h->P.lambda, S, noise,
+                                                               plan, ustar, plan_next, out, iter);
+  return cudaGetLastError();
+}
+
+// the whole update on device buffers: rollouts, then Eq. 4 into the other plan
+cudaError_t enqueue_update(mppi_s* h, int cur) {
+  cudaError_t e = launch_rollout(h, h->d_in, h->d_plan[cur], h->d_S, h->d_noise);
+  if (e != cudaSuccess) return e;
+  return launch_update(h, h->d_S, h->d_noise, h->d_plan[cur], h->d_ustar, h->d_plan[cur ^ 1],
+                       h->d_out, h->d_iter);
+}
+
+size_t out_bytes(const mppi_s* h) { return sizeof(float) * (OUT_PLAN + h->P.T * NJ); }
+
+// host-buffer step: H2D inputs, update, D2H outputs (captured once per parity)
+cudaError_t enqueue_host_step(mppi_s* h, int cur) {
+  cudaError_t e = cudaMemcpyAsync(h->d_in, h->h_in, sizeof(float) * IN_FLOATS,
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return e;
+  e = enqueue_update(h, cur);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(h->h_out, h->d_out, out_bytes(h), cudaMemcpyDeviceToHost, h->stream);
+}
+
+void destroy_graphs(mppi_s* h) {
+  for (auto& g : h->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+int check_inputs(mppi_s* h, const float* q, const float* qd, const float* goal, const float* plane) {
+  for (int j = 0; j < 7; ++j)
+    if (!std::isfinite(q[j]) || !std::isfinite(qd[j]))
+      return fail(h, MPPI_ERR_INVALID_ARG, "q and qd must be finite");
+  for (int a = 0; a < 7; ++a)
+    if (!std::isfinite(goal[a])) return fail(h, MPPI_ERR_INVALID_ARG, "goal must be finite");
+  const double qn = double(goal[3]) * goal[3] + double(goal[4]) * goal[4] +
+                    double(goal[5]) * goal[5] + double(goal[6]) * goal[6];
+  if (!(qn > 1e-12)) return fail(h, MPPI_ERR_INVALID_ARG, "goal quaternion must be nonzero");
+  if (h->P.cost.contact) {
+    for (int a = 0; a < 4; ++a)
+      if (!std::isfinite(plane[a])) return fail(h, MPPI_ERR_INVALID_ARG, "plane must be finite");
+    const double nn = double(plane[0]) * plane[0] + double(plane[1]) * plane[1] +
+                      double(plane[2]) * plane[2];
+    if (std::fabs(nn - 1.0) > 1e-3) return fail(h, MPPI_ERR_INVALID_ARG, "plane normal must be unit");
+  }
+  return MPPI_OK;
+}
+
+int read_status(mppi_s* h) {
+  int st;
+  std::memcpy(&st, &h->h_out[OUT_STATUS], sizeof st);
+  return st == 0 ? MPPI_OK : fail(h, MPPI_ERR_NONFINITE, "no sample had a finite cost; plan kept");
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+const char* mppi_version(void) { return MPPI_VERSION_STR; }
+
+const char* mppi_last_error(mppi_t h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_config* cfg,
+                void* stream, mppi_t* out) {
+  if (!robot || !cost || !cfg || !out) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  mppi_s* h = new (std::nothrow) mppi_s();
+  if (!h) return fail(nullptr, MPPI_ERR_OOM, "host allocation failed");
+  std::string why;
+  if (convert(robot, cost, cfg, &h->P, &why) != 0) {
+    delete h;
+    return fail(nullptr, MPPI_ERR_INVALID_ARG, why);
+  }
+  h->reduce_fp64 = cfg->reduce_fp64 ? 1 : 0;
+  h->use_graph = cfg->use_graph ? 1 : 0;
+  const int T = cfg->T, K = cfg->K;
+  auto bail = [&](cudaError_t e, const char* what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    mppi_destroy(h);
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? MPPI_ERR_OOM : MPPI_ERR_CUDA, msg);
+  };
+  cudaError_t e;
+  if (stream) {
+    h->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return bail(e, "cudaStreamCreate");
+    h->own_stream = true;
+  }
+  const size_t plan_b = sizeof(float) * T * NJ;
+  if ((e = cudaMalloc(&h->d_plan[0], plan_b)) != cudaSuccess) return bail(e, "cudaMalloc plan");
+  if ((e = cudaMalloc(&h->d_plan[1], plan_b)) != cudaSuccess) return bail(e, "cudaMalloc plan");
+  if ((e = cudaMalloc(&h->d_ustar, plan_b)) != cudaSuccess) return bail(e, "cudaMalloc ustar");
+  if ((e = cudaMalloc(&h->d_scratch_plan, 2 * plan_b)) != cudaSuccess) return bail(e, "cudaMalloc scratch");
+  if ((e = cudaMalloc(&h->d_S, sizeof(float) * K)) != cudaSuccess) return bail(e, "cudaMalloc S");
+  if ((e = cudaMalloc(&h->d_noise, sizeof(float) * size_t(T) * NJ * K)) != cudaSuccess)
+    return bail(e, "cudaMalloc noise");
+  if ((e = cudaMalloc(&h->d_in, sizeof(float) * 32)) != cudaSuccess) return bail(e, "cudaMalloc in");
+  if ((e = cudaMalloc(&h->d_misc, sizeof(float) * 32)) != cudaSuccess) return bail(e, "cudaMalloc misc");
+  if ((e = cudaMalloc(&h->d_words, sizeof(uint32_t) * 8 * 1024)) != cudaSuccess)
+    return bail(e, "cudaMalloc words");
+  h->out_floats = OUT_PLAN + T * NJ;
+  if ((e = cudaMalloc(&h->d_out, sizeof(float) * h->out_floats)) != cudaSuccess)
+    return bail(e, "cudaMalloc out");
+  if ((e = cudaMalloc(&h->d_iter, sizeof(unsigned long long))) != cudaSuccess)
+    return bail(e, "cudaMalloc iter");
+  if ((e = cudaMallocHost(&h->h_in, sizeof(float) * 32)) != cudaSuccess) return bail(e, "cudaMallocHost");
+  if ((e = cudaMallocHost(&h->h_out, sizeof(float) * h->out_floats)) != cudaSuccess)
+    return bail(e, "cudaMallocHost");
+  std::memset(h->h_in, 0, sizeof(float) * 32);
+  std::memset(h->h_out, 0, sizeof(float) * h->out_floats);
+  if ((e = cudaMemsetAsync(h->d_plan[0], 0, plan_b, h->stream)) != cudaSuccess) return bail(e, "memset");
+  if ((e = cudaMemsetAsync(h->d_plan[1], 0, plan_b, h->stream)) != cudaSuccess) return bail(e, "memset");
+  if ((e = cudaMemsetAsync(h->d_ustar, 0, plan_b, h->stream)) != cudaSuccess) return bail(e, "memset");
+  if ((e = cudaMemsetAsync(h->d_in, 0, sizeof(float) * 32, h->stream)) != cudaSuccess) return bail(e, "memset");
+  if ((e = cudaMemsetAsync(h->d_out, 0, sizeof(float) * h->out_floats, h->stream)) != cudaSuccess)
+    return bail(e, "memset");
+  if ((e = cudaMemsetAsync(h->d_iter, 0, sizeof(unsigned long long), h->stream)) != cudaSuccess)
+    return bail(e, "memset");
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(e, "sync");
+  *out = h;
+  return MPPI_OK;
+}
+
+int mppi_destroy(mppi_t h) {
+  if (!h) return MPPI_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  destroy_graphs(h);
+  cudaFree(h->d_plan[0]);
+  cudaFree(h->d_plan[1]);
+  cudaFree(h->d_ustar);
+  cudaFree(h->d_scratch_plan);
+  cudaFree(h->d_S);
+  cudaFree(h->d_noise);
+  cudaFree(h->d_in);
+  cudaFree(h->d_misc);
+  cudaFree(h->d_words);
+  cudaFree(h->d_out);
+  cudaFree(h->d_iter);
+  if (h->h_in) cudaFreeHost(h->h_in);
+  if (h->h_out) cudaFreeHost(h->h_out);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return MPPI_OK;
+}
+
+int mppi_step(mppi_t h, const float q[7], const float qd[7], const float goal[7],
+              const float plane[4], float tau0_out[7], float* plan_out) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (!q || !qd || !goal || !tau0_out || (h->P.cost.contact && !plane))
+    return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  static const float no_plane[4] = {0.f, 0.f, 1.f, -1e9f};
+  if (!plane) plane = no_plane;
+  int rc = check_inputs(h, q, qd, goal, plane);
+  if (rc != MPPI_OK) return rc;
+  std::memcpy(h->h_in, q, 7 * sizeof(float));
+  std::memcpy(h->h_in + 7, qd, 7 * sizeof(float));
+  std::memcpy(h->h_in + 14, goal, 7 * sizeof(float));
+  std::memcpy(h->h_in + 21, plane, 4 * sizeof(float));
+  const int cur = h->cur;
+  if (h->use_graph) {
+    if (!h->graph[cur]) {
+      cudaGraph_t g;
+      CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue_host_step(h, cur);
+      cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+      if (e != cudaSuccess) return fail(h, MPPI_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+      if (e2 != cudaSuccess) return fail(h, MPPI_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e2));
+      e = cudaGraphInstantiate(&h->graph[cur], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        h->graph[cur] = nullptr;
+        return fail(h, MPPI_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+      }
+    }
+    CUDA_TRY(h, cudaGraphLaunch(h->graph[cur], h->stream));
+  } else {
+    CUDA_TRY(h, enqueue_host_step(h, cur));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  h->cur = cur ^ 1;  // the update wrote the next plan into the other buffer
+  rc = read_status(h);
+  std::memcpy(tau0_out, h->h_out + OUT_TAU0, 7 * sizeof(float));
+  if (plan_out) std::memcpy(plan_out, h->h_out + OUT_PLAN, sizeof(float) * h->P.T * NJ);
+  return rc;
+}
+
+int mppi_step_device(mppi_t h, const float* d_in, float* d_tau0, float* d_plan) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (!d_in) return fail(h, MPPI_ERR_INVALID_ARG, "null d_in");
+  const int cur = h->cur;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_in, d_in, sizeof(float) * IN_FLOATS, cudaMemcpyDeviceToDevice,
+                              h->stream));
+  CUDA_TRY(h, enqueue_update(h, cur));
+  h->cur = cur ^ 1;
+  if (d_tau0)
+    CUDA_TRY(h, cudaMemcpyAsync(d_tau0, h->d_out + OUT_TAU0, 7 * sizeof(float),
+                                cudaMemcpyDeviceToDevice, h->stream));
+  if (d_plan)
+    CUDA_TRY(h, cudaMemcpyAsync(d_plan, h->d_plan[h->cur], sizeof(float) * h->P.T * NJ,
+                                cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_out + OUT_STATUS, h->d_out + OUT_STATUS, 5 * sizeof(float),
+                              cudaMemcpyDeviceToHost, h->stream));
+  return MPPI_OK;
+}
+
+int mppi_sync(mppi_t h) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return read_status(h);
+}
+
+int mppi_get_costs(mppi_t h, float* S_out) {
+  if (!h || !S_out) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, cudaMemcpyAsync(S_out, h->d_S, sizeof(float) * h->P.K, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPPI_OK;
+}
+
+int mppi_get_noise(mppi_t h, float* noise_out) {
+  if (!h || !noise_out) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, cudaMemcpyAsync(noise_out, h->d_noise, sizeof(float) * size_t(h->P.T) * NJ * h->P.K,
+                              cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPPI_OK;
+}
+
+int mppi_get_updated_plan(mppi_t h, float* u_out) {
+  if (!h || !u_out) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, cudaMemcpyAsync(u_out, h->d_ustar, sizeof(float) * h->P.T * NJ, cudaMemcpyDeviceToHost,
+                              h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPPI_OK;
+}
+
+int mppi_get_stats(mppi_t h, double stats[4]) {
+  if (!h || !stats) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  float tmp[4];
+  CUDA_TRY(h, cudaMemcpyAsync(tmp, h->d_out + OUT_STATS, sizeof tmp, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < 4; ++i) stats[i] = tmp[i];
+  return MPPI_OK;
+}
+
+int mppi_set_plan(mppi_t h, const float* u) {
+  if (!h || !u) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  for (int i = 0; i < h->P.T * NJ; ++i)
+    if (!std::isfinite(u[i])) return fail(h, MPPI_ERR_INVALID_ARG, "plan must be finite");
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_plan[h->cur], u, sizeof(float) * h->P.T * NJ,
+                              cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPPI_OK;
+}
+
+int mppi_get_plan(mppi_t h, float* u) {
+  if (!h || !u) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, cudaMemcpyAsync(u, h->d_plan[h->cur], sizeof(float) * h->P.T * NJ,
+                              cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPPI_OK;
+}
+
+int mppi_set_iter(mppi_t h, uint64_t iter) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  unsigned long long v = iter;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_iter, &v, sizeof v, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPPI_OK;
+}
+
+int mppi_get_iter(mppi_t h, uint64_t* iter) {
+  if (!h || !iter) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  unsigned long long v = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&v, h->d_iter, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  *iter = v;
+  return MPPI_OK;
+}
+
+int mppi_rollout_device(mppi_t h, const float* d_in, float* d_S, float* d_noise) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (!d_in || !d_S) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, launch_rollout(h, d_in, h->d_plan[h->cur], d_S, d_noise));
+  return MPPI_OK;
+}
+
+int mppi_update_device(mppi_t h, const float* d_S, const float* d_noise, const float* d_plan,
+                       float* d_ustar, float* d_plan_next) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (!d_S || !d_noise || !d_plan || !d_ustar || !d_plan_next)
+    return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, launch_update(h, d_S, d_noise, d_plan, d_ustar, d_plan_next, nullptr, nullptr));
+  return MPPI_OK;
+}
+
+int mppi_ee_pose(mppi_t h, const float q[7], float pose_out[7]) {
+  if (!h || !q || !pose_out) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_misc, q, 7 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  ee_pose_kernel<<<1, 32, 0, h->stream>>>(h->P, h->d_misc, h->d_misc + 16);
+  cudaError_t e = cudaGetLastError();
+  float r[12];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(r, h->d_misc + 16, sizeof r, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(h, MPPI_ERR_CUDA, std::string("ee_pose: ") + cudaGetErrorString(e));
+  // rotation matrix -> unit quaternion (w >= 0), Shepperd's method
+  const double R[3][3] = {{r[3], r[4], r[5]}, {r[6], r[7], r[8]}, {r[9], r[10], r[11]}};
+  const double tr = R[0][0] + R[1][1] + R[2][2];
+  double w, x, y, z;
+  if (tr > 0) {
+    const double s = std::sqrt(tr + 1.0) * 2;
+    w = 0.25 * s; x = (R[2][1] - R[1][2]) / s; y = (R[0][2] - R[2][0]) / s; z = (R[1][0] - R[0][1]) / s;
+  } else if (R[0][0] > R[1][1] && R[0][0] > R[2][2]) {
+    const double s = std::sqrt(1.0 + R[0][0] - R[1][1] - R[2][2]) * 2;
+    w = (R[2][1] - R[1][2]) / s; x = 0.25 * s; y = (R[0][1] + R[1][0]) / s; z = (R[0][2] + R[2][0]) / s;
+  } else if (R[1][1] > R[2][2]) {
+    const double s = std::sqrt(1.0 + R[1][1] - R[0][0] - R[2][2]) * 2;
+    w = (R[0][2] - R[2][0]) / s; x = (R[0][1] + R[1][0]) / s; y = 0.25 * s; z = (R[1][2] + R[2][1]) / s;
+  } else {
+    const double s = std::sqrt(1.0 + R[2][2] - R[0][0] - R[1][1]) * 2;
+    w = (R[1][0] - R[0][1]) / s; x = (R[0][2] + R[2][0]) / s; y = (R[1][2] + R[2][1]) / s; z = 0.25 * s;
+  }
+  const double n = std::sqrt(w * w + x * x + y * y + z * z);
+  const double sg = w < 0 ? -1.0 : 1.0;
+  pose_out[0] = r[0]; pose_out[1] = r[1]; pose_out[2] = r[2];
+  pose_out[3] = static_cast<float>(sg * w / n);
+  pose_out[4] = static_cast<float>(sg * x / n);
+  pose_out[5] = static_cast<float>(sg * y / n);
+  pose_out[6] = static_cast<float>(sg * z / n);
+  return MPPI_OK;
+}
+
+int mppi_noise_words(mppi_t h, uint64_t iter, uint32_t k0, int count, uint32_t t, uint32_t* out) {
+  if (!h || !out) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  if (count < 1 || count > 1024) return fail(h, MPPI_ERR_INVALID_ARG, "count must be in 1..1024");
+  noise_words_kernel<<<(count + 127) / 128, 128, 0, h->stream>>>(h->P.key0, h->P.key1, iter, k0,
+                                                                 count, t, h->d_words);
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaMemcpyAsync(out, h->d_words, sizeof(uint32_t) * 8 * count, cudaMemcpyDeviceToHost,
+                              h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPPI_OK;
+}
+
+int mppi_time_kernels(mppi_t h, const float* d_in, int iters, float* ms_rollout, float* ms_update) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (!d_in || iters < 1 || !ms_rollout || !ms_update) return fail(h, MPPI_ERR_INVALID_ARG, "bad argument");
+  cudaEvent_t ev[3];
+  for (auto& x : ev) CUDA_TRY(h, cudaEventCreate(&x));
+  float tr = 0.f, tu = 0.f;
+  const size_t plan_f = size_t(h->P.T) * NJ;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < iters && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(ev[0], h->stream);
+    if (e == cudaSuccess) e = launch_rollout(h, d_in, h->d_plan[h->cur], h->d_S, h->d_noise);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+    if (e == cudaSuccess)
+      e = launch_update(h, h->d_S, h->d_noise, h->d_plan[h->cur], h->d_scratch_plan,
+                        h->d_scratch_plan + plan_f, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+    float a = 0.f, b = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+    tr += a;
+    tu += b;
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return fail(h, MPPI_ERR_CUDA, std::string("time_kernels: ") + cudaGetErrorString(e));
+  *ms_rollout = tr / iters;
+  *ms_update = tu / iters;
+  return MPPI_OK;
+}
+
+}  // extern "C"

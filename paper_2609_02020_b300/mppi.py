@@ -1,0 +1,350 @@
+"""Thin Python binding of the C ABI in include/mppi.h (argument marshalling only).
+
+Every step of an update runs in the CUDA library ``libmppi.so``; this module
+only converts numpy arrays / torch tensors to pointers.  There is no CPU
+fallback: if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmppi.so")
+
+NJ = 7
+IN_FLOATS = 25
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_OOM = -2
+ERR_CUDA = -3
+ERR_TIMEOUT = -4
+ERR_NONFINITE = -5
+
+_ERRNAMES = {ERR_INVALID_ARG: "INVALID_ARG", ERR_OOM: "OOM", ERR_CUDA: "CUDA",
+             ERR_TIMEOUT: "TIMEOUT", ERR_NONFINITE: "NONFINITE"}
+
+
+class MPPIError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Robot(C.Structure):
+    _fields_ = [
+        ("n", C.c_int),
+        ("joint_xyz", C.c_double * 3 * NJ),
+        ("joint_rpy", C.c_double * 3 * NJ),
+        ("axis", C.c_double * 3 * NJ),
+        ("com", C.c_double * 3 * NJ),
+        ("mass", C.c_double * NJ),
+        ("inertia", C.c_double * 6 * NJ),
+        ("armature", C.c_double * NJ),
+        ("damping", C.c_double * NJ),
+        ("ee_xyz", C.c_double * 3),
+        ("q_min", C.c_double * NJ),
+        ("q_max", C.c_double * NJ),
+        ("qd_max", C.c_double * NJ),
+        ("tau_max", C.c_double * NJ),
+        ("gravity", C.c_double * 3),
+    ]
+
+
+class Cost(C.Structure):
+    _fields_ = [
+        ("w_pos", C.c_double * 3),
+        ("w_ori", C.c_double * 3),
+        ("w_force", C.c_double),
+        ("f_des", C.c_double),
+        ("w_reg", C.c_double),
+        ("w_qlim", C.c_double),
+        ("w_qdlim", C.c_double),
+        ("w_tau", C.c_double),
+        ("w_posture", C.c_double),
+        ("q_posture", C.c_double * NJ),
+        ("w_terminal", C.c_double),
+        ("contact", C.c_int),
+        ("k_contact", C.c_double),
+        ("d_contact", C.c_double),
+    ]
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("dt", C.c_double),
+        ("T", C.c_int),
+        ("K", C.c_int),
+        ("lambda_", C.c_double),
+        ("sigma", C.c_double * NJ),
+        ("seed", C.c_uint64),
+        ("reduce_fp64", C.c_int),
+        ("use_graph", C.c_int),
+    ]
+
+
+# every symbol include/mppi.h declares
+EXPORTS = [
+    "mppi_create", "mppi_destroy", "mppi_step", "mppi_step_device", "mppi_sync",
+    "mppi_get_costs", "mppi_get_noise", "mppi_get_updated_plan", "mppi_get_stats",
+    "mppi_set_plan", "mppi_get_plan", "mppi_set_iter", "mppi_get_iter",
+    "mppi_rollout_device", "mppi_update_device", "mppi_ee_pose", "mppi_time_kernels",
+    "mppi_noise_words", "mppi_last_error", "mppi_version",
+]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libmppi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} "
+                           "(run python -m paper_2609_02020_b300.build)")
+    L = C.CDLL(path)
+    fp, dp, vp = C.POINTER(C.c_float), C.POINTER(C.c_double), C.c_void_p
+    H = C.c_void_p
+    sig = {
+        "mppi_create": ([C.POINTER(Robot), C.POINTER(Cost), C.POINTER(Config), vp,
+                         C.POINTER(C.c_void_p)], C.c_int),
+        "mppi_destroy": ([H], C.c_int),
+        "mppi_step": ([H, fp, fp, fp, fp, fp, fp], C.c_int),
+        "mppi_step_device": ([H, vp, vp, vp], C.c_int),
+        "mppi_sync": ([H], C.c_int),
+        "mppi_get_costs": ([H, fp], C.c_int),
+        "mppi_get_noise": ([H, fp], C.c_int),
+        "mppi_get_updated_plan": ([H, fp], C.c_int),
+        "mppi_get_stats": ([H, dp], C.c_int),
+        "mppi_set_plan": ([H, fp], C.c_int),
+        "mppi_get_plan": ([H, fp], C.c_int),
+        "mppi_set_iter": ([H, C.c_uint64], C.c_int),
+        "mppi_get_iter": ([H, C.POINTER(C.c_uint64)], C.c_int),
+        "mppi_rollout_device": ([H, vp, vp, vp], C.c_int),
+        "mppi_update_device": ([H, vp, vp, vp, vp, vp], C.c_int),
+        "mppi_ee_pose": ([H, fp, fp], C.c_int),
+        "mppi_time_kernels": ([H, vp, C.c_int, fp, fp], C.c_int),
+        "mppi_noise_words": ([H, C.c_uint64, C.c_uint32, C.c_int, C.c_uint32,
+                              C.POINTER(C.c_uint32)], C.c_int),
+        "mppi_last_error": ([H], C.c_char_p),
+        "mppi_version": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _f32(x, n=None):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def robot_struct(d: dict) -> Robot:
+    r = Robot()
+    r.n = int(d["n"])
+    for name, shape in (("joint_xyz", (NJ, 3)), ("joint_rpy", (NJ, 3)), ("axis", (NJ, 3)),
+                        ("com", (NJ, 3)), ("inertia", (NJ, 6))):
+        v = np.asarray(d[name], dtype=np.float64).reshape(shape)
+        dst = getattr(r, name)
+        for i in range(shape[0]):
+            for j in range(shape[1]):
+                dst[i][j] = v[i, j]
+    for name in ("mass", "armature", "damping", "q_min", "q_max", "qd_max", "tau_max"):
+        v = np.asarray(d[name], dtype=np.float64).reshape(NJ)
+        dst = getattr(r, name)
+        for i in range(NJ):
+            dst[i] = v[i]
+    for name in ("ee_xyz", "gravity"):
+        v = np.asarray(d[name], dtype=np.float64).reshape(3)
+        dst = getattr(r, name)
+        for i in range(3):
+            dst[i] = v[i]
+    return r
+
+
+def cost_struct(d: dict) -> Cost:
+    c = Cost()
+    for a in range(3):
+        c.w_pos[a] = float(np.asarray(d["w_pos"])[a])
+        c.w_ori[a] = float(np.asarray(d["w_ori"])[a])
+    for name in ("w_force", "f_des", "w_reg", "w_qlim", "w_qdlim", "w_tau", "w_posture",
+                 "w_terminal", "k_contact", "d_contact"):
+        setattr(c, name, float(d.get(name, 0.0)))
+    qp = np.asarray(d.get("q_posture", np.zeros(NJ)), dtype=np.float64)
+    for j in range(NJ):
+        c.q_posture[j] = qp[j]
+    c.contact = int(d.get("contact", 0))
+    return c
+
+
+class MPPI:
+    """One controller handle (mppi_create ... mppi_destroy)."""
+
+    def __init__(self, robot: dict, cost: dict, *, dt: float, T: int, K: int, lam: float,
+                 sigma, seed: int, reduce_fp64: bool = False, use_graph: bool = True,
+                 stream=None):
+        self.lib = load()
+        self.T, self.K = int(T), int(K)
+        self._robot = robot_struct(robot)
+        self._cost = cost_struct(cost)
+        cfg = Config()
+        cfg.dt = float(dt)
+        cfg.T = self.T
+        cfg.K = self.K
+        cfg.lambda_ = float(lam)
+        s = np.broadcast_to(np.asarray(sigma, dtype=np.float64), (NJ,))
+        for j in range(NJ):
+            cfg.sigma[j] = float(s[j])
+        cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        cfg.reduce_fp64 = int(bool(reduce_fp64))
+        cfg.use_graph = int(bool(use_graph))
+        self._cfg = cfg
+        h = C.c_void_p()
+        sp = C.c_void_p(stream.cuda_stream) if stream is not None else None
+        rc = self.lib.mppi_create(C.byref(self._robot), C.byref(self._cost), C.byref(cfg), sp,
+                                  C.byref(h))
+        if rc != OK:
+            raise MPPIError(rc, self.lib.mppi_last_error(None).decode())
+        self.h = h
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mppi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc):
+        if rc != OK:
+            raise MPPIError(rc, self.lib.mppi_last_error(self.h).decode())
+        return rc
+
+    # -- updates ------------------------------------------------------------
+    def step(self, q, qd, goal, plane=None, want_plan: bool = True):
+        """mppi_step from host arrays -> (tau0 [7], shifted plan [T, 7] or None)."""
+        tau0 = np.zeros(NJ, dtype=np.float32)
+        plan = np.zeros((self.T, NJ), dtype=np.float32) if want_plan else None
+        pl = _f32(plane, 4) if plane is not None else None
+        self._check(self.lib.mppi_step(self.h, _fp(_f32(q, NJ)), _fp(_f32(qd, NJ)),
+                                       _fp(_f32(goal, 7)), _fp(pl) if pl is not None else None,
+                                       _fp(tau0), _fp(plan) if plan is not None else None))
+        return tau0, plan
+
+    def step_status(self, q, qd, goal, plane=None):
+        """Like step() but returns (rc, tau0) instead of raising on NONFINITE."""
+        tau0 = np.zeros(NJ, dtype=np.float32)
+        pl = _f32(plane, 4) if plane is not None else None
+        rc = self.lib.mppi_step(self.h, _fp(_f32(q, NJ)), _fp(_f32(qd, NJ)), _fp(_f32(goal, 7)),
+                                _fp(pl) if pl is not None else None, _fp(tau0), None)
+        return rc, tau0
+
+    def step_device(self, d_in, d_tau0=None, d_plan=None):
+        """mppi_step_device on torch CUDA tensors (queued; see sync())."""
+        self._check(self.lib.mppi_step_device(self.h, _dptr(d_in), _dptr(d_tau0), _dptr(d_plan)))
+
+    def sync(self) -> int:
+        return self.lib.mppi_sync(self.h)
+
+    def rollout_device(self, d_in, d_S, d_noise=None):
+        self._check(self.lib.mppi_rollout_device(self.h, _dptr(d_in), _dptr(d_S), _dptr(d_noise)))
+
+    def update_device(self, d_S, d_noise, d_plan, d_ustar, d_plan_next):
+        self._check(self.lib.mppi_update_device(self.h, _dptr(d_S), _dptr(d_noise), _dptr(d_plan),
+                                                _dptr(d_ustar), _dptr(d_plan_next)))
+
+    # -- inspection / state -------------------------------------------------
+    def costs(self) -> np.ndarray:
+        S = np.zeros(self.K, dtype=np.float32)
+        self._check(self.lib.mppi_get_costs(self.h, _fp(S)))
+        return S
+
+    def noise(self) -> np.ndarray:
+        """[T*7, K] as stored by the rollouts."""
+        n = np.zeros((self.T * NJ, self.K), dtype=np.float32)
+        self._check(self.lib.mppi_get_noise(self.h, _fp(n)))
+        return n
+
+    def updated_plan(self) -> np.ndarray:
+        u = np.zeros((self.T, NJ), dtype=np.float32)
+        self._check(self.lib.mppi_get_updated_plan(self.h, _fp(u)))
+        return u
+
+    def stats(self) -> np.ndarray:
+        s = np.zeros(4, dtype=np.float64)
+        self._check(self.lib.mppi_get_stats(self.h, s.ctypes.data_as(C.POINTER(C.c_double))))
+        return s
+
+    def set_plan(self, u):
+        self._check(self.lib.mppi_set_plan(self.h, _fp(_f32(u, self.T * NJ))))
+
+    def get_plan(self) -> np.ndarray:
+        u = np.zeros((self.T, NJ), dtype=np.float32)
+        self._check(self.lib.mppi_get_plan(self.h, _fp(u)))
+        return u
+
+    def set_iter(self, it: int):
+        self._check(self.lib.mppi_set_iter(self.h, int(it)))
+
+    def get_iter(self) -> int:
+        v = C.c_uint64()
+        self._check(self.lib.mppi_get_iter(self.h, C.byref(v)))
+        return int(v.value)
+
+    def ee_pose(self, q) -> np.ndarray:
+        out = np.zeros(7, dtype=np.float32)
+        self._check(self.lib.mppi_ee_pose(self.h, _fp(_f32(q, NJ)), _fp(out)))
+        return out
+
+    def noise_words(self, it: int, k0: int, count: int, t: int) -> np.ndarray:
+        """Raw Philox words [count, 8] of the device generator."""
+        out = np.zeros((count, 8), dtype=np.uint32)
+        self._check(self.lib.mppi_noise_words(self.h, int(it), int(k0), int(count), int(t),
+                                              out.ctypes.data_as(C.POINTER(C.c_uint32))))
+        return out
+
+    def time_kernels(self, d_in, iters: int = 10):
+        a, b = C.c_float(), C.c_float()
+        self._check(self.lib.mppi_time_kernels(self.h, _dptr(d_in), int(iters), C.byref(a),
+                                               C.byref(b)))
+        return a.value, b.value
+
+
+def pack_inputs(q, qd, goal, plane=None) -> np.ndarray:
+    """The 25-float input record (q, qd, goal, plane) of mppi_step_device."""
+    pl = np.array([0.0, 0.0, 1.0, -1.0e9]) if plane is None else plane
+    return np.concatenate([_f32(q, NJ), _f32(qd, NJ), _f32(goal, 7), _f32(pl, 4)]).astype(np.float32)
+
+
+def version() -> str:
+    return load().mppi_version().decode()

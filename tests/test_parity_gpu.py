@@ -1,0 +1,377 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 path against the FP64 oracle):
+  * Philox words: bit-exact (integer work);
+  * per-sample cost S_k: |S_gpu - S_orc| <= 1e-4 |S_orc| + 1e-6;
+  * updated plan u* and tau0: <= 1e-5 N m on workloads whose costs FP32
+    resolves (parity_cost); on the heavier free-space weights the plan error
+    minus the first-order effect of the measured cost errors must be
+    <= 1e-5 N m (the error is fully explained by the costs);
+  * the update alone (same costs and noise on both sides): <= 1e-5 N m.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_02020_b300 import mppi, synth
+from _common import (SEED, explained_plan_error, f32, gpu_controller, make_case, noise_ktj,
+                     oracle_step, parity_cost)
+
+pytestmark = pytest.mark.gpu
+
+S_RTOL, S_ATOL = 1e-4, 1e-6
+PLAN_TOL = 1e-5
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def torch_mod():
+    import torch
+    return torch
+
+
+def assert_costs(S_gpu, S_orc):
+    err = np.abs(S_gpu.astype(np.float64) - S_orc)
+    lim = S_RTOL * np.abs(S_orc) + S_ATOL
+    bad = np.nonzero(err > lim)[0]
+    assert bad.size == 0, f"{bad.size} costs off, worst rel {np.max(err / np.abs(S_orc)):.3e}"
+
+
+def run_pair(c, **kw):
+    with gpu_controller(c, **kw) as g:
+        tau0, plan = g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        out = dict(tau0=tau0, plan=plan, S=g.costs(), noise=g.noise(), ustar=g.updated_plan(),
+                   stats=g.stats(), iter=g.get_iter())
+    o = oracle_step(c)
+    return out, o
+
+
+# ---------------------------------------------------------------------------
+# noise (Eq. 2)
+
+def test_philox_words_bit_exact():
+    c = make_case(0)
+    with gpu_controller(c) as g:
+        for it, t, k0 in [(0, 0, 0), (5, 17, 1000), (2 ** 33 + 7, 3, 2 ** 31),
+                          (1, 255, 2 ** 32 - 40)]:
+            w = g.noise_words(it, k0, 64, t)
+            key = [SEED & 0xFFFFFFFF, SEED >> 32]
+            for i in range(64):
+                for call in range(2):
+                    ctr = [(k0 + i) & 0xFFFFFFFF, 2 * t + call, it & 0xFFFFFFFF, it >> 32]
+                    ref = oracle.philox4x32_10(ctr, key)
+                    assert np.array_equal(w[i, 4 * call:4 * call + 4], ref), (it, t, k0, i)
+
+
+def test_noise_matches_oracle():
+    c = make_case(1)
+    g, o = run_pair(c)
+    nz = noise_ktj(g["noise"], c["T"], c["K"])
+    # FP32 Box-Muller against FP64: a few ulp of log, sqrt and sincospi
+    err = np.abs(nz - o["noise"])
+    assert err.max() <= 2e-6 * 2.0 * np.maximum(1.0, np.abs(o["noise"]) / 2.0).max()
+
+
+# ---------------------------------------------------------------------------
+# per-sample costs (Eq. 3) and the plan (Eq. 4)
+
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("contact", [False, True])
+def test_costs_match_oracle(seed, contact):
+    c = make_case(seed, contact=contact)
+    g, o = run_pair(c)
+    assert_costs(g["S"], o["S"])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_plan_matches_oracle(seed):
+    c = make_case(seed, cost=parity_cost())
+    g, o = run_pair(c)
+    assert_costs(g["S"], o["S"])
+    assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL
+    assert np.abs(g["tau0"] - o["ustar"][0]).max() <= PLAN_TOL
+    assert np.abs(g["plan"] - o["plan_next"]).max() <= PLAN_TOL
+    assert g["iter"] == 1
+    # statistics of Eq. 4a
+    assert abs(g["stats"][0] - o["stats"][0]) <= S_RTOL * abs(o["stats"][0])
+    assert abs(g["stats"][2] - o["stats"][2]) <= 1e-3 * o["stats"][2]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_plan_error_explained_by_cost_error(seed):
+    """Free-space weights with S ~ 300 lambda: FP32 cost errors move the
+    weights; after removing their first-order effect the plan agrees."""
+    c = make_case(seed)
+    g, o = run_pair(c)
+    assert_costs(g["S"], o["S"])
+    dS = g["S"].astype(np.float64) - o["S"]
+    expl = explained_plan_error(o["S"], dS, o["noise"], c["lam"])
+    resid = g["ustar"] - o["ustar"] - expl
+    assert np.abs(resid).max() <= PLAN_TOL
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_update_swaps(fp64):
+    """The update alone, both ways: GPU costs and noise into the oracle's FP64
+    update, and the oracle's costs and noise into the GPU update."""
+    torch = torch_mod()
+    c = make_case(2, cost=parity_cost(1.0))
+    with gpu_controller(c, reduce_fp64=fp64) as g:
+        g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        S, nz, us = g.costs(), g.noise(), g.updated_plan()
+        _, ref, nxt, _ = oracle.mppi_update(S.astype(np.float64), noise_ktj(nz, c["T"], c["K"]),
+                                            np.zeros((c["T"], 7)), c["lam"])
+        assert np.abs(us - ref).max() <= (2e-6 if fp64 else PLAN_TOL)
+        o = oracle_step(c)
+        S32 = o["S"].astype(np.float32)
+        n32 = o["noise"].astype(np.float32)
+        dev = "cuda"
+        d_S = torch.tensor(S32, device=dev)
+        d_n = torch.tensor(n32.transpose(1, 2, 0).reshape(c["T"] * 7, c["K"]).copy(), device=dev)
+        plan = np.random.default_rng(3).normal(0, 1, (c["T"], 7)).astype(np.float32)
+        d_p = torch.tensor(plan, device=dev)
+        d_u = torch.zeros_like(d_p)
+        d_x = torch.zeros_like(d_p)
+        g.update_device(d_S, d_n, d_p, d_u, d_x)
+        torch.cuda.synchronize()
+        _, ref, nxt, _ = oracle.mppi_update(S32.astype(np.float64), n32.astype(np.float64),
+                                            plan.astype(np.float64), c["lam"])
+        assert np.abs(d_u.cpu().numpy() - ref).max() <= (2e-6 if fp64 else PLAN_TOL)
+        assert np.abs(d_x.cpu().numpy() - nxt).max() <= (2e-6 if fp64 else PLAN_TOL)
+
+
+def test_update_nonfinite_costs():
+    torch = torch_mod()
+    c = make_case(0, K=300, T=5)
+    rng = np.random.default_rng(0)
+    S = rng.uniform(0, 3, c["K"]).astype(np.float32)
+    S[[0, 17, 299]] = [np.nan, np.inf, -np.inf]
+    nz = rng.normal(0, 2, (c["T"] * 7, c["K"])).astype(np.float32)
+    plan = rng.normal(0, 1, (c["T"], 7)).astype(np.float32)
+    with gpu_controller(c) as g:
+        dS, dn, dp = (torch.tensor(x, device="cuda") for x in (S, nz, plan))
+        du, dx = torch.zeros_like(dp), torch.zeros_like(dp)
+        g.update_device(dS, dn, dp, du, dx)
+        _, ref, nxt, _ = oracle.mppi_update(S.astype(np.float64), noise_ktj(nz, c["T"], c["K"]),
+                                            plan.astype(np.float64), c["lam"])
+        assert np.abs(du.cpu().numpy() - ref).max() <= PLAN_TOL
+        # no finite cost at all: the plan is kept as it is, not shifted
+        dS.fill_(float("nan"))
+        g.update_device(dS, dn, dp, du, dx)
+        assert np.array_equal(du.cpu().numpy(), plan)
+        assert np.array_equal(dx.cpu().numpy(), plan)
+
+
+def test_step_with_no_finite_cost_keeps_plan():
+    c = make_case(0, K=64, T=4)
+    with gpu_controller(c) as g:
+        p0 = np.random.default_rng(1).normal(0, 1, (4, 7)).astype(np.float32)
+        g.set_plan(p0)
+        qd = np.full(7, 1e18, dtype=np.float32)  # finite input whose rollouts overflow
+        rc, _ = g.step_status(c["q"], qd, c["goal"], c["plane"])
+        assert rc == mppi.ERR_NONFINITE
+        assert np.array_equal(g.get_plan(), p0)
+        assert g.get_iter() == 0
+        assert g.stats()[3] == 64
+        # the handle stays usable
+        tau0, _ = g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        assert np.all(np.isfinite(tau0)) and g.get_iter() == 1
+
+
+# ---------------------------------------------------------------------------
+# sizes: ragged tails of the 128-thread rollout blocks, K = 1, T = 1
+
+@pytest.mark.parametrize("K,T", [(1, 18), (2, 3), (31, 1), (33, 2), (129, 7), (1000, 5),
+                                 (128, 18)])
+def test_sizes(K, T):
+    c = make_case(4, cost=parity_cost(), K=K, T=T)
+    g, o = run_pair(c)
+    assert_costs(g["S"], o["S"])
+    assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL
+    assert np.abs(g["plan"] - o["plan_next"]).max() <= PLAN_TOL
+    if K == 1:
+        nz = noise_ktj(g["noise"], T, K)[0]
+        assert np.array_equal(g["ustar"], nz.astype(np.float32))
+
+
+def test_fp64_reduction_matches():
+    c = make_case(3, cost=parity_cost())
+    g, o = run_pair(c, reduce_fp64=True)
+    assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL
+
+
+# ---------------------------------------------------------------------------
+# execution modes are bitwise identical; resume from a checkpoint
+
+def test_graph_eager_device_paths_identical():
+    torch = torch_mod()
+    c = make_case(5, contact=True, K=1000, T=9)
+    res = []
+    for use_graph in (True, False):
+        with gpu_controller(c, use_graph=use_graph) as g:
+            outs = [g.step(c["q"], c["qd"], c["goal"], c["plane"]) for _ in range(3)]
+            res.append(outs)
+    with gpu_controller(c) as g:
+        d_in = torch.tensor(mppi.pack_inputs(c["q"], c["qd"], c["goal"], c["plane"]), device="cuda")
+        d_tau = torch.zeros(7, device="cuda")
+        d_plan = torch.zeros(c["T"], 7, device="cuda")
+        outs = []
+        for _ in range(3):
+            g.step_device(d_in, d_tau, d_plan)
+            assert g.sync() == 0
+            outs.append((d_tau.cpu().numpy(), d_plan.cpu().numpy()))
+        res.append(outs)
+    for r in res[1:]:
+        for (a, pa), (b, pb) in zip(res[0], r):
+            assert np.array_equal(a, b) and np.array_equal(pa, pb)
+
+
+def test_resume_from_plan_and_iter():
+    c = make_case(6, contact=True, K=512, T=10)
+    with gpu_controller(c) as g:
+        for _ in range(3):
+            g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        plan, it = g.get_plan(), g.get_iter()
+        assert it == 3
+        want = g.step(c["q"], c["qd"], c["goal"], c["plane"])
+    with gpu_controller(c) as g2:
+        g2.set_plan(plan)
+        g2.set_iter(it)
+        got = g2.step(c["q"], c["qd"], c["goal"], c["plane"])
+    assert np.array_equal(want[0], got[0]) and np.array_equal(want[1], got[1])
+
+
+def test_warm_start_shift_across_updates():
+    """Two consecutive updates against the oracle: the second samples around
+    the first's shifted plan with iter = 1."""
+    c = make_case(1, cost=parity_cost(), K=512, T=12)
+    with gpu_controller(c) as g:
+        g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        plan1 = g.get_plan()
+        g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        u2 = g.updated_plan()
+    o1 = oracle_step(c)
+    assert np.abs(plan1 - o1["plan_next"]).max() <= PLAN_TOL
+    o2 = oracle_step(c, plan=plan1, it=1)
+    assert np.abs(u2 - o2["ustar"]).max() <= PLAN_TOL
+
+
+# ---------------------------------------------------------------------------
+# kinematics helper, the paper's own workload, and the full-size workload
+
+def test_ee_pose_matches_oracle():
+    c = make_case(2)
+    with gpu_controller(c) as g:
+        for s in range(5):
+            q = f32(synth.state(50 + s, c["arm"])[0])
+            pose = g.ee_pose(q)
+            _, _, Re, pe = oracle.fk(c["rb"], q)
+            assert np.abs(pose[:3] - pe).max() < 2e-6
+            Rg = oracle.quat_matrix(pose[3:].astype(np.float64))
+            assert np.abs(Rg - Re).max() < 2e-6
+
+
+def test_paper_table1_workload():
+    """Table I's contact-mode sizes and weights (K=128, T=30, dt=0.006)."""
+    cfg = json.load(open(os.path.join(HERE, "golden", "table1_contact.json")))
+    cost = synth.cost_contact()
+    cost.update(w_pos=np.array(cfg["W_pos"]), w_ori=np.array(cfg["W_ori"]),
+                w_force=cfg["W_force_normal"], w_reg=cfg["W_reg"], f_des=4.0)
+    c = make_case(7, cost=cost, K=cfg["K"], T=cfg["T"], dt=cfg["dt"], penetration=0.004)
+    g, o = run_pair(c)
+    assert_costs(g["S"], o["S"])
+    order = np.argsort(o["S"])
+    gap = o["S"][order[1]] - o["S"][order[0]]
+    dS = np.abs(g["S"].astype(np.float64) - o["S"]).max()
+    assert np.argmin(g["S"]) == order[0]
+    if gap > 40.0 * max(dS, 1e-30) * c["lam"] or gap > 40 * c["lam"]:
+        assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL
+
+
+def test_full_size_workload_sampled():
+    """K=16384, T=18 with contact (the benchmark's workload): sampled costs
+    and noise against single oracle rollouts; the update against the FP64
+    update of the GPU's own costs and noise."""
+    c = make_case(0, contact=True, K=16384, T=18)
+    with gpu_controller(c) as g:
+        g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        S, nz, us = g.costs(), g.noise(), g.updated_plan()
+    ks = sorted(set(np.linspace(0, c["K"] - 1, 40).astype(int).tolist() + [c["K"] - 1, 127, 128]))
+    nzk = noise_ktj(nz, c["T"], c["K"])
+    for k in ks:
+        Sk, nk = oracle.rollout(c["rb"], c["oc"], c["dt"], c["T"], c["sigma"], c["seed"], 0, k,
+                                c["q"], c["qd"], c["goal"], c["plane"], np.zeros((c["T"], 7)),
+                                want_noise=True)
+        assert abs(S[k] - Sk) <= S_RTOL * abs(Sk) + S_ATOL, k
+        assert np.abs(nzk[k] - nk).max() <= 1e-5
+    _, ref, _, _ = oracle.mppi_update(S.astype(np.float64), nzk, np.zeros((c["T"], 7)), c["lam"])
+    assert np.abs(us - ref).max() <= PLAN_TOL
+
+
+def test_rollout_device_matches_step_costs():
+    torch = torch_mod()
+    c = make_case(3, contact=True, K=777, T=6)
+    with gpu_controller(c) as g:
+        d_in = torch.tensor(mppi.pack_inputs(c["q"], c["qd"], c["goal"], c["plane"]), device="cuda")
+        d_S = torch.zeros(c["K"], device="cuda")
+        d_n = torch.zeros(c["T"] * 7, c["K"], device="cuda")
+        g.rollout_device(d_in, d_S, d_n)
+        torch.cuda.synchronize()
+        g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        assert np.array_equal(d_S.cpu().numpy(), g.costs())
+        assert np.array_equal(d_n.cpu().numpy(), g.noise())
+
+
+def test_time_kernels_leaves_state():
+    torch = torch_mod()
+    c = make_case(3, contact=True, K=2048, T=18)
+    with gpu_controller(c) as g:
+        g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        p, it = g.get_plan(), g.get_iter()
+        d_in = torch.tensor(mppi.pack_inputs(c["q"], c["qd"], c["goal"], c["plane"]), device="cuda")
+        tr, tu = g.time_kernels(d_in, 3)
+        assert tr > 0 and tu > 0
+        assert np.array_equal(g.get_plan(), p) and g.get_iter() == it
+
+
+# ---------------------------------------------------------------------------
+# receding horizon with contact: GPU controller on the FP64 plant
+
+def plant_step(c, q, qd, tau, dt, sub=10):
+    h = dt / sub
+    for _ in range(sub):
+        f, tex = oracle.contact(c["rb"], c["oc"], c["plane"], q, qd)
+        qdd = oracle.forward_dynamics(c["rb"], q, qd, tau + tex)
+        qd = qd + qdd * h
+        q = q + qd * h
+    return q, qd
+
+
+def test_receding_horizon_contact_loop():
+    """200 warm-started updates (K=4096, T=18) closing the loop on the FP64
+    model with a zero-order hold; one update mid-way is checked against the
+    oracle from the same state, plan and iter."""
+    c = make_case(0, contact=True, K=4096, T=18, penetration=0.02)
+    q, qd = c["q"].copy(), c["qd"].copy()
+    gcomp = oracle.rnea(c["rb"], q, np.zeros(7), np.zeros(7))
+    forces = []
+    with gpu_controller(c) as g:
+        g.set_plan(np.tile(gcomp, (c["T"], 1)).astype(np.float32))
+        for it in range(200):
+            if it == 100:
+                plan = g.get_plan()
+                q32, qd32 = f32(q), f32(qd)
+                tau0, _ = g.step(q32, qd32, c["goal"], c["plane"])
+                S = g.costs()
+                o = oracle_step(c, plan=plan, it=100, q=q32, qd=qd32, want_noise=False)
+                assert_costs(S, o["S"])
+            else:
+                tau0, _ = g.step(f32(q), f32(qd), c["goal"], c["plane"])
+            assert np.all(np.isfinite(tau0))
+            q, qd = plant_step(c, q, qd, tau0.astype(np.float64), c["dt"])
+            forces.append(oracle.contact(c["rb"], c["oc"], c["plane"], q, qd)[0])
+        assert g.get_iter() == 200
+    assert np.all(np.isfinite(q)) and np.all(np.abs(qd) < 50)
