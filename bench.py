@@ -35,11 +35,17 @@ K_DEFAULT, T_DEFAULT, DT = 16384, 18, 0.01
 SIGMA, LAMBDA, SEED = 2.0, 1.0, 0xC0FFEE
 L2_FLUSH_BYTES = 256 << 20  # twice the 126 MB L2
 
-# FP32 floating-point operations the rollout kernel executes per rollout-step
-# (FADD + FMUL + 2 x FFMA, plus MUFU as 1), counted by ncu on the rollout
-# kernel (smsp__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on) and
-# divided by K*T; the derivation is in the design notes.
-FLOP_PER_ROLLOUT_STEP = None
+# FP32 floating-point operations of one rollout-step (one sample advanced by
+# one step: noise, kinematics, RNEA, CRBA, LDL^T solve, Euler step, contact
+# and costs): FADD + FMUL + 2 x FFMA executed by rollout_kernel, counted by
+# ncu (smsp__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on) on the
+# contact workload at K=4096, T=18 and divided by K*T.
+FLOP_PER_ROLLOUT_STEP = 4811.0
+# DRAM read + write bytes of one rollout_kernel launch at K=16384, T=18
+# (ncu dram__bytes_{read,write}.sum, mean of two launches).  The 8.3 MB of
+# stored noise stays in L2 for update_kernel and is not written back inside
+# the launch.
+ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = 115456
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 
@@ -47,7 +53,7 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--K", type=int, default=K_DEFAULT)
@@ -88,13 +94,20 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 10.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
+
+    def mark(self):
+        """Index of the next sample: rows from here on fall in the timed region."""
+        return len(self.rows)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -108,12 +121,13 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
-        if not self.rows:
+    def summary(self, spans=None):
+        rows = self.rows if not spans else [r for a, b in spans for r in self.rows[a:b]]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for r in rows:
             try:
                 sm.append(float(r[1]))
                 mx = float(r[2])
@@ -129,7 +143,9 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on the host cores
 
-def cpu_baseline(K_sample: int, T: int, reps: int = 2):
+def cpu_baseline(K: int, T: int, budget_s: float = 10.0):
+    """The oracle, as it stands, on the host cores: full FP64 updates of the
+    same workload repeated until about `budget_s` seconds have passed."""
     import oracle
     from paper_2609_02020_b300 import synth
     arm, cost, q, qd, goal = workload(0)
@@ -139,14 +155,16 @@ def cpu_baseline(K_sample: int, T: int, reps: int = 2):
     cores = os.cpu_count() or 1
     nth = min(cores, oracle.max_threads())
     plan = np.zeros((T, 7))
+    reps = 0
     t0 = time.perf_counter()
-    for r in range(reps):
-        oracle.mppi_step(rb, oc, DT, T, K_sample, LAMBDA, np.full(7, SIGMA), SEED, r, q, qd, goal,
+    while reps == 0 or time.perf_counter() - t0 < budget_s:
+        oracle.mppi_step(rb, oc, DT, T, K, LAMBDA, np.full(7, SIGMA), SEED, reps, q, qd, goal,
                          plane, plan, nthreads=nth)
+        reps += 1
     dt = time.perf_counter() - t0
-    return {"value": K_sample * T * reps / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
-            "sample": f"{reps} full FP64 updates at K={K_sample}, T={T} (same arm, contact "
-                      f"cost), OpenMP over samples on {nth} threads",
+    return {"value": K * T * reps / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": f"{reps} full FP64 updates at K={K}, T={T} (same arm and contact cost), "
+                      f"OpenMP over samples on {nth} threads, {dt:.1f} s",
             "seconds": dt}
 
 
@@ -154,7 +172,6 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     K, T = args.K, args.T
-    K_sample = min(K, 2048)
     import oracle
     from paper_2609_02020_b300 import synth
     arm, cost, q, qd, goal = workload(0)
@@ -162,6 +179,13 @@ def run_reference(args, rank, world):
     plane = synth.plane_through(oracle.fk(rb, q)[3][2])
     nth = min(os.cpu_count() or 1, oracle.max_threads())
     plan = np.zeros((T, 7))
+    # size each step's sample so the whole run takes about two minutes
+    t0 = time.perf_counter()
+    oracle.mppi_step(rb, oc, DT, T, 512, LAMBDA, np.full(7, SIGMA), SEED, 0, q, qd, goal, plane,
+                     plan, nthreads=nth)
+    per_sample = (time.perf_counter() - t0) / 512
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    K_sample = int(max(64, min(K, budget / per_sample)))
     for w in range(args.warmup):
         oracle.mppi_step(rb, oc, DT, T, K_sample, LAMBDA, np.full(7, SIGMA), SEED, w, q, qd, goal,
                          plane, plan, nthreads=nth)
@@ -222,8 +246,14 @@ def run_ours(args, rank, world):
     assert ctl.sync() == 0
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    barrier()
+    q32 = np.asarray(q, np.float32)
+    qd32 = np.asarray(qd, np.float32)
+    g32 = np.asarray(goal, np.float32)
+    p32 = np.asarray(plane, np.float32)
+    spans = []
     with ClockSampler(dev) as clk:
+        barrier()
+        a = clk.mark()
         t_wall = time.perf_counter()
         for i in range(args.steps):
             flush.zero_()
@@ -232,30 +262,29 @@ def run_ours(args, rank, world):
             ends[i].record(stream)
         barrier()
         t_wall = time.perf_counter() - t_wall
-    rc = ctl.sync()
-    if rc != 0:
-        raise RuntimeError(f"update failed with status {rc}")
-    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
-    mean_ms = float(step_ms.mean())
-    launches = 2 * args.steps  # rollout_kernel + update_kernel per update
+        spans.append((a, clk.mark()))
+        rc = ctl.sync()
+        if rc != 0:
+            raise RuntimeError(f"update failed with status {rc}")
+        step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+        mean_ms = float(step_ms.mean())
+        launches = 2 * args.steps  # rollout_kernel + update_kernel per update
 
-    # --- per-kernel times for the roofline (events on the library stream) ---
-    ms_roll, ms_upd = ctl.time_kernels(d_in, 50)
+        # --- per-kernel times for the roofline (events on the library stream)
+        ms_roll, ms_upd = ctl.time_kernels(d_in, 200)
 
-    # --- end to end through the public host call ----------------------------
-    q32 = np.asarray(q, np.float32)
-    qd32 = np.asarray(qd, np.float32)
-    g32 = np.asarray(goal, np.float32)
-    p32 = np.asarray(plane, np.float32)
-    for _ in range(args.warmup):
-        ctl.step(q32, qd32, g32, p32)
-    barrier()
-    e2e_ms = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        ctl.step(q32, qd32, g32, p32)
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    barrier()
+        # --- end to end through the public host call --------------------------
+        for _ in range(args.warmup):
+            ctl.step(q32, qd32, g32, p32)
+        barrier()
+        a = clk.mark()
+        e2e_ms = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            ctl.step(q32, qd32, g32, p32)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        barrier()
+        spans.append((a, clk.mark()))
     e2e_ms = np.array(e2e_ms)
 
     # --- aggregate over ranks -------------------------------------------------
@@ -272,14 +301,15 @@ def run_ours(args, rank, world):
     if rank != 0:
         ctl.close()
         return
-    clocks = clk.summary()
+    clocks = clk.summary(spans)
     sm_mhz = clocks.get("sm_mhz") or 2032.0
     peak_max = SM_COUNT * FP32_LANES_PER_SM * 2 * 2032e6 / 1e12
     roof = None
     if FLOP_PER_ROLLOUT_STEP:
         achieved = FLOP_PER_ROLLOUT_STEP * K * T / (ms_roll * 1e-3) / 1e12
+        traffic = ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH if (K, T) == (K_DEFAULT, T_DEFAULT) else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
-                "frac": achieved / peak_max, "traffic": ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH,
+                "frac": achieved / peak_max, "traffic": traffic,
                 "kernel": "rollout_kernel", "kernel_ms": ms_roll,
                 "peak_note": "FP32 peak of 148 SMs x 128 lanes x 2 FLOP at the 2032 MHz "
                              "maximum SM clock (derived; no measured FP32 peak)"}
@@ -301,12 +331,10 @@ def run_ours(args, rank, world):
             "gpu_launches": launches,
             "wall_s": t_wall}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(min(K, 4096), T)
+        line["cpu_baseline"] = cpu_baseline(K, T)
     ctl.close()
     print(json.dumps(line), flush=True)
 
-
-ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def main():

@@ -179,7 +179,7 @@ __device__ __forceinline__ void forward_sweep(const RobotK& rb, const float q[NJ
     float RF[9];
     mm3(R, L.F, RF);
     float s, c;
-    sincospif(q[i] * 0.318309886183790672f, &s, &c);
+    sincosf(q[i], &s, &c);
     // R = RF * Rz(q): columns 0 and 1 rotate, column 2 is the joint axis
 #pragma unroll
     for (int r = 0; r < 3; ++r) {

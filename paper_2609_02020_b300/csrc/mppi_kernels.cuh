@@ -12,7 +12,7 @@
 namespace mppi_dev {
 
 constexpr int T_MAX = 256;
-constexpr int ROLLOUT_BLOCK = 128;
+constexpr int ROLLOUT_BLOCK = 32;
 constexpr int UPDATE_BLOCK = 256;
 
 // Offsets in the per-handle output record (floats): tau0, status, stats.
@@ -21,36 +21,27 @@ constexpr int OUT_STATUS = 7;   // written as an int: 0 ok, 1 no finite cost
 constexpr int OUT_STATS = 8;    // S_min, Z, n_eff, n_nonfinite
 constexpr int OUT_PLAN = 16;    // shifted plan [T][7]
 
-// One rollout per thread.  plan: [T][7] nominal torques; in: IN_FLOATS
-// inputs; iter: update counter (device); S: [K] costs; noise: [T*7][K].
+// One rollout (sample k of T steps) of the problem P: Eq. 1-3 with Eq. 5-7
+// and the running cost of Eq. 9-14.  in: IN_FLOATS inputs and plan: [T][7]
+// nominal torques (both usually staged in shared memory); returns S_k and,
+// when STORE_NOISE, writes dtau to noise[(t*7 + j) * K + k].
 template <bool STORE_NOISE>
-__global__ void __launch_bounds__(ROLLOUT_BLOCK)
-rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
-               const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
-               float* __restrict__ S, float* __restrict__ noise) {
-  __shared__ float s_plan[T_MAX * NJ];
-  __shared__ float s_in[IN_FLOATS];
+__device__ __forceinline__ float rollout_sample(const ProbK& P, const float* in, const float* plan,
+                                                uint64_t iter, int k, float* __restrict__ noise) {
   const int T = P.T, K = P.K;
-  for (int i = threadIdx.x; i < T * NJ; i += blockDim.x) s_plan[i] = plan[i];
-  if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
-  __syncthreads();
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const uint64_t iter = *iter_p;
-
   float q[NJ], qd[NJ];
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
-    q[j] = s_in[j];
-    qd[j] = s_in[NJ + j];
+    q[j] = in[j];
+    qd[j] = in[NJ + j];
   }
-  const float pdes[3] = {s_in[14], s_in[15], s_in[16]};
+  const float pdes[3] = {in[14], in[15], in[16]};
   float Rd[9];
   {
-    const float qt[4] = {s_in[17], s_in[18], s_in[19], s_in[20]};
+    const float qt[4] = {in[17], in[18], in[19], in[20]};
     quat_to_R(qt, Rd);
   }
-  const float plane[4] = {s_in[21], s_in[22], s_in[23], s_in[24]};
+  const float plane[4] = {in[21], in[22], in[23], in[24]};
   const CostK& C = P.cost;
   const bool contact = C.contact != 0;
 
@@ -69,7 +60,7 @@ rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
     for (int j = 0; j < NJ; ++j) {
       const float du = P.sigma[j] * z[j];
       if (STORE_NOISE) noise[static_cast<size_t>(t * NJ + j) * K + k] = du;
-      v[j] = s_plan[t * NJ + j] + du;
+      v[j] = plan[t * NJ + j] + du;
     }
     // Eq. 5-6: qdd = M^-1 (v + J^T F_ext - h)
     float h[NJ], M[NJ * (NJ + 1) / 2];
@@ -115,7 +106,25 @@ rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
     Sacc += static_cast<double>(cst) + static_cast<double>(cj);
   }
   if (C.wterm != 0.f) Sacc += static_cast<double>(C.wterm * motion_cost(C, pdes, Rd, ee));
-  S[k] = static_cast<float>(Sacc);
+  return static_cast<float>(Sacc);
+}
+
+// One rollout per thread.  plan: [T][7] nominal torques; in: IN_FLOATS
+// inputs; iter: update counter (device); S: [K] costs; noise: [T*7][K].
+template <bool STORE_NOISE>
+__global__ void __launch_bounds__(ROLLOUT_BLOCK)
+rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
+               const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
+               float* __restrict__ S, float* __restrict__ noise) {
+  __shared__ float s_plan[T_MAX * NJ];
+  __shared__ float s_in[IN_FLOATS];
+  const int T = P.T, K = P.K;
+  for (int i = threadIdx.x; i < T * NJ; i += blockDim.x) s_plan[i] = plan[i];
+  if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
+  __syncthreads();
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  S[k] = rollout_sample<STORE_NOISE>(P, s_in, s_plan, *iter_p, k, noise);
 }
 
 // ---------------------------------------------------------------------------
@@ -241,7 +250,7 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
 }
 
 // Raw Philox words of (iter, t) for samples k0 + i, i < count: out[8 i + 4 call + w].
-__global__ void noise_words_kernel(uint32_t key0, uint32_t key1, uint64_t iter, uint32_t k0,
+static __global__ void noise_words_kernel(uint32_t key0, uint32_t key1, uint64_t iter, uint32_t k0,
                                    int count, uint32_t t, uint32_t* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
@@ -256,7 +265,7 @@ __global__ void noise_words_kernel(uint32_t key0, uint32_t key1, uint64_t iter, 
 }
 
 // End-effector pose at q (one thread): p (3) and R (9, row-major).
-__global__ void ee_pose_kernel(const __grid_constant__ ProbK P, const float* __restrict__ q_in,
+static __global__ void ee_pose_kernel(const __grid_constant__ ProbK P, const float* __restrict__ q_in,
                                float* __restrict__ out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   float q[NJ], qd[NJ];

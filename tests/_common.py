@@ -18,9 +18,11 @@ def f32(x):
     return np.asarray(x, dtype=np.float32).astype(np.float64)
 
 
-def parity_cost(scale: float = 0.1) -> dict:
-    """Free-space weights scaled so that S is O(10-100) lambda: FP32 costs
-    then resolve the weights to the 1e-5 N m plan tolerance."""
+def parity_cost(scale: float = 0.05) -> dict:
+    """Free-space weights scaled so that S is O(10-50) lambda.  FP32 rollouts
+    carry a relative cost error of about 2e-7, and the plan moves by about
+    sigma * (cost error) / lambda through the weights of Eq. 4a, so the 1e-5
+    N m plan tolerance needs S / lambda of a few tens at most."""
     c = synth.cost_free_space()
     for k in ("w_pos", "w_ori"):
         c[k] = np.asarray(c[k]) * scale
