@@ -21,7 +21,8 @@
  * device buffers it allocates in mppi_create and frees them in mppi_destroy.
  * All entry points return MPPI_OK (0) or a negative MPPI_ERR_* code; the
  * message of the last failure on a handle is available from mppi_last_error
- * (and from mppi_last_error(NULL) for failures of mppi_create).  On any error
+ * (and from mppi_last_error(NULL) for failures of mppi_create and
+ * mppi_step_static).  On any error
  * the nominal plan is left as it was.  A handle may be used by one host thread
  * at a time; distinct handles are independent.
  *
@@ -210,8 +211,38 @@ MPPI_API int mppi_time_kernels(mppi_t h, const float* d_in, int iters, float* ms
 MPPI_API int mppi_noise_words(mppi_t h, uint64_t iter, uint32_t k0, int count, uint32_t t,
                               uint32_t* out);
 
-/* Message of the last failure on h, or of the last mppi_create failure of the
- * calling thread when h is NULL.  Never NULL. */
+/* Allocation-free update.  The paper has no counterpart: this entry point is
+ * for callers that cannot allocate device memory while they run, such as a
+ * hard-real-time control thread (cudaMalloc may block on the device and has
+ * no latency bound) or a plug-in whose host application owns all device
+ * memory through its own pool.  It runs one update (rollouts, Eq. 4 and the
+ * shift) like mppi_step_device, without a handle and without any allocation:
+ *   robot, cost, cfg: as for mppi_create (host records, copied per call);
+ *     cfg->K must be <= MPPI_STATIC_K_MAX, else MPPI_ERR_INVALID_ARG;
+ *   iter: the update counter used in the Philox counter;
+ *   d_in: 25 device floats (q, qd, goal, plane); d_plan: nominal plan [T][7];
+ *   d_ustar, d_plan_next: device outputs [T][7] (u* and the shifted plan;
+ *     when no sample has a finite cost both receive d_plan unchanged);
+ *   stream: cudaStream_t to queue on (NULL: the legacy default stream).
+ * The work is queued and the call returns without waiting.  The per-sample
+ * costs live in one file-scope device array of MPPI_STATIC_K_MAX floats
+ * (about 256 KB), which every GPU that loads the library holds until the
+ * process exits; the noise is regenerated instead of stored.  Every call
+ * shares that array and overwrites it, so calls whose work overlaps on the
+ * GPU (different streams, or different host threads, on the same device)
+ * race and must be serialised by the caller.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Errors
+ * are reported by the return code, with the message in
+ * mppi_last_error(NULL). */
+#define MPPI_STATIC_K_MAX 65536
+MPPI_API int mppi_step_static(const mppi_robot* robot, const mppi_cost* cost,
+                              const mppi_config* cfg, uint64_t iter, const float* d_in,
+                              const float* d_plan, float* d_ustar, float* d_plan_next,
+                              void* stream);
+
+/* Message of the last failure on h, or of the last mppi_create or
+ * mppi_step_static failure of the calling thread when h is NULL.  Never NULL. */
 MPPI_API const char* mppi_last_error(mppi_t h);
 
 /* Library version string. */

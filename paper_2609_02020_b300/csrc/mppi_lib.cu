@@ -312,6 +312,15 @@ int read_status(mppi_s* h) {
 
 }  // namespace
 
+// Message for mppi_last_error(NULL) from the other translation units.
+void mppi_set_thread_error(const std::string& msg) { g_create_err = msg; }
+
+// Parameter conversion shared with the other translation units of the library.
+int mppi_convert_params(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg,
+                        ProbK* P, std::string* why) {
+  return convert(rb, c, cfg, P, why);
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 

@@ -92,7 +92,7 @@ EXPORTS = [
     "mppi_get_costs", "mppi_get_noise", "mppi_get_updated_plan", "mppi_get_stats",
     "mppi_set_plan", "mppi_get_plan", "mppi_set_iter", "mppi_get_iter",
     "mppi_rollout_device", "mppi_update_device", "mppi_ee_pose", "mppi_time_kernels",
-    "mppi_noise_words", "mppi_last_error", "mppi_version",
+    "mppi_noise_words", "mppi_step_static", "mppi_last_error", "mppi_version",
 ]
 
 _lib = None
@@ -130,6 +130,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_time_kernels": ([H, vp, C.c_int, fp, fp], C.c_int),
         "mppi_noise_words": ([H, C.c_uint64, C.c_uint32, C.c_int, C.c_uint32,
                               C.POINTER(C.c_uint32)], C.c_int),
+        "mppi_step_static": ([C.POINTER(Robot), C.POINTER(Cost), C.POINTER(Config), C.c_uint64,
+                              vp, vp, vp, vp, vp], C.c_int),
         "mppi_last_error": ([H], C.c_char_p),
         "mppi_version": ([], C.c_char_p),
     }
@@ -338,6 +340,29 @@ class MPPI:
         self._check(self.lib.mppi_time_kernels(self.h, _dptr(d_in), int(iters), C.byref(a),
                                                C.byref(b)))
         return a.value, b.value
+
+
+def step_static(robot: dict, cost: dict, *, dt: float, T: int, K: int, lam: float, sigma,
+                seed: int, it: int, d_in, d_plan, d_ustar, d_plan_next, stream=None) -> None:
+    """mppi_step_static: one update without any device allocation (torch
+    CUDA tensors in and out; queued on `stream`, torch's current stream when
+    None)."""
+    L = load()
+    cfg = Config()
+    cfg.dt, cfg.T, cfg.K, cfg.lambda_ = float(dt), int(T), int(K), float(lam)
+    s = np.broadcast_to(np.asarray(sigma, dtype=np.float64), (NJ,))
+    for j in range(NJ):
+        cfg.sigma[j] = float(s[j])
+    cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    rb, cs = robot_struct(robot), cost_struct(cost)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    rc = L.mppi_step_static(C.byref(rb), C.byref(cs), C.byref(cfg), int(it), _dptr(d_in),
+                            _dptr(d_plan), _dptr(d_ustar), _dptr(d_plan_next),
+                            C.c_void_p(stream.cuda_stream))
+    if rc != OK:
+        raise MPPIError(rc, L.mppi_last_error(None).decode())
 
 
 def pack_inputs(q, qd, goal, plane=None) -> np.ndarray:
