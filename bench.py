@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--K", type=int, default=K_DEFAULT)
     ap.add_argument("--T", type=int, default=T_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="rollout kernel: 0 library default, 1 unrolled, 2 rolled")
     return ap.parse_args()
 
 
@@ -227,7 +229,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctl = mppi.MPPI(arm, cost, dt=DT, T=T, K=K, lam=LAMBDA, sigma=SIGMA, seed=SEED + rank,
-                    stream=stream)
+                    variant=args.variant, stream=stream)
     pose = ctl.ee_pose(q)
     plane = synth.plane_through(float(pose[2]))
     d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, plane), device="cuda")

@@ -121,6 +121,8 @@ typedef struct mppi_config {
   uint64_t seed;    /* Philox key                                            */
   int reduce_fp64;  /* 0: FP32 weight reduction; 1: FP64 accumulators       */
   int use_graph;    /* 1: mppi_step replays a captured CUDA graph            */
+  int variant;      /* rollout kernel: 0 default, 1 links unrolled in registers,
+                       2 link loops rolled through shared memory             */
 } mppi_config;
 
 #define MPPI_T_MAX 256

@@ -162,95 +162,138 @@ struct EEState {
   float v[3];   // end-effector linear velocity
 };
 
+// Recursion state carried from link to link by the forward sweep.
+struct ChainState {
+  float R[9];          // world rotation of the current link frame
+  float p[3];          // world position of the current joint
+  float Vw[3], Vv[3];  // spatial velocity (angular; linear at O)
+  float Aw[3], Av[3];  // spatial bias acceleration
+};
+
+__device__ __forceinline__ void chain_init(const RobotK& rb, ChainState& c) {
+#pragma unroll
+  for (int a = 0; a < 9; ++a) c.R[a] = (a % 4 == 0) ? 1.f : 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    c.p[a] = 0.f;
+    c.Vw[a] = c.Vv[a] = c.Aw[a] = 0.f;
+    c.Av[a] = -rb.g[a];
+  }
+}
+
+// One link of the forward sweep: joint transform, link spatial inertia about
+// O, velocity, bias acceleration and the RNEA link force.
+__device__ __forceinline__ void forward_link(const LinkK& L, float qi, float qdi, ChainState& c,
+                                             LinkState& S) {
+  float d[3];
+  mv3(c.R, L.r, d);
+  c.p[0] += d[0]; c.p[1] += d[1]; c.p[2] += d[2];
+  float RF[9];
+  mm3(c.R, L.F, RF);
+  float s, co;
+  sincosf(qi, &s, &co);
+  // R = RF * Rz(q): columns 0 and 1 rotate, column 2 is the joint axis
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float c0 = RF[3 * r], c1 = RF[3 * r + 1];
+    c.R[3 * r] = fmaf(co, c0, s * c1);
+    c.R[3 * r + 1] = fmaf(co, c1, -s * c0);
+    c.R[3 * r + 2] = RF[3 * r + 2];
+  }
+  const float* R = c.R;
+  const float* p = c.p;
+  S.z[0] = R[2]; S.z[1] = R[5]; S.z[2] = R[8];
+  cross3(p, S.z, S.w);
+
+  // spatial inertia of the link about O
+  float cw[3];
+  mv3(R, L.c, cw);
+  cw[0] += p[0]; cw[1] += p[1]; cw[2] += p[2];
+  // Ibar = R I R^T via T = R I (I symmetric)
+  float Tm[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    Tm[3 * r + 0] = fmaf(R[3 * r], L.I[0], fmaf(R[3 * r + 1], L.I[3], R[3 * r + 2] * L.I[4]));
+    Tm[3 * r + 1] = fmaf(R[3 * r], L.I[3], fmaf(R[3 * r + 1], L.I[1], R[3 * r + 2] * L.I[5]));
+    Tm[3 * r + 2] = fmaf(R[3 * r], L.I[4], fmaf(R[3 * r + 1], L.I[5], R[3 * r + 2] * L.I[2]));
+  }
+  const float m = L.m;
+  const float cc = dot3(cw, cw);
+  float* In = S.In;
+  In[0] = m;
+  In[1] = m * cw[0]; In[2] = m * cw[1]; In[3] = m * cw[2];
+  In[4] = fmaf(Tm[0], R[0], fmaf(Tm[1], R[1], Tm[2] * R[2])) + m * (cc - cw[0] * cw[0]);
+  In[5] = fmaf(Tm[3], R[3], fmaf(Tm[4], R[4], Tm[5] * R[5])) + m * (cc - cw[1] * cw[1]);
+  In[6] = fmaf(Tm[6], R[6], fmaf(Tm[7], R[7], Tm[8] * R[8])) + m * (cc - cw[2] * cw[2]);
+  In[7] = fmaf(Tm[0], R[3], fmaf(Tm[1], R[4], Tm[2] * R[5])) - m * cw[0] * cw[1];
+  In[8] = fmaf(Tm[0], R[6], fmaf(Tm[1], R[7], Tm[2] * R[8])) - m * cw[0] * cw[2];
+  In[9] = fmaf(Tm[3], R[6], fmaf(Tm[4], R[7], Tm[5] * R[8])) - m * cw[1] * cw[2];
+
+  // velocity and bias acceleration
+  const float jw[3] = {S.z[0] * qdi, S.z[1] * qdi, S.z[2] * qdi};
+  const float jv[3] = {S.w[0] * qdi, S.w[1] * qdi, S.w[2] * qdi};
+  float t0[3], t1[3], t2[3];
+  cross3(c.Vw, jw, t0);  // (V x S qd) angular
+  cross3(c.Vw, jv, t1);
+  cross3(c.Vv, jw, t2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    c.Aw[a] += t0[a];
+    c.Av[a] += t1[a] + t2[a];
+    c.Vw[a] += jw[a];
+    c.Vv[a] += jv[a];
+  }
+  // F = I A + V x* (I V)
+  float HA[3], LA[3], HV[3], LV[3];
+  inertia_apply(In, c.Aw, c.Av, HA, LA);
+  inertia_apply(In, c.Vw, c.Vv, HV, LV);
+  float a0[3], a1[3], a2[3];
+  cross3(c.Vw, HV, a0);
+  cross3(c.Vv, LV, a1);
+  cross3(c.Vw, LV, a2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    S.F[a] = HA[a] + a0[a] + a1[a];
+    S.F[3 + a] = LA[a] + a2[a];
+  }
+}
+
+// End-effector pose and linear velocity from the last link's chain state.
+__device__ __forceinline__ void chain_ee(const RobotK& rb, const ChainState& c, EEState& ee) {
+  float de[3];
+  mv3(c.R, rb.ee, de);
+  ee.p[0] = c.p[0] + de[0]; ee.p[1] = c.p[1] + de[1]; ee.p[2] = c.p[2] + de[2];
+  mm3(c.R, rb.Qee, ee.R);
+  float wp[3];
+  cross3(c.Vw, ee.p, wp);
+  ee.v[0] = c.Vv[0] + wp[0]; ee.v[1] = c.Vv[1] + wp[1]; ee.v[2] = c.Vv[2] + wp[2];
+}
+
 // Forward sweep at state (q, qd): kinematics (Fig. 1), RNEA forward
 // recursion with qdd = 0, end-effector pose and velocity.
 __device__ __forceinline__ void forward_sweep(const RobotK& rb, const float q[NJ],
                                               const float qd[NJ], LinkState ls[NJ], EEState& ee) {
-  float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
-  float p[3] = {0.f, 0.f, 0.f};
-  float Vw[3] = {0.f, 0.f, 0.f}, Vv[3] = {0.f, 0.f, 0.f};
-  float Aw[3] = {0.f, 0.f, 0.f}, Av[3] = {-rb.g[0], -rb.g[1], -rb.g[2]};
+  ChainState c;
+  chain_init(rb, c);
 #pragma unroll
-  for (int i = 0; i < NJ; ++i) {
-    const LinkK& L = rb.L[i];
-    float d[3];
-    mv3(R, L.r, d);
-    p[0] += d[0]; p[1] += d[1]; p[2] += d[2];
-    float RF[9];
-    mm3(R, L.F, RF);
-    float s, c;
-    sincosf(q[i], &s, &c);
-    // R = RF * Rz(q): columns 0 and 1 rotate, column 2 is the joint axis
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const float c0 = RF[3 * r], c1 = RF[3 * r + 1];
-      R[3 * r] = fmaf(c, c0, s * c1);
-      R[3 * r + 1] = fmaf(c, c1, -s * c0);
-      R[3 * r + 2] = RF[3 * r + 2];
-    }
-    LinkState& S = ls[i];
-    S.z[0] = R[2]; S.z[1] = R[5]; S.z[2] = R[8];
-    cross3(p, S.z, S.w);
+  for (int i = 0; i < NJ; ++i) forward_link(rb.L[i], q[i], qd[i], c, ls[i]);
+  chain_ee(rb, c, ee);
+}
 
-    // spatial inertia of link i about O
-    float cw[3];
-    mv3(R, L.c, cw);
-    cw[0] += p[0]; cw[1] += p[1]; cw[2] += p[2];
-    // Ibar = R I R^T via T = R I (I symmetric)
-    float Tm[9];
+// One link of the backward sweep: accumulate the suffix force Fs and the
+// composite inertia Ic; return the bias torque h_i and the composite
+// momentum (H, Lm) of S_i, from which M_ji = S_j . (H, Lm) for j <= i.
+__device__ __forceinline__ float backward_link(const LinkK& L, float qdi, const LinkState& S,
+                                               float Fs[6], float Ic[10], float H[3],
+                                               float Lm[3]) {
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      Tm[3 * r + 0] = fmaf(R[3 * r], L.I[0], fmaf(R[3 * r + 1], L.I[3], R[3 * r + 2] * L.I[4]));
-      Tm[3 * r + 1] = fmaf(R[3 * r], L.I[3], fmaf(R[3 * r + 1], L.I[1], R[3 * r + 2] * L.I[5]));
-      Tm[3 * r + 2] = fmaf(R[3 * r], L.I[4], fmaf(R[3 * r + 1], L.I[5], R[3 * r + 2] * L.I[2]));
-    }
-    const float m = L.m;
-    const float cc = dot3(cw, cw);
-    float* In = S.In;
-    In[0] = m;
-    In[1] = m * cw[0]; In[2] = m * cw[1]; In[3] = m * cw[2];
-    In[4] = fmaf(Tm[0], R[0], fmaf(Tm[1], R[1], Tm[2] * R[2])) + m * (cc - cw[0] * cw[0]);
-    In[5] = fmaf(Tm[3], R[3], fmaf(Tm[4], R[4], Tm[5] * R[5])) + m * (cc - cw[1] * cw[1]);
-    In[6] = fmaf(Tm[6], R[6], fmaf(Tm[7], R[7], Tm[8] * R[8])) + m * (cc - cw[2] * cw[2]);
-    In[7] = fmaf(Tm[0], R[3], fmaf(Tm[1], R[4], Tm[2] * R[5])) - m * cw[0] * cw[1];
-    In[8] = fmaf(Tm[0], R[6], fmaf(Tm[1], R[7], Tm[2] * R[8])) - m * cw[0] * cw[2];
-    In[9] = fmaf(Tm[3], R[6], fmaf(Tm[4], R[7], Tm[5] * R[8])) - m * cw[1] * cw[2];
-
-    // velocity and bias acceleration
-    const float jw[3] = {S.z[0] * qd[i], S.z[1] * qd[i], S.z[2] * qd[i]};
-    const float jv[3] = {S.w[0] * qd[i], S.w[1] * qd[i], S.w[2] * qd[i]};
-    float t0[3], t1[3], t2[3];
-    cross3(Vw, jw, t0);  // (V x S qd) angular
-    cross3(Vw, jv, t1);
-    cross3(Vv, jw, t2);
+  for (int a = 0; a < 6; ++a) Fs[a] += S.F[a];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      Aw[a] += t0[a];
-      Av[a] += t1[a] + t2[a];
-      Vw[a] += jw[a];
-      Vv[a] += jv[a];
-    }
-    // F = I A + V x* (I V)
-    float HA[3], LA[3], HV[3], LV[3];
-    inertia_apply(In, Aw, Av, HA, LA);
-    inertia_apply(In, Vw, Vv, HV, LV);
-    float a0[3], a1[3], a2[3];
-    cross3(Vw, HV, a0);
-    cross3(Vv, LV, a1);
-    cross3(Vw, LV, a2);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      S.F[a] = HA[a] + a0[a] + a1[a];
-      S.F[3 + a] = LA[a] + a2[a];
-    }
-  }
-  float de[3];
-  mv3(R, rb.ee, de);
-  ee.p[0] = p[0] + de[0]; ee.p[1] = p[1] + de[1]; ee.p[2] = p[2] + de[2];
-  mm3(R, rb.Qee, ee.R);
-  float wp[3];
-  cross3(Vw, ee.p, wp);
-  ee.v[0] = Vv[0] + wp[0]; ee.v[1] = Vv[1] + wp[1]; ee.v[2] = Vv[2] + wp[2];
+  for (int a = 0; a < 10; ++a) Ic[a] += S.In[a];
+  const float h = fmaf(L.damp, qdi,
+                       dot3(S.z, Fs) + fmaf(S.w[0], Fs[3], fmaf(S.w[1], Fs[4], S.w[2] * Fs[5])));
+  inertia_apply(Ic, S.z, S.w, H, Lm);
+  return h;
 }
 
 // Backward sweep: bias torque h (incl. damping) and the joint-space inertia
@@ -262,15 +305,8 @@ __device__ __forceinline__ void backward_sweep(const RobotK& rb, const float qd[
   float Ic[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = NJ - 1; i >= 0; --i) {
-    const LinkState& S = ls[i];
-#pragma unroll
-    for (int a = 0; a < 6; ++a) Fs[a] += S.F[a];
-#pragma unroll
-    for (int a = 0; a < 10; ++a) Ic[a] += S.In[a];
-    h[i] = fmaf(rb.L[i].damp, qd[i],
-                dot3(S.z, Fs) + fmaf(S.w[0], Fs[3], fmaf(S.w[1], Fs[4], S.w[2] * Fs[5])));
     float H[3], Lm[3];
-    inertia_apply(Ic, S.z, S.w, H, Lm);
+    h[i] = backward_link(rb.L[i], qd[i], ls[i], Fs, Ic, H, Lm);
 #pragma unroll
     for (int j = 0; j <= i; ++j) {
       const LinkState& Sj = ls[j];

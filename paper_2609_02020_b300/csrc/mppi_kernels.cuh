@@ -128,6 +128,211 @@ rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
 }
 
 // ---------------------------------------------------------------------------
+// Rolled variant: the link loops are not unrolled, so one step's code is
+// about a third of the unrolled variant's and stays in the instruction
+// caches.  Per-link results cross from the forward to the backward sweep
+// through shared memory, each thread owning the column `tid` of arrays laid
+// out [row][B] (conflict-free).  Same arithmetic, same order, as
+// rollout_sample.
+
+constexpr int LINK_FIELDS = 22;  // z 3, w 3, F 6, In 10
+constexpr int ROLLED_FLOATS_PER_THREAD = NJ * LINK_FIELDS + NJ * (NJ + 1) / 2 + 3 * NJ;
+
+template <int B>
+__device__ __forceinline__ void store_link(float* sl, int i, int tid, const LinkState& S) {
+  float* b = sl + i * LINK_FIELDS * B + tid;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    b[a * B] = S.z[a];
+    b[(3 + a) * B] = S.w[a];
+  }
+#pragma unroll
+  for (int a = 0; a < 6; ++a) b[(6 + a) * B] = S.F[a];
+#pragma unroll
+  for (int a = 0; a < 10; ++a) b[(12 + a) * B] = S.In[a];
+}
+
+template <int B>
+__device__ __forceinline__ void load_link(const float* sl, int i, int tid, LinkState& S) {
+  const float* b = sl + i * LINK_FIELDS * B + tid;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    S.z[a] = b[a * B];
+    S.w[a] = b[(3 + a) * B];
+  }
+#pragma unroll
+  for (int a = 0; a < 6; ++a) S.F[a] = b[(6 + a) * B];
+#pragma unroll
+  for (int a = 0; a < 10; ++a) S.In[a] = b[(12 + a) * B];
+}
+
+template <int B>
+__device__ __forceinline__ void load_axis(const float* sl, int j, int tid, float z[3], float w[3]) {
+  const float* b = sl + j * LINK_FIELDS * B + tid;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    z[a] = b[a * B];
+    w[a] = b[(3 + a) * B];
+  }
+}
+
+template <int B>
+__device__ __forceinline__ void forward_sweep_rolled(const RobotK& rb, const float* sq,
+                                                     const float* sqd, float* sl, int tid,
+                                                     EEState& ee) {
+  ChainState c;
+  chain_init(rb, c);
+#pragma unroll 1
+  for (int i = 0; i < NJ; ++i) {
+    LinkState S;
+    forward_link(rb.L[i], sq[i * B + tid], sqd[i * B + tid], c, S);
+    store_link<B>(sl, i, tid, S);
+  }
+  chain_ee(rb, c, ee);
+}
+
+// sm: this block's work area of ROLLED_FLOATS_PER_THREAD * B floats.
+template <bool STORE_NOISE, int B>
+__device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const float* in,
+                                                       const float* plan, uint64_t iter, int k,
+                                                       float* __restrict__ noise, float* sm,
+                                                       int tid) {
+  float* sl = sm;                                   // [7][22][B]
+  float* sM = sl + NJ * LINK_FIELDS * B;            // [28][B]
+  float* sq = sM + (NJ * (NJ + 1) / 2) * B;         // [7][B]
+  float* sqd = sq + NJ * B;                         // [7][B]
+  float* sh = sqd + NJ * B;                         // [7][B]
+  const int T = P.T, K = P.K;
+  float q[NJ], qd[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    q[j] = in[j];
+    qd[j] = in[NJ + j];
+    sq[j * B + tid] = q[j];
+    sqd[j * B + tid] = qd[j];
+  }
+  const float pdes[3] = {in[14], in[15], in[16]};
+  float Rd[9];
+  {
+    const float qt[4] = {in[17], in[18], in[19], in[20]};
+    quat_to_R(qt, Rd);
+  }
+  const float plane[4] = {in[21], in[22], in[23], in[24]};
+  const CostK& C = P.cost;
+  const bool contact = C.contact != 0;
+
+  EEState ee;
+  forward_sweep_rolled<B>(P.rb, sq, sqd, sl, tid, ee);
+  float f = contact ? contact_force(C, plane, ee) : 0.f;
+  double Sacc = 0.0;
+
+  for (int t = 0; t < T; ++t) {
+    float z[8];
+    normals8(P.key0, P.key1, iter, static_cast<uint32_t>(k), static_cast<uint32_t>(t), z);
+    float v[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      const float du = P.sigma[j] * z[j];
+      if (STORE_NOISE) noise[static_cast<size_t>(t * NJ + j) * K + k] = du;
+      v[j] = plan[t * NJ + j] + du;
+    }
+    // backward sweep: h and M into shared memory
+    {
+      float Fs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float Ic[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+      for (int ii = 0; ii < NJ; ++ii) {
+        const int i = NJ - 1 - ii;
+        LinkState S;
+        load_link<B>(sl, i, tid, S);
+        float H[3], Lm[3];
+        sh[i * B + tid] = backward_link(P.rb.L[i], sqd[i * B + tid], S, Fs, Ic, H, Lm);
+        const int row = i * (i + 1) / 2;
+#pragma unroll 1
+        for (int j = 0; j < i; ++j) {
+          float zj[3], wj[3];
+          load_axis<B>(sl, j, tid, zj, wj);
+          sM[(row + j) * B + tid] = dot3(zj, H) + dot3(wj, Lm);
+        }
+        sM[(row + i) * B + tid] = dot3(S.z, H) + dot3(S.w, Lm) + P.rb.L[i].arm;
+      }
+    }
+    float M[NJ * (NJ + 1) / 2];
+#pragma unroll
+    for (int a = 0; a < NJ * (NJ + 1) / 2; ++a) M[a] = sM[a * B + tid];
+    float rhs[NJ];
+    if (contact && f > 0.f) {
+      const float Fc[3] = {f * plane[0], f * plane[1], f * plane[2]};
+      float pxF[3];
+      cross3(ee.p, Fc, pxF);
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        float zj[3], wj[3];
+        load_axis<B>(sl, j, tid, zj, wj);
+        rhs[j] = v[j] + dot3(zj, pxF) + dot3(wj, Fc) - sh[j * B + tid];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) rhs[j] = v[j] - sh[j * B + tid];
+    }
+    float qdd[NJ];
+    ldlt_solve(M, rhs, qdd);
+    const float dt = P.dt;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      qd[j] = fmaf(qdd[j], dt, qd[j]);
+      q[j] = fmaf(qd[j], dt, q[j]);
+      sq[j * B + tid] = q[j];
+      sqd[j * B + tid] = qd[j];
+    }
+    forward_sweep_rolled<B>(P.rb, sq, sqd, sl, tid, ee);
+    float cst = motion_cost(C, pdes, Rd, ee);
+    if (contact) {
+      f = contact_force(C, plane, ee);
+      const float e = C.fdes - f;
+      cst += C.wforce * e * e + C.wreg * f * f;
+    }
+    float cj = 0.f;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      cj += C.wqlim * (hinge2(q[j] - P.rb.qmax[j]) + hinge2(P.rb.qmin[j] - q[j]));
+      cj += C.wqdlim * hinge2(fabsf(qd[j]) - P.rb.qdmax[j]);
+      const float e = q[j] - C.qpost[j];
+      cj += C.wpost * e * e;
+      cj += C.wtau * hinge2(fabsf(v[j]) - P.rb.taumax[j]);
+    }
+    Sacc += static_cast<double>(cst) + static_cast<double>(cj);
+  }
+  if (C.wterm != 0.f) Sacc += static_cast<double>(C.wterm * motion_cost(C, pdes, Rd, ee));
+  return static_cast<float>(Sacc);
+}
+
+// Dynamic shared memory of rollout_kernel_rolled for horizon T, block B.
+__host__ __device__ constexpr size_t rolled_smem_bytes(int T, int B) {
+  return sizeof(float) * (static_cast<size_t>((T * NJ + 3) / 4 * 4) + 32 +
+                          static_cast<size_t>(ROLLED_FLOATS_PER_THREAD) * B);
+}
+
+template <bool STORE_NOISE, int B>
+__global__ void __launch_bounds__(B)
+rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__ in,
+                      const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
+                      float* __restrict__ S, float* __restrict__ noise) {
+  extern __shared__ float dsm[];
+  const int T = P.T, K = P.K;
+  float* s_plan = dsm;
+  float* s_in = dsm + (T * NJ + 3) / 4 * 4;
+  float* s_work = s_in + 32;
+  for (int i = threadIdx.x; i < T * NJ; i += B) s_plan[i] = plan[i];
+  if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
+  __syncthreads();
+  const int k = blockIdx.x * B + threadIdx.x;
+  if (k >= K) return;
+  S[k] = rollout_sample_rolled<STORE_NOISE, B>(P, s_in, s_plan, *iter_p, k, noise, s_work,
+                                               threadIdx.x);
+}
+
+// ---------------------------------------------------------------------------
 // block reductions
 
 template <typename V>
@@ -180,8 +385,23 @@ __device__ __forceinline__ double acc_exp(double x) { return exp(x); }
 // Costs that are not finite get weight 0; if none is finite the plan is kept
 // (u* = u, next plan = u) and status 1 is reported.  out (may be null):
 // tau0, status, stats and a copy of the shifted plan (OUT_* offsets).
+// Each block walks K twice (min, then weights and the weighted noise row);
+// when S and the row are 16-byte aligned it reads float4 and keeps four
+// independent accumulators so that the L2 loads overlap.
+constexpr int UPDATE_THREADS = 512;
+
 template <typename Acc>
-__global__ void __launch_bounds__(UPDATE_BLOCK)
+__device__ __forceinline__ void weight_acc(float s, float n, float m, Acc inv_l, Acc& z, Acc& z2,
+                                           Acc& nacc) {
+  const Acc w = isfinite(s) ? acc_exp((static_cast<Acc>(m) - static_cast<Acc>(s)) * inv_l)
+                            : Acc(0);
+  z += w;
+  z2 += w * w;
+  nacc += w * static_cast<Acc>(n);
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(UPDATE_THREADS)
 update_kernel(int K, int T, float lambda, const float* __restrict__ S,
               const float* __restrict__ noise, const float* __restrict__ plan,
               float* __restrict__ ustar, float* __restrict__ plan_next, float* __restrict__ out,
@@ -189,34 +409,60 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
   __shared__ float sm_f[32];
   __shared__ Acc sm_a[3 * 32];
   const int e = blockIdx.x;
+  const float* nrow = noise + static_cast<size_t>(e) * K;
+  const bool vec = (K % 4 == 0) && ((reinterpret_cast<uintptr_t>(S) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(nrow) & 15) == 0);
+  const int K4 = vec ? K / 4 : 0;
   float m = INFINITY;
   int bad = 0;
-  for (int k = threadIdx.x; k < K; k += UPDATE_BLOCK) {
-    const float s = S[k];
-    if (isfinite(s)) m = fminf(m, s);
-    else ++bad;
+  {
+    const float4* S4 = reinterpret_cast<const float4*>(S);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < K4; i += UPDATE_THREADS) {
+      const float4 v = S4[i];
+      const float a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (isfinite(a[c])) m = fminf(m, a[c]);
+        else ++bad;
+      }
+    }
+    for (int k = 4 * K4 + threadIdx.x; k < K; k += UPDATE_THREADS) {
+      const float v = S[k];
+      if (isfinite(v)) m = fminf(m, v);
+      else ++bad;
+    }
   }
-  m = block_min<UPDATE_BLOCK>(m, sm_f);
+  m = block_min<UPDATE_THREADS>(m, sm_f);
   const bool ok = isfinite(m);
   Acc z = Acc(0), z2 = Acc(0), nacc = Acc(0);
   if (ok) {
     const Acc inv_l = Acc(1) / static_cast<Acc>(lambda);
-    const float* nrow = noise + static_cast<size_t>(e) * K;
-    for (int k = threadIdx.x; k < K; k += UPDATE_BLOCK) {
-      const float s = S[k];
-      const Acc w = isfinite(s) ? acc_exp((static_cast<Acc>(m) - static_cast<Acc>(s)) * inv_l)
-                                : Acc(0);
-      z += w;
-      z2 += w * w;
-      nacc += w * static_cast<Acc>(nrow[k]);
+    const float4* S4 = reinterpret_cast<const float4*>(S);
+    const float4* N4 = reinterpret_cast<const float4*>(nrow);
+    Acc za[4] = {Acc(0), Acc(0), Acc(0), Acc(0)}, z2a[4] = {Acc(0), Acc(0), Acc(0), Acc(0)},
+        na[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+#pragma unroll 2
+    for (int i = threadIdx.x; i < K4; i += UPDATE_THREADS) {
+      const float4 sv = S4[i];
+      const float4 nv = N4[i];
+      weight_acc(sv.x, nv.x, m, inv_l, za[0], z2a[0], na[0]);
+      weight_acc(sv.y, nv.y, m, inv_l, za[1], z2a[1], na[1]);
+      weight_acc(sv.z, nv.z, m, inv_l, za[2], z2a[2], na[2]);
+      weight_acc(sv.w, nv.w, m, inv_l, za[3], z2a[3], na[3]);
     }
+    for (int k = 4 * K4 + threadIdx.x; k < K; k += UPDATE_THREADS)
+      weight_acc(S[k], nrow[k], m, inv_l, za[0], z2a[0], na[0]);
+    z = (za[0] + za[1]) + (za[2] + za[3]);
+    z2 = (z2a[0] + z2a[1]) + (z2a[2] + z2a[3]);
+    nacc = (na[0] + na[1]) + (na[2] + na[3]);
   }
-  block_sum3<UPDATE_BLOCK>(z, z2, nacc, sm_a);
+  block_sum3<UPDATE_THREADS>(z, z2, nacc, sm_a);
   Acc nbad = Acc(0), d1 = Acc(0), d2 = Acc(0);
   if (e == 0) {
     nbad = static_cast<Acc>(bad);
     __syncthreads();
-    block_sum3<UPDATE_BLOCK>(nbad, d1, d2, sm_a);
+    block_sum3<UPDATE_THREADS>(nbad, d1, d2, sm_a);
   }
   if (threadIdx.x != 0) return;
   const float u = plan[e];

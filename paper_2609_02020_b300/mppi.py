@@ -83,6 +83,7 @@ class Config(C.Structure):
         ("seed", C.c_uint64),
         ("reduce_fp64", C.c_int),
         ("use_graph", C.c_int),
+        ("variant", C.c_int),
     ]
 
 
@@ -204,7 +205,7 @@ class MPPI:
 
     def __init__(self, robot: dict, cost: dict, *, dt: float, T: int, K: int, lam: float,
                  sigma, seed: int, reduce_fp64: bool = False, use_graph: bool = True,
-                 stream=None):
+                 variant: int = 0, stream=None):
         self.lib = load()
         self.T, self.K = int(T), int(K)
         self._robot = robot_struct(robot)
@@ -220,6 +221,7 @@ class MPPI:
         cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
         cfg.reduce_fp64 = int(bool(reduce_fp64))
         cfg.use_graph = int(bool(use_graph))
+        cfg.variant = int(variant)
         self._cfg = cfg
         h = C.c_void_p()
         sp = C.c_void_p(stream.cuda_stream) if stream is not None else None
