@@ -400,16 +400,25 @@ __device__ __forceinline__ void weight_acc(float s, float n, float m, Acc inv_l,
   nacc += w * static_cast<Acc>(n);
 }
 
+// Result of Eq. 4 for one plan entry, valid in thread 0 of the block.
 template <typename Acc>
-__global__ void __launch_bounds__(UPDATE_THREADS)
-update_kernel(int K, int T, float lambda, const float* __restrict__ S,
-              const float* __restrict__ noise, const float* __restrict__ plan,
-              float* __restrict__ ustar, float* __restrict__ plan_next, float* __restrict__ out,
-              unsigned long long* __restrict__ iter_p) {
+struct EntryResult {
+  float u, us;  // nominal and updated value
+  bool ok;      // some cost was finite
+  float m;      // S_min
+  Acc z, z2;    // sum of weights and of squared weights
+  int bad;      // non-finite costs seen by this thread (block-reduced for e == 0)
+};
+
+// Block-wide Eq. 4a-4b for one entry: plan value u, costs S[K], noise row
+// nrow[K].  Every thread of the block must call it.
+template <typename Acc>
+__device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
+                                                          const float* __restrict__ S,
+                                                          const float* __restrict__ nrow,
+                                                          float u, bool count_bad) {
   __shared__ float sm_f[32];
   __shared__ Acc sm_a[3 * 32];
-  const int e = blockIdx.x;
-  const float* nrow = noise + static_cast<size_t>(e) * K;
   const bool vec = (K % 4 == 0) && ((reinterpret_cast<uintptr_t>(S) & 15) == 0) &&
                    ((reinterpret_cast<uintptr_t>(nrow) & 15) == 0);
   const int K4 = vec ? K / 4 : 0;
@@ -459,17 +468,36 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
   }
   block_sum3<UPDATE_THREADS>(z, z2, nacc, sm_a);
   Acc nbad = Acc(0), d1 = Acc(0), d2 = Acc(0);
-  if (e == 0) {
+  if (count_bad) {
     nbad = static_cast<Acc>(bad);
     __syncthreads();
     block_sum3<UPDATE_THREADS>(nbad, d1, d2, sm_a);
   }
+  __syncthreads();  // shared scratch may be reused by the caller's next entry
+  EntryResult<Acc> r;
+  r.u = u;
+  r.ok = ok;
+  r.m = m;
+  r.z = z;
+  r.z2 = z2;
+  r.bad = static_cast<int>(nbad);
+  r.us = ok ? static_cast<float>(static_cast<Acc>(u) + nacc / z) : u;
+  return r;
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(UPDATE_THREADS)
+update_kernel(int K, int T, float lambda, const float* __restrict__ S,
+              const float* __restrict__ noise, const float* __restrict__ plan,
+              float* __restrict__ ustar, float* __restrict__ plan_next, float* __restrict__ out,
+              unsigned long long* __restrict__ iter_p) {
+  const int e = blockIdx.x;
+  const float* nrow = noise + static_cast<size_t>(e) * K;
+  const EntryResult<Acc> r = update_entry<Acc>(K, lambda, S, nrow, plan[e], e == 0);
   if (threadIdx.x != 0) return;
-  const float u = plan[e];
   const int t = e / NJ;
-  float us;
-  if (ok) {
-    us = static_cast<float>(static_cast<Acc>(u) + nacc / z);
+  const float us = r.us;
+  if (r.ok) {
     if (t >= 1) plan_next[e - NJ] = us;
     if (t == T - 1) plan_next[e] = us;
     if (out) {
@@ -477,21 +505,20 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
       if (t == T - 1) out[OUT_PLAN + e] = us;
     }
   } else {
-    us = u;
-    plan_next[e] = u;
-    if (out) out[OUT_PLAN + e] = u;
+    plan_next[e] = us;
+    if (out) out[OUT_PLAN + e] = us;
   }
   ustar[e] = us;
   if (out && e < NJ) out[OUT_TAU0 + e] = us;
   if (e == 0) {
     if (out) {
-      reinterpret_cast<int*>(out)[OUT_STATUS] = ok ? 0 : 1;
-      out[OUT_STATS + 0] = m;
-      out[OUT_STATS + 1] = static_cast<float>(z);
-      out[OUT_STATS + 2] = ok ? static_cast<float>(z * z / z2) : 0.f;
-      out[OUT_STATS + 3] = static_cast<float>(nbad);
+      reinterpret_cast<int*>(out)[OUT_STATUS] = r.ok ? 0 : 1;
+      out[OUT_STATS + 0] = r.m;
+      out[OUT_STATS + 1] = static_cast<float>(r.z);
+      out[OUT_STATS + 2] = r.ok ? static_cast<float>(r.z * r.z / r.z2) : 0.f;
+      out[OUT_STATS + 3] = static_cast<float>(r.bad);
     }
-    if (iter_p && ok) *iter_p += 1ull;
+    if (iter_p && r.ok) *iter_p += 1ull;
   }
 }
 

@@ -87,13 +87,31 @@ class Config(C.Structure):
     ]
 
 
-# every symbol include/mppi.h declares
+class ServerConfig(C.Structure):
+    _fields_ = [
+        ("pool_bytes", C.c_size_t),
+        ("max_problems", C.c_int),
+        ("max_batch", C.c_int),
+        ("lanes", C.c_int),
+        ("variant", C.c_int),
+        ("rollout_block", C.c_int),
+    ]
+
+
+# every symbol include/*.h declares
 EXPORTS = [
     "mppi_create", "mppi_destroy", "mppi_step", "mppi_step_device", "mppi_sync",
     "mppi_get_costs", "mppi_get_noise", "mppi_get_updated_plan", "mppi_get_stats",
     "mppi_set_plan", "mppi_get_plan", "mppi_set_iter", "mppi_get_iter",
     "mppi_rollout_device", "mppi_update_device", "mppi_ee_pose", "mppi_time_kernels",
     "mppi_noise_words", "mppi_step_static", "mppi_last_error", "mppi_version",
+    # include/mppi_serve.h
+    "mppi_pool_create", "mppi_pool_destroy", "mppi_pool_alloc", "mppi_pool_free",
+    "mppi_pool_stats", "mppi_server_create", "mppi_server_destroy", "mppi_server_add_problem",
+    "mppi_server_set_plan", "mppi_server_get_plan", "mppi_server_get_iter", "mppi_server_submit",
+    "mppi_server_poll", "mppi_server_wait", "mppi_server_start", "mppi_server_stop",
+    "mppi_server_tick", "mppi_server_drain", "mppi_server_autotune", "mppi_server_stats",
+    "mppi_server_set_input", "mppi_server_load_test",
 ]
 
 _lib = None
@@ -135,6 +153,29 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                               vp, vp, vp, vp, vp], C.c_int),
         "mppi_last_error": ([H], C.c_char_p),
         "mppi_version": ([], C.c_char_p),
+        "mppi_pool_create": ([C.c_size_t, C.POINTER(C.c_void_p)], C.c_int),
+        "mppi_pool_destroy": ([H], C.c_int),
+        "mppi_pool_alloc": ([H, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
+        "mppi_pool_free": ([H, C.c_size_t], C.c_int),
+        "mppi_pool_stats": ([H, C.POINTER(C.c_size_t)], C.c_int),
+        "mppi_server_create": ([C.POINTER(ServerConfig), C.POINTER(C.c_void_p)], C.c_int),
+        "mppi_server_destroy": ([H], C.c_int),
+        "mppi_server_add_problem": ([H, C.POINTER(Robot), C.POINTER(Cost), C.POINTER(Config),
+                                     C.POINTER(C.c_int)], C.c_int),
+        "mppi_server_set_plan": ([H, C.c_int, fp], C.c_int),
+        "mppi_server_get_plan": ([H, C.c_int, fp], C.c_int),
+        "mppi_server_get_iter": ([H, C.c_int, C.POINTER(C.c_uint64)], C.c_int),
+        "mppi_server_submit": ([H, C.c_int, fp, C.POINTER(C.c_uint64)], C.c_int),
+        "mppi_server_poll": ([H, C.c_uint64, fp, C.POINTER(C.c_int)], C.c_int),
+        "mppi_server_wait": ([H, C.c_uint64, fp], C.c_int),
+        "mppi_server_start": ([H], C.c_int),
+        "mppi_server_stop": ([H], C.c_int),
+        "mppi_server_tick": ([H, C.POINTER(C.c_int)], C.c_int),
+        "mppi_server_drain": ([H], C.c_int),
+        "mppi_server_autotune": ([H, C.POINTER(C.c_float)], C.c_int),
+        "mppi_server_stats": ([H, dp], C.c_int),
+        "mppi_server_set_input": ([H, C.c_int, fp], C.c_int),
+        "mppi_server_load_test": ([H, C.c_double, C.c_double, C.c_uint64, dp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -375,3 +416,174 @@ def pack_inputs(q, qd, goal, plane=None) -> np.ndarray:
 
 def version() -> str:
     return load().mppi_version().decode()
+
+
+def _config(dt, T, K, lam, sigma, seed, reduce_fp64=False, use_graph=True, variant=0) -> Config:
+    cfg = Config()
+    cfg.dt, cfg.T, cfg.K, cfg.lambda_ = float(dt), int(T), int(K), float(lam)
+    s = np.broadcast_to(np.asarray(sigma, dtype=np.float64), (NJ,))
+    for j in range(NJ):
+        cfg.sigma[j] = float(s[j])
+    cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    cfg.reduce_fp64 = int(bool(reduce_fp64))
+    cfg.use_graph = int(bool(use_graph))
+    cfg.variant = int(variant)
+    return cfg
+
+
+class Pool:
+    """Host-side first-fit pool bookkeeping of include/mppi_serve.h."""
+
+    def __init__(self, nbytes: int):
+        self.lib = load()
+        h = C.c_void_p()
+        rc = self.lib.mppi_pool_create(int(nbytes), C.byref(h))
+        if rc != OK:
+            raise MPPIError(rc, "mppi_pool_create failed")
+        self.h = h
+
+    def alloc(self, nbytes: int):
+        """Offset, or None when nothing fits."""
+        off = C.c_size_t()
+        rc = self.lib.mppi_pool_alloc(self.h, int(nbytes), C.byref(off))
+        if rc == ERR_OOM:
+            return None
+        if rc != OK:
+            raise MPPIError(rc, "mppi_pool_alloc failed")
+        return int(off.value)
+
+    def free(self, off: int) -> int:
+        return self.lib.mppi_pool_free(self.h, int(off))
+
+    def stats(self):
+        out = (C.c_size_t * 4)()
+        self.lib.mppi_pool_stats(self.h, out)
+        return dict(size=out[0], used=out[1], peak=out[2], largest_free=out[3])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mppi_pool_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Batched MPPI server (include/mppi_serve.h)."""
+
+    def __init__(self, *, pool_bytes: int = 1 << 30, max_problems: int = 256,
+                 max_batch: int = 256, lanes: int = 2, variant: int = 0, rollout_block: int = 0):
+        self.lib = load()
+        cfg = ServerConfig()
+        cfg.pool_bytes, cfg.max_problems, cfg.max_batch = int(pool_bytes), int(max_problems), int(max_batch)
+        cfg.lanes, cfg.variant, cfg.rollout_block = int(lanes), int(variant), int(rollout_block)
+        h = C.c_void_p()
+        rc = self.lib.mppi_server_create(C.byref(cfg), C.byref(h))
+        if rc != OK:
+            raise MPPIError(rc, self.lib.mppi_last_error(None).decode())
+        self.h = h
+        self.T = {}
+
+    def _check(self, rc):
+        if rc != OK:
+            raise MPPIError(rc, self.lib.mppi_last_error(None).decode())
+        return rc
+
+    def add_problem(self, robot: dict, cost: dict, *, dt, T, K, lam, sigma, seed) -> int:
+        i = C.c_int()
+        rb, cs = robot_struct(robot), cost_struct(cost)
+        cfg = _config(dt, T, K, lam, sigma, seed)
+        self._check(self.lib.mppi_server_add_problem(self.h, C.byref(rb), C.byref(cs), C.byref(cfg),
+                                                     C.byref(i)))
+        self.T[i.value] = int(T)
+        return i.value
+
+    def set_plan(self, pid: int, u):
+        self._check(self.lib.mppi_server_set_plan(self.h, pid, _fp(_f32(u, self.T[pid] * NJ))))
+
+    def get_plan(self, pid: int) -> np.ndarray:
+        u = np.zeros((self.T[pid], NJ), dtype=np.float32)
+        self._check(self.lib.mppi_server_get_plan(self.h, pid, _fp(u)))
+        return u
+
+    def get_iter(self, pid: int) -> int:
+        v = C.c_uint64()
+        self._check(self.lib.mppi_server_get_iter(self.h, pid, C.byref(v)))
+        return int(v.value)
+
+    def set_input(self, pid: int, inp):
+        self._check(self.lib.mppi_server_set_input(self.h, pid, _fp(_f32(inp, IN_FLOATS))))
+
+    def submit(self, pid: int, inp) -> int:
+        t = C.c_uint64()
+        self._check(self.lib.mppi_server_submit(self.h, pid, _fp(_f32(inp, IN_FLOATS)), C.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """(done, status, tau0)"""
+        tau0 = np.zeros(NJ, dtype=np.float32)
+        d = C.c_int()
+        rc = self.lib.mppi_server_poll(self.h, int(ticket), _fp(tau0), C.byref(d))
+        if rc not in (OK, ERR_NONFINITE):
+            self._check(rc)
+        return bool(d.value), rc, tau0
+
+    def wait(self, ticket: int):
+        """(status, tau0)"""
+        tau0 = np.zeros(NJ, dtype=np.float32)
+        rc = self.lib.mppi_server_wait(self.h, int(ticket), _fp(tau0))
+        if rc not in (OK, ERR_NONFINITE):
+            self._check(rc)
+        return rc, tau0
+
+    def start(self):
+        self._check(self.lib.mppi_server_start(self.h))
+
+    def stop(self):
+        self._check(self.lib.mppi_server_stop(self.h))
+
+    def tick(self) -> int:
+        n = C.c_int()
+        self._check(self.lib.mppi_server_tick(self.h, C.byref(n)))
+        return n.value
+
+    def drain(self):
+        self._check(self.lib.mppi_server_drain(self.h))
+
+    def autotune(self) -> float:
+        ms = C.c_float()
+        self._check(self.lib.mppi_server_autotune(self.h, C.byref(ms)))
+        return ms.value
+
+    def stats(self) -> dict:
+        o = (C.c_double * 8)()
+        self._check(self.lib.mppi_server_stats(self.h, o))
+        return dict(completed=o[0], ticks=o[1], mean_batch=o[2], pool_peak=o[3], pool_size=o[4],
+                    variant=int(o[5]), block=int(o[6]), rollout_steps=o[7])
+
+    def load_test(self, rate_hz: float, seconds: float, seed: int = 1) -> dict:
+        o = (C.c_double * 8)()
+        self._check(self.lib.mppi_server_load_test(self.h, float(rate_hz), float(seconds), int(seed), o))
+        return dict(completed=o[0], p50_ms=o[1], p99_ms=o[2], mean_ms=o[3], updates_per_s=o[4],
+                    rollout_steps_per_s=o[5], mean_batch=o[6], max_queue=o[7])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mppi_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

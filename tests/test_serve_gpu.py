@@ -1,0 +1,174 @@
+"""Batched serving (include/mppi_serve.h) on the GPU.
+
+The central check: every request's result is the same alone (single-problem
+handle, mppi_step) and in a mixed tick of problems with uneven K and T, within
+the plan tolerance of the parity tests (1e-5 N m).  Also: parity of a served
+problem with the FP64 oracle, memory-based admission with a pool that holds
+only a few requests, in-order service of several requests of one problem,
+continuous batching with the scheduler thread, non-finite updates, the
+autotuner and the native Poisson load test.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2609_02020_b300 import mppi, synth
+from _common import gpu_controller, make_case, oracle_step, parity_cost
+
+pytestmark = pytest.mark.gpu
+
+PLAN_TOL = 1e-5
+
+
+def mix(n, seed=7, k_range=(512, 8192), t_range=(10, 50)):
+    Ks, Ts = synth.serving_mix(seed, n, k_range, t_range)
+    out = []
+    for i in range(n):
+        c = make_case(100 + i, contact=(i % 2 == 1), K=int(Ks[i]), T=int(Ts[i]))
+        c["seed"] = 0xBEEF + i
+        out.append(c)
+    return out
+
+
+def register(srv, cases):
+    return [srv.add_problem(c["arm"], c["cost"], dt=c["dt"], T=c["T"], K=c["K"], lam=c["lam"],
+                            sigma=c["sigma"], seed=c["seed"]) for c in cases]
+
+
+def inputs(c, qd=None):
+    return mppi.pack_inputs(c["q"], c["qd"] if qd is None else qd, c["goal"], c["plane"])
+
+
+def alone(c, variant, steps=1):
+    with gpu_controller(c, variant=variant) as g:
+        outs = [g.step(c["q"], c["qd"], c["goal"], c["plane"]) for _ in range(steps)]
+        return outs[-1][0], g.get_plan(), g.get_iter()
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_each_result_same_alone_and_in_the_mix(variant):
+    cases = mix(12)
+    with mppi.Server(pool_bytes=1 << 30, max_problems=32, max_batch=32, lanes=2,
+                     variant=variant, rollout_block=64) as srv:
+        ids = register(srv, cases)
+        tickets = [srv.submit(i, inputs(c)) for i, c in zip(ids, cases)]
+        res = [srv.wait(t) for t in tickets]
+        plans = [srv.get_plan(i) for i in ids]
+        st = srv.stats()
+        assert st["ticks"] == 1 and st["completed"] == len(cases)
+    for c, (rc, tau0), plan in zip(cases, res, plans):
+        assert rc == mppi.OK
+        t_ref, p_ref, it = alone(c, variant)
+        assert it == 1
+        assert np.abs(tau0 - t_ref).max() <= PLAN_TOL
+        assert np.abs(plan - p_ref).max() <= PLAN_TOL
+
+
+def test_served_problem_matches_oracle():
+    cases = [make_case(s, cost=parity_cost(), K=K, T=T) for s, K, T in
+             [(0, 700, 18), (1, 256, 9), (2, 1500, 25)]]
+    with mppi.Server(pool_bytes=256 << 20, max_problems=8, max_batch=8, lanes=1, variant=2,
+                     rollout_block=32) as srv:
+        ids = register(srv, cases)
+        res = [srv.wait(srv.submit(i, inputs(c))) for i, c in zip(ids, cases)]
+        plans = [srv.get_plan(i) for i in ids]
+    for c, (rc, tau0), plan in zip(cases, res, plans):
+        o = oracle_step(c, want_noise=False)
+        assert rc == mppi.OK
+        assert np.abs(tau0 - o["ustar"][0]).max() <= PLAN_TOL
+        assert np.abs(plan - o["plan_next"]).max() <= PLAN_TOL
+
+
+def test_memory_admission_with_a_small_pool():
+    cases = mix(10, seed=3, k_range=(2048, 4096), t_range=(20, 30))
+    need = [4 * c["K"] * (7 * c["T"] + 1) for c in cases]
+    pool = int(2.5 * max(need)) + (1 << 20)
+    with mppi.Server(pool_bytes=pool, max_problems=16, max_batch=16, lanes=2, variant=2,
+                     rollout_block=32) as srv:
+        ids = register(srv, cases)
+        tickets = [srv.submit(i, inputs(c)) for i, c in zip(ids, cases)]
+        res = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    assert all(rc == mppi.OK for rc, _ in res)
+    assert st["pool_peak"] <= st["pool_size"]
+    # every tick's scratch fits in the pool, so the ten requests need at least
+    # ceil(total scratch / pool) ticks
+    assert st["ticks"] >= int(np.ceil(sum(need) / st["pool_size"]))
+    assert st["ticks"] >= 3
+    for c, (rc, tau0) in zip(cases[:3], res[:3]):
+        assert np.abs(tau0 - alone(c, 2)[0]).max() <= PLAN_TOL
+
+
+def test_requests_of_one_problem_run_in_order():
+    c = mix(1, seed=5, k_range=(1000, 1000), t_range=(15, 15))[0]
+    with mppi.Server(pool_bytes=256 << 20, max_problems=4, max_batch=4, lanes=2, variant=2,
+                     rollout_block=32) as srv:
+        (pid,) = register(srv, [c])
+        tickets = [srv.submit(pid, inputs(c)) for _ in range(3)]
+        res = [srv.wait(t) for t in tickets]
+        plan, it = srv.get_plan(pid), srv.get_iter(pid)
+        assert srv.stats()["ticks"] == 3
+    t_ref, p_ref, it_ref = alone(c, 2, steps=3)
+    assert it == it_ref == 3
+    assert np.abs(res[-1][1] - t_ref).max() <= PLAN_TOL
+    assert np.abs(plan - p_ref).max() <= PLAN_TOL
+
+
+def test_continuous_batching_with_the_scheduler_thread():
+    cases = mix(16, seed=11, k_range=(512, 4096), t_range=(10, 30))
+    with mppi.Server(pool_bytes=1 << 30, max_problems=32, max_batch=32, lanes=3, variant=2,
+                     rollout_block=32) as srv:
+        ids = register(srv, cases)
+        srv.start()
+        tickets = []
+        for r in range(3):  # three waves; later waves arrive while earlier ticks run
+            for i, c in zip(ids, cases):
+                tickets.append((i, srv.submit(i, inputs(c))))
+                time.sleep(0.0002)
+        res = {t: srv.wait(t) for _, t in tickets}
+        srv.drain()
+        srv.stop()
+        st = srv.stats()
+        plans = [srv.get_plan(i) for i in ids]
+        iters = [srv.get_iter(i) for i in ids]
+    assert st["completed"] == 48 and all(it == 3 for it in iters)
+    assert st["ticks"] >= 3
+    for c, plan in zip(cases[:4], plans[:4]):
+        _, p_ref, _ = alone(c, 2, steps=3)
+        assert np.abs(plan - p_ref).max() <= PLAN_TOL
+    assert all(rc == mppi.OK for rc, _ in res.values())
+
+
+def test_nonfinite_request_keeps_its_plan_and_spares_the_others():
+    cases = mix(4, seed=2, k_range=(600, 900), t_range=(8, 12))
+    with mppi.Server(pool_bytes=256 << 20, max_problems=8, max_batch=8, lanes=1, variant=2,
+                     rollout_block=32) as srv:
+        ids = register(srv, cases)
+        p0 = np.random.default_rng(0).normal(0, 1, (cases[1]["T"], 7)).astype(np.float32)
+        srv.set_plan(ids[1], p0)
+        bad = np.full(7, 1e18, np.float32)
+        tk = [srv.submit(i, inputs(c, qd=bad if i == ids[1] else None)) for i, c in zip(ids, cases)]
+        res = [srv.wait(t) for t in tk]
+        assert res[1][0] == mppi.ERR_NONFINITE
+        assert np.array_equal(srv.get_plan(ids[1]), p0) and srv.get_iter(ids[1]) == 0
+        for j in (0, 2, 3):
+            assert res[j][0] == mppi.OK
+            assert np.abs(res[j][1] - alone(cases[j], 2)[0]).max() <= PLAN_TOL
+
+
+def test_autotune_and_poisson_load():
+    cases = mix(32, seed=13, k_range=(512, 2048), t_range=(10, 20))
+    with mppi.Server(pool_bytes=1 << 30, max_problems=64, max_batch=64, lanes=2) as srv:
+        ids = register(srv, cases)
+        for i, c in zip(ids, cases):
+            srv.set_input(i, inputs(c))
+        best = srv.autotune()
+        st = srv.stats()
+        assert best > 0 and st["variant"] in (1, 2) and st["block"] in (32, 64, 128)
+        srv.start()
+        r = srv.load_test(2000.0, 0.3, seed=4)
+        srv.stop()
+    assert r["completed"] > 200
+    assert 0 < r["p50_ms"] <= r["p99_ms"]
+    assert r["mean_batch"] >= 1.0
