@@ -61,6 +61,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", type=int, default=0,
                     help="rollout kernel: 0 library default, 1 unrolled, 2 rolled")
+    ap.add_argument("--mode", default="update", choices=["update", "serve"],
+                    help="update: the headline single-update benchmark; serve: batched "
+                         "serving of 256 problems under Poisson load")
+    ap.add_argument("--rates", default="2000,5000,10000,20000,100000",
+                    help="serve mode: arrival rates [updates/s]")
+    ap.add_argument("--seconds", type=float, default=2.0, help="serve mode: seconds per rate")
+    ap.add_argument("--problems", type=int, default=256, help="serve mode: problems")
+    ap.add_argument("--pool-mb", type=int, default=1024, help="serve mode: scratch pool [MiB]")
     return ap.parse_args()
 
 
@@ -339,6 +347,51 @@ def run_ours(args, rank, world):
 
 
 
+def run_serve(args, rank, world):
+    """Batched serving: many problems with uneven K and T, Poisson arrivals,
+    memory-based admission, continuous batching (include/mppi_serve.h)."""
+    import torch
+    from paper_2609_02020_b300 import mppi, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n = args.problems
+    Ks, Ts = synth.serving_mix(17 + rank, n)
+    srv = mppi.Server(pool_bytes=args.pool_mb << 20, max_problems=n, max_batch=min(n, 1024),
+                      lanes=3)
+    total_scratch = 0
+    for i in range(n):
+        arm = synth.arm(10_000 * rank + i)
+        q, qd = synth.state(20_000 + i, arm)
+        goal = synth.goal(20_000 + i, arm)
+        cost = synth.cost_contact() if i % 2 else synth.cost_free_space()
+        pid = srv.add_problem(arm, cost, dt=DT, T=int(Ts[i]), K=int(Ks[i]), lam=LAMBDA,
+                              sigma=SIGMA, seed=SEED + i)
+        plane = synth.NO_PLANE
+        srv.set_input(pid, mppi.pack_inputs(q, qd, goal, plane if not cost["contact"] else
+                                            np.array([0.0, 0.0, 1.0, -10.0])))
+        total_scratch += 4 * int(Ks[i]) * (7 * int(Ts[i]) + 1)
+    best = srv.autotune()
+    st = srv.stats()
+    srv.start()
+    points = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        r = srv.load_test(rate, args.seconds, seed=int(rate))
+        points.append({"rate_hz": rate, **{k: float(v) for k, v in r.items()}})
+    srv.stop()
+    srv.close()
+    if rank == 0:
+        print(json.dumps({
+            "mode": "serve",
+            "metric": "batched MPPI serving: update latency p50/p99 and throughput under Poisson load",
+            "unit": "ms / updates/s / rollout-steps/s", "n_gpus": world, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{n} seeded 7-DoF problems, K~U{{512..8192}}, T~U{{10..50}}, "
+                                   f"dt={DT} s, half with plane contact",
+                       "pool_mib": args.pool_mb, "all_scratch_mib": total_scratch / 2**20,
+                       "lanes": 3, "seconds_per_rate": args.seconds},
+            "autotune": {"variant": st["variant"], "tile": st["block"], "rollout_ms": best},
+            "points": points}), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -353,6 +406,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
+        elif args.mode == "serve":
+            run_serve(args, rank, world)
         else:
             run_ours(args, rank, world)
     finally:
