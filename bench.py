@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--K", type=int, default=K_DEFAULT)
     ap.add_argument("--T", type=int, default=T_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--budget-s", type=float, default=120.0,
+                    help="reference arm: wall-clock budget of the whole run [s]")
     ap.add_argument("--variant", type=int, default=0,
                     help="rollout kernel: 0 library default, 1 unrolled, 2 rolled")
     ap.add_argument("--mode", default="update", choices=["update", "serve"],
@@ -70,6 +72,18 @@ def parse():
     ap.add_argument("--problems", type=int, default=256, help="serve mode: problems")
     ap.add_argument("--pool-mb", type=int, default=1024, help="serve mode: scratch pool [MiB]")
     return ap.parse_args()
+
+
+def max_over_ranks(values, world: int, device: str):
+    """Element-wise maximum of `values` over all ranks (the slowest rank's
+    times); the identity for a single rank."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
 
 
 def workload(rank: int):
@@ -189,12 +203,12 @@ def run_reference(args, rank, world):
     plane = synth.plane_through(oracle.fk(rb, q)[3][2])
     nth = min(os.cpu_count() or 1, oracle.max_threads())
     plan = np.zeros((T, 7))
-    # size each step's sample so the whole run takes about two minutes
+    # size each step's sample so the whole run takes about --budget-s seconds
     t0 = time.perf_counter()
     oracle.mppi_step(rb, oc, DT, T, 512, LAMBDA, np.full(7, SIGMA), SEED, 0, q, qd, goal, plane,
                      plan, nthreads=nth)
     per_sample = (time.perf_counter() - t0) / 512
-    budget = 120.0 / max(1, args.steps + args.warmup)
+    budget = args.budget_s / max(1, args.steps + args.warmup)
     K_sample = int(max(64, min(K, budget / per_sample)))
     for w in range(args.warmup):
         oracle.mppi_step(rb, oc, DT, T, K_sample, LAMBDA, np.full(7, SIGMA), SEED, w, q, qd, goal,
@@ -298,12 +312,8 @@ def run_ours(args, rank, world):
     e2e_ms = np.array(e2e_ms)
 
     # --- aggregate over ranks -------------------------------------------------
-    total_ms = float(step_ms.sum())
-    e2e_total = float(e2e_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms, e2e_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, e2e_total = float(t[0]), float(t[1])
+    total_ms, e2e_total = max_over_ranks([float(step_ms.sum()), float(e2e_ms.sum())], world,
+                                         "cuda")
     units = K * T * args.steps * world
     value = units / (total_ms * 1e-3)
     e2e_value = units / (e2e_total * 1e-3)

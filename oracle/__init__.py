@@ -17,6 +17,7 @@ What each wrapped function follows in the paper:
   stage_cost .............. Eq. 9-12, 14
   rollout ................. Eq. 1-3, 5-7
   mppi_update ............. Eq. 4a-4b and the warm-start shift
+  mppi_partial / merge .... Eq. 4 over K split into shards (log-sum-exp merge)
   mppi_step ............... the full update
 """
 from __future__ import annotations
@@ -143,6 +144,9 @@ def _declare(L):
                                 C.c_int, _dp, _dp, _dp, _dp, _dp]
     L.orc_mppi_step.restype = C.c_int
     L.orc_max_threads.restype = C.c_int
+    L.orc_mppi_partial.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_double, _dp]
+    L.orc_mppi_merge.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_double, _dp, _dp]
+    L.orc_mppi_merge.restype = C.c_int
 
 
 def _arr(x, n=None):
@@ -401,6 +405,28 @@ def mppi_step(robot: Robot, cost: Cost, dt, T, K, lam, sigma, seed, it, q0, qd0,
     if want_noise:
         out["noise"] = noise
     return out
+
+
+def mppi_partial(S, noise, lam):
+    """One shard's (m, Z, N[T*n]) of the sharded Eq. 4 (noise [K, T, n])."""
+    S = _arr(S)
+    noise = _arr(noise)
+    K, T, n = noise.shape
+    part = np.zeros(2 + T * n)
+    lib().orc_mppi_partial(K, T, n, _p(S), _p(noise), float(lam), _p(part))
+    return part
+
+
+def mppi_merge(parts, plan, lam):
+    """Merge of G shard partials [G, 2 + T*n] -> (rc, ustar, plan_next)."""
+    parts = _arr(parts)
+    plan = _arr(plan)
+    T, n = plan.shape
+    G = parts.shape[0]
+    ustar = np.zeros((T, n))
+    nxt = np.zeros((T, n))
+    rc = lib().orc_mppi_merge(G, T, n, _p(parts), _p(plan), float(lam), _p(ustar), _p(nxt))
+    return rc, ustar, nxt
 
 
 def max_threads() -> int:

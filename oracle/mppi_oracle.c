@@ -807,3 +807,57 @@ int orc_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sharded update (the exchange step if the K samples were split over G     */
+/* devices): each shard g reduces its own samples to (m_g, Z_g, N_g) with     */
+/* m_g = min S, Z_g = sum exp(-(S - m_g)/lambda), N_g = sum exp(...) dtau     */
+/* (T*n entries); the merge rescales by exp(-(m_g - m)/lambda), m = min m_g,  */
+/* which is exactly Eq. 4 over all samples.                                   */
+
+/* part: 2 + T*n doubles (m, Z, N[T*n]).  noise: [k][t][j] for this shard. */
+void orc_mppi_partial(int K, int T, int n, const double* S, const double* noise, double lambda,
+                      double* part) {
+  double m = INFINITY;
+  for (int k = 0; k < K; k++)
+    if (isfinite(S[k]) && S[k] < m) m = S[k];
+  part[0] = m;
+  part[1] = 0.0;
+  for (int i = 0; i < T * n; i++) part[2 + i] = 0.0;
+  if (!isfinite(m)) return;
+  for (int k = 0; k < K; k++) {
+    if (!isfinite(S[k])) continue;
+    double w = exp(-(S[k] - m) / lambda);
+    part[1] += w;
+    for (int i = 0; i < T * n; i++) part[2 + i] += w * noise[(size_t)k * T * n + i];
+  }
+}
+
+/* Merges G partials (G x (2 + T*n)) into u* and the shifted plan; returns 1
+ * (plan kept) when no shard had a finite cost. */
+int orc_mppi_merge(int G, int T, int n, const double* parts, const double* plan, double lambda,
+                   double* ustar, double* plan_next) {
+  const int stride = 2 + T * n;
+  double m = INFINITY;
+  for (int g = 0; g < G; g++)
+    if (parts[g * stride] < m) m = parts[g * stride];
+  if (!isfinite(m)) {
+    for (int i = 0; i < T * n; i++) ustar[i] = plan_next[i] = plan[i];
+    return 1;
+  }
+  double Z = 0.0;
+  for (int g = 0; g < G; g++)
+    if (isfinite(parts[g * stride])) Z += parts[g * stride + 1] * exp(-(parts[g * stride] - m) / lambda);
+  for (int i = 0; i < T * n; i++) {
+    double N = 0.0;
+    for (int g = 0; g < G; g++)
+      if (isfinite(parts[g * stride]))
+        N += parts[g * stride + 2 + i] * exp(-(parts[g * stride] - m) / lambda);
+    ustar[i] = plan[i] + N / Z;
+  }
+  for (int t = 0; t < T; t++) {
+    int src = (t + 1 < T) ? t + 1 : T - 1;
+    for (int j = 0; j < n; j++) plan_next[t * n + j] = ustar[src * n + j];
+  }
+  return 0;
+}
