@@ -18,6 +18,8 @@ What each wrapped function follows in the paper:
   rollout ................. Eq. 1-3, 5-7
   mppi_update ............. Eq. 4a-4b and the warm-start shift
   mppi_partial / merge .... Eq. 4 over K split into shards (log-sum-exp merge)
+  mlp_forward / loss_grad . the learned proposal network (no paper equation:
+                            an MLP and its backpropagation, from the definitions)
   mppi_step ............... the full update
 """
 from __future__ import annotations
@@ -147,6 +149,10 @@ def _declare(L):
     L.orc_mppi_partial.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_double, _dp]
     L.orc_mppi_merge.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_double, _dp, _dp]
     L.orc_mppi_merge.restype = C.c_int
+    ip = C.POINTER(C.c_int)
+    L.orc_mlp_forward.argtypes = [C.c_int, ip, _dp, C.c_int, _dp, C.c_int, _dp, _dp]
+    L.orc_mlp_loss_grad.argtypes = [C.c_int, ip, _dp, C.c_int, _dp, _dp, C.c_int, _dp]
+    L.orc_mlp_loss_grad.restype = C.c_double
 
 
 def _arr(x, n=None):
@@ -427,6 +433,37 @@ def mppi_merge(parts, plan, lam):
     nxt = np.zeros((T, n))
     rc = lib().orc_mppi_merge(G, T, n, _p(parts), _p(plan), float(lam), _p(ustar), _p(nxt))
     return rc, ustar, nxt
+
+
+def _dims(dims):
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32))
+    return d, d.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def mlp_num_params(dims) -> int:
+    return int(sum(dims[l - 1] * dims[l] + dims[l] for l in range(1, len(dims))))
+
+
+def mlp_forward(dims, params, X, bf16=False, want_acts=False):
+    """MLP forward (hidden GELU layers, linear output) -> Y [n, out] (and the
+    pre-activations of every layer when want_acts)."""
+    d, dp = _dims(dims)
+    X = _arr(X)
+    n = X.shape[0]
+    Y = np.zeros((n, dims[-1]))
+    acts = np.zeros(n * sum(dims[1:])) if want_acts else None
+    lib().orc_mlp_forward(len(dims) - 1, dp, _p(_arr(params)), n, _p(X), int(bf16), _p(Y), _p(acts))
+    return (Y, acts) if want_acts else Y
+
+
+def mlp_loss_grad(dims, params, X, Yt, bf16=False):
+    """Mean squared error and its gradient w.r.t. the flat parameters."""
+    d, dp = _dims(dims)
+    X, Yt = _arr(X), _arr(Yt)
+    g = np.zeros(mlp_num_params(dims))
+    loss = lib().orc_mlp_loss_grad(len(dims) - 1, dp, _p(_arr(params)), X.shape[0], _p(X), _p(Yt),
+                                   int(bf16), _p(g))
+    return loss, g
 
 
 def max_threads() -> int:

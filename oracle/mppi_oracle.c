@@ -861,3 +861,145 @@ int orc_mppi_merge(int G, int T, int n, const double* parts, const double* plan,
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned proposal: an MLP (input -> L hidden GELU layers -> linear output) */
+/* and its gradients, in double precision, written from the definitions:     */
+/*   z_l = W_l h_{l-1} + b_l,  h_l = gelu(z_l) (hidden),  y = W_L h_{L-1} + b_L */
+/*   gelu(x) = x Phi(x) = x (1 + erf(x / sqrt 2)) / 2,                        */
+/*   loss = mean over batch and outputs of (y - y*)^2.                        */
+/* W_l is row-major [out][in].  With bf16 != 0 the tensors that the GPU keeps */
+/* in BF16 (weights, layer inputs, the loss gradient and the backpropagated   */
+/* deltas) are rounded to BF16 (round to nearest even) at the same points, so */
+/* that only accumulation order separates the two sides.                      */
+
+static double bf16_round(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {  /* finite: round to nearest even */
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+  }
+  u &= 0xffff0000u;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+static double gelu_grad(double x) {
+  return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * exp(-0.5 * x * x) / sqrt(2.0 * PI);
+}
+
+/* dims[0..L]: widths (input, hidden..., output); params: W_1, b_1, ..., W_L,
+ * b_L flat.  X: [n][dims[0]]; Y: [n][dims[L]].  acts (may be NULL): the
+ * pre-activations z_l of every layer, [n][dims[l]] each, concatenated. */
+void orc_mlp_forward(int L, const int* dims, const double* params, int n, const double* X,
+                     int bf16, double* Y, double* acts) {
+  int maxw = 0;
+  for (int l = 0; l <= L; l++) if (dims[l] > maxw) maxw = dims[l];
+  double* h = (double*)malloc(sizeof(double) * maxw);
+  double* z = (double*)malloc(sizeof(double) * maxw);
+  for (int s = 0; s < n; s++) {
+    for (int i = 0; i < dims[0]; i++) h[i] = bf16 ? bf16_round(X[(size_t)s * dims[0] + i]) : X[(size_t)s * dims[0] + i];
+    const double* p = params;
+    size_t aoff = 0;
+    for (int l = 1; l <= L; l++) {
+      const int in = dims[l - 1], out = dims[l];
+      const double* W = p;
+      const double* b = p + (size_t)in * out;
+      for (int o = 0; o < out; o++) {
+        double acc = 0.0;
+        for (int i = 0; i < in; i++) acc += (bf16 ? bf16_round(W[(size_t)o * in + i]) : W[(size_t)o * in + i]) * h[i];
+        z[o] = acc + b[o];
+      }
+      if (acts) for (int o = 0; o < out; o++) acts[aoff + (size_t)s * out + o] = z[o];
+      aoff += (size_t)n * out;
+      if (l < L) {
+        for (int o = 0; o < out; o++) h[o] = bf16 ? bf16_round(gelu(z[o])) : gelu(z[o]);
+      } else {
+        for (int o = 0; o < out; o++) Y[(size_t)s * out + o] = z[o];
+      }
+      p += (size_t)in * out + out;
+    }
+  }
+  free(h);
+  free(z);
+}
+
+/* Loss and its gradient with respect to every parameter (same flat layout
+ * as params).  Returns the loss. */
+double orc_mlp_loss_grad(int L, const int* dims, const double* params, int n, const double* X,
+                         const double* Yt, int bf16, double* grad) {
+  size_t nact = 0, nparam = 0;
+  for (int l = 1; l <= L; l++) {
+    nact += (size_t)n * dims[l];
+    nparam += (size_t)dims[l - 1] * dims[l] + dims[l];
+  }
+  double* acts = (double*)malloc(sizeof(double) * nact);
+  double* Y = (double*)malloc(sizeof(double) * (size_t)n * dims[L]);
+  orc_mlp_forward(L, dims, params, n, X, bf16, Y, acts);
+  for (size_t i = 0; i < nparam; i++) grad[i] = 0.0;
+  const int nout = dims[L];
+  const double scale = 2.0 / ((double)n * nout);
+  double loss = 0.0;
+  for (size_t i = 0; i < (size_t)n * nout; i++) {
+    const double e = Y[i] - Yt[i];
+    loss += e * e;
+  }
+  loss /= (double)n * nout;
+  /* offsets of every layer's parameters and pre-activations */
+  size_t poff[16], aoff[16];
+  {
+    size_t p = 0, a = 0;
+    for (int l = 1; l <= L; l++) {
+      poff[l] = p;
+      aoff[l] = a;
+      p += (size_t)dims[l - 1] * dims[l] + dims[l];
+      a += (size_t)n * dims[l];
+    }
+  }
+  int maxw = 0;
+  for (int l = 0; l <= L; l++) if (dims[l] > maxw) maxw = dims[l];
+  double* d = (double*)malloc(sizeof(double) * maxw);   /* dloss/dz_l */
+  double* dn = (double*)malloc(sizeof(double) * maxw);
+  double* hin = (double*)malloc(sizeof(double) * maxw);
+  for (int s = 0; s < n; s++) {
+    for (int o = 0; o < nout; o++) {
+      const double g = scale * (Y[(size_t)s * nout + o] - Yt[(size_t)s * nout + o]);
+      d[o] = bf16 ? bf16_round(g) : g;
+    }
+    for (int l = L; l >= 1; l--) {
+      const int in = dims[l - 1], out = dims[l];
+      /* input of layer l */
+      for (int i = 0; i < in; i++) {
+        double v;
+        if (l == 1) v = X[(size_t)s * in + i];
+        else v = gelu(acts[aoff[l - 1] + (size_t)s * in + i]);
+        hin[i] = bf16 ? bf16_round(v) : v;
+      }
+      const double* W = params + poff[l];
+      double* gW = grad + poff[l];
+      double* gb = grad + poff[l] + (size_t)in * out;
+      for (int o = 0; o < out; o++) {
+        gb[o] += d[o];
+        for (int i = 0; i < in; i++) gW[(size_t)o * in + i] += d[o] * hin[i];
+      }
+      if (l > 1) {
+        for (int i = 0; i < in; i++) {
+          double acc = 0.0;
+          for (int o = 0; o < out; o++) acc += (bf16 ? bf16_round(W[(size_t)o * in + i]) : W[(size_t)o * in + i]) * d[o];
+          const double g = acc * gelu_grad(acts[aoff[l - 1] + (size_t)s * in + i]);
+          dn[i] = bf16 ? bf16_round(g) : g;
+        }
+        for (int i = 0; i < in; i++) d[i] = dn[i];
+      }
+    }
+  }
+  free(acts);
+  free(Y);
+  free(d);
+  free(dn);
+  free(hin);
+  return loss;
+}
