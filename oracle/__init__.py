@@ -18,6 +18,8 @@ What each wrapped function follows in the paper:
   rollout ................. Eq. 1-3, 5-7
   mppi_update ............. Eq. 4a-4b and the warm-start shift
   mppi_partial / merge .... Eq. 4 over K split into shards (log-sum-exp merge)
+  mppi_update_mix ......... Eq. 4 with two proposal plans (learned proposal and
+                            the plain warm start as its fallback)
   mlp_forward / loss_grad . the learned proposal network (no paper equation:
                             an MLP and its backpropagation, from the definitions)
   mppi_step ............... the full update
@@ -149,6 +151,9 @@ def _declare(L):
     L.orc_mppi_partial.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_double, _dp]
     L.orc_mppi_merge.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_double, _dp, _dp]
     L.orc_mppi_merge.restype = C.c_int
+    L.orc_mppi_update_mix.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, C.c_int,
+                                      C.c_double, _dp, _dp]
+    L.orc_mppi_update_mix.restype = C.c_int
     ip = C.POINTER(C.c_int)
     L.orc_mlp_forward.argtypes = [C.c_int, ip, _dp, C.c_int, _dp, C.c_int, _dp, _dp]
     L.orc_mlp_loss_grad.argtypes = [C.c_int, ip, _dp, C.c_int, _dp, _dp, C.c_int, _dp]
@@ -411,6 +416,35 @@ def mppi_step(robot: Robot, cost: Cost, dt, T, K, lam, sigma, seed, it, q0, qd0,
     if want_noise:
         out["noise"] = noise
     return out
+
+
+def mppi_update_mix(S, noise, plan, prop, k_split, lam):
+    """Two-proposal update: samples k >= k_split were drawn around `prop`.
+    -> (rc, ustar, plan_next)"""
+    S = _arr(S)
+    noise = _arr(noise)
+    K, T, n = noise.shape
+    ustar = np.zeros((T, n))
+    nxt = np.zeros((T, n))
+    rc = lib().orc_mppi_update_mix(K, T, n, _p(S), _p(noise), _p(_arr(plan, T * n)),
+                                   _p(_arr(prop, T * n)), int(k_split), float(lam), _p(ustar),
+                                   _p(nxt))
+    return rc, ustar, nxt
+
+
+def mixed_step(robot, cost, dt, T, K, lam, sigma, seed, it, q0, qd0, goal, plane, plan, prop,
+               k_split, nthreads=8):
+    """Full two-proposal update: rollouts around plan (k < k_split) or prop,
+    then mppi_update_mix. -> dict(rc, S, ustar, plan_next)"""
+    n = robot.n
+    S = np.zeros(K)
+    noise = np.zeros((K, T, n))
+    for k in range(K):
+        base = plan if k < k_split else prop
+        S[k], noise[k] = rollout(robot, cost, dt, T, sigma, seed, it, k, q0, qd0, goal, plane,
+                                 base, want_noise=True)
+    rc, us, nxt = mppi_update_mix(S, noise, plan, prop, k_split, lam)
+    return dict(rc=rc, S=S, ustar=us, plan_next=nxt)
 
 
 def mppi_partial(S, noise, lam):

@@ -1003,3 +1003,41 @@ double orc_mlp_loss_grad(int L, const int* dims, const double* params, int n, co
   free(hin);
   return loss;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Two-proposal update (learned proposal with plain MPPI as the fallback):    */
+/* samples k < k_split are drawn around the nominal plan u (the warm start),  */
+/* samples k >= k_split around a second plan p (the learned proposal); with   */
+/* the weights of Eq. 4a the update is the weighted mean of the sampled       */
+/* controls, u*_t = sum_k wbar_k (u^(k)_t + dtau_{k,t}), which is Eq. 4b when */
+/* k_split = K.  Non-finite costs get weight 0; if none is finite the plan is */
+/* kept and 1 is returned.                                                    */
+int orc_mppi_update_mix(int K, int T, int n, const double* S, const double* noise,
+                        const double* plan, const double* prop, int k_split, double lambda,
+                        double* ustar, double* plan_next) {
+  double Smin = INFINITY;
+  for (int k = 0; k < K; k++)
+    if (isfinite(S[k]) && S[k] < Smin) Smin = S[k];
+  if (!isfinite(Smin)) {
+    for (int i = 0; i < T * n; i++) ustar[i] = plan_next[i] = plan[i];
+    return 1;
+  }
+  double Z = 0.0;
+  for (int k = 0; k < K; k++)
+    if (isfinite(S[k])) Z += exp(-(S[k] - Smin) / lambda);
+  for (int i = 0; i < T * n; i++) {
+    double acc = 0.0;
+    for (int k = 0; k < K; k++) {
+      if (!isfinite(S[k])) continue;
+      const double w = exp(-(S[k] - Smin) / lambda) / Z;
+      const double base = (k < k_split) ? plan[i] : prop[i];
+      acc += w * (base + noise[(size_t)k * T * n + i]);
+    }
+    ustar[i] = acc;
+  }
+  for (int t = 0; t < T; t++) {
+    int src = (t + 1 < T) ? t + 1 : T - 1;
+    for (int j = 0; j < n; j++) plan_next[t * n + j] = ustar[src * n + j];
+  }
+  return 0;
+}

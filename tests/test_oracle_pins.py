@@ -479,3 +479,31 @@ def test_step_equals_rollouts_plus_update_and_threads_agree():
         assert S == o1["S"][k] and np.array_equal(nz, o1["noise"][k])
     _, us, _, _ = oracle.mppi_update(o1["S"], o1["noise"], plan, 1.0)
     assert np.array_equal(us, o1["ustar"])
+
+
+# ---------------------------------------------------------------------------
+# two-proposal update (learned proposal with the plain warm start beside it)
+
+def test_mixture_update_reduces_to_eq4_and_closed_forms():
+    K, T, n = 30, 4, 7
+    plan = RNG.normal(size=(T, n))
+    prop = RNG.normal(size=(T, n))
+    noise = RNG.normal(size=(K, T, n))
+    S = RNG.uniform(0, 4, K)
+    _, ref, refn, _ = oracle.mppi_update(S, noise, plan, 0.8)
+    # k_split = K: every sample around the nominal -> Eq. 4b
+    rc, us, nxt = oracle.mppi_update_mix(S, noise, plan, prop, K, 0.8)
+    assert rc == 0 and np.allclose(us, ref, atol=1e-13) and np.allclose(nxt, refn, atol=1e-13)
+    # identical proposals -> Eq. 4b for any split
+    _, us, _ = oracle.mppi_update_mix(S, noise, plan, plan, 11, 0.8)
+    assert np.allclose(us, ref, atol=1e-13)
+    # two samples, one per proposal: weighted mean of the two sampled controls
+    S2 = np.array([1.0, 1.5])
+    rc, us, _ = oracle.mppi_update_mix(S2, noise[:2], plan, prop, 1, 0.5)
+    w = np.exp(-0.5 / 0.5)
+    want = ((plan + noise[0]) + w * (prop + noise[1])) / (1 + w)
+    assert np.allclose(us, want, atol=1e-14)
+    # lambda -> 0: the argmin sample's control, whichever proposal it came from
+    _, us, _ = oracle.mppi_update_mix(S, noise, plan, prop, 13, 1e-12)
+    k = int(np.argmin(S))
+    assert np.allclose(us, (plan if k < 13 else prop) + noise[k], atol=1e-14)
