@@ -195,6 +195,31 @@ MPPI_API int mppi_rollout_device(mppi_t h, const float* d_in, float* d_S, float*
 MPPI_API int mppi_update_device(mppi_t h, const float* d_S, const float* d_noise, const float* d_plan,
                        float* d_ustar, float* d_plan_next);
 
+/* The handle's model used as a plant: n independent states advanced by one
+ * control period dt under a torque held constant (zero-order hold, as the
+ * paper's robot side does between updates, Sec. IV-A), in `substeps` Euler
+ * steps of Eq. 5-7 with the handle's contact model.  d_in: [n][25] device
+ * records (q, qd, goal, plane); d_tau: [n][7]; d_out: [n][14] (q, qd after
+ * dt).  Queued on the handle's stream.  substeps in 1..1000. */
+MPPI_API int mppi_simulate_device(mppi_t h, int n, const float* d_in, const float* d_tau,
+                                  int substeps, float* d_out);
+
+/* Device-to-device plan access on the handle's stream (no host wait):
+ * current nominal plan in/out and u* of the last update ([T][7] each). */
+MPPI_API int mppi_set_plan_device(mppi_t h, const float* d_u);
+MPPI_API int mppi_get_plan_device(mppi_t h, float* d_u);
+MPPI_API int mppi_get_updated_plan_device(mppi_t h, float* d_u);
+
+/* Second proposal for the NEXT update only (learned proposal with plain MPPI
+ * as its fallback): samples k < n_plain are drawn around the nominal plan
+ * (the warm start) and samples k >= n_plain around d_prop ([T][7], device,
+ * copied).  The update is then the importance-weighted mean of the sampled
+ * controls, u*_t = sum_k wbar_k (u^(k)_t + dtau_{k,t}) with the weights of
+ * Eq. 4a, so whichever proposal produces the cheaper rollouts dominates.
+ * n_plain in 0..K; after the update every sample is around the nominal plan
+ * again.  Queued on the handle's stream. */
+MPPI_API int mppi_set_proposal_device(mppi_t h, const float* d_prop, int n_plain);
+
 /* End-effector pose (p xyz, quaternion wxyz) at joint angles q, computed on
  * the device by the rollouts' own kinematics (host arrays). */
 MPPI_API int mppi_ee_pose(mppi_t h, const float q[7], float pose_out[7]);

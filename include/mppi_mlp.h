@@ -1,0 +1,73 @@
+/*
+ * mppi_mlp.h - learned proposal for the MPPI update (C ABI).
+ *
+ * The paper samples around the previous plan (Sec. II) with the strategy of
+ * another paper (Sec. III-B).  This layer adds a learned proposal: an MLP
+ * maps (q, qd, goal, current nominal plan) to the plan that plain MPPI would
+ * produce, and the update samples around that prediction.  The network is
+ *   x (n_in) -> [Linear -> GELU] x n_layers (width n_hidden) -> Linear (n_out)
+ * with BF16 weights and activations and FP32 accumulation on the tensor
+ * cores (mma.sync m16n8k16), FP32 master weights and Adam.  Inputs and
+ * outputs are standardised with fixed per-feature means and deviations.
+ * The loss is the mean squared error of the standardised outputs.
+ * Parameters are flat FP32: W_1 [n_hidden][n_in] row-major, b_1, W_2, b_2,
+ * ..., W_L [n_out][n_hidden], b_L.  All device pointers are caller-owned
+ * FP32 arrays; work is queued on the stream given at creation.
+ */
+#ifndef MPPI_MLP_H
+#define MPPI_MLP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "mppi.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mppi_mlp_s* mppi_mlp_t;
+
+typedef struct mppi_mlp_config {
+  int n_in, n_hidden, n_layers, n_out;  /* n_layers hidden layers, 1..6; widths <= 1024 */
+  int max_batch;                        /* rows per forward / train step, 1..65536      */
+  uint64_t seed;                        /* weight initialisation                         */
+  float beta1, beta2, eps;              /* Adam                                          */
+} mppi_mlp_config;
+
+/* Creates the network on the current device with Kaiming-uniform weights,
+ * zero biases, identity standardisation.  stream: cudaStream_t or NULL. */
+MPPI_API int mppi_mlp_create(const mppi_mlp_config* cfg, void* stream, mppi_mlp_t* out);
+MPPI_API int mppi_mlp_destroy(mppi_mlp_t m);
+MPPI_API int mppi_mlp_num_params(mppi_mlp_t m, size_t* n);
+/* FP32 master parameters (host arrays of num_params floats); set also
+ * refreshes the BF16 copies and clears the Adam moments. */
+MPPI_API int mppi_mlp_get_params(mppi_mlp_t m, float* host);
+MPPI_API int mppi_mlp_set_params(mppi_mlp_t m, const float* host);
+/* Per-feature standardisation (host arrays; deviations must be > 0). */
+MPPI_API int mppi_mlp_set_normalization(mppi_mlp_t m, const float* mean_in, const float* std_in,
+                                        const float* mean_out, const float* std_out);
+/* y = net(x) for n rows of raw inputs d_x [n][n_in]; raw outputs d_y [n][n_out]. */
+MPPI_API int mppi_mlp_forward(mppi_mlp_t m, const float* d_x, int n, float* d_y);
+/* Loss and gradient for n rows (d_y: raw targets); grad_host (num_params
+ * floats, may be NULL) receives the gradient; blocks until done. */
+MPPI_API int mppi_mlp_loss_grad(mppi_mlp_t m, const float* d_x, const float* d_y, int n,
+                                float* loss, float* grad_host);
+/* One Adam step (learning rate lr) on n rows; *loss (may be NULL: no wait)
+ * receives the batch loss before the step. */
+MPPI_API int mppi_mlp_train_step(mppi_mlp_t m, const float* d_x, const float* d_y, int n,
+                                 float lr, float* loss);
+/* Learned proposal for an MPPI handle: x = (q, qd, goal from d_in [25
+ * device floats], the handle's current nominal plan [T][7]) -> the network's
+ * plan, installed as the second proposal of the handle's next update with
+ * n_plain samples kept around the plain warm start (mppi_set_proposal_device;
+ * n_plain = 0 samples only around the network's plan).  Queued on the
+ * handle's stream; the network's buffers must not be in use by a training
+ * step at the same time.  Needs n_in = 21 + 7T and n_out = 7T. */
+MPPI_API int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPPI_MLP_H */

@@ -111,20 +111,27 @@ __device__ __forceinline__ float rollout_sample(const ProbK& P, const float* in,
 
 // One rollout per thread.  plan: [T][7] nominal torques; in: IN_FLOATS
 // inputs; iter: update counter (device); S: [K] costs; noise: [T*7][K].
+// Samples k < k_split roll out around plan; samples k >= k_split around the
+// second proposal prop (ksplit_p null: every sample around plan).
 template <bool STORE_NOISE>
 __global__ void __launch_bounds__(ROLLOUT_BLOCK)
 rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
                const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
-               float* __restrict__ S, float* __restrict__ noise) {
+               float* __restrict__ S, float* __restrict__ noise,
+               const float* __restrict__ prop = nullptr, const int* __restrict__ ksplit_p = nullptr) {
   __shared__ float s_plan[T_MAX * NJ];
+  __shared__ float s_prop[T_MAX * NJ];
   __shared__ float s_in[IN_FLOATS];
   const int T = P.T, K = P.K;
+  const int k_split = ksplit_p ? *ksplit_p : K;
   for (int i = threadIdx.x; i < T * NJ; i += blockDim.x) s_plan[i] = plan[i];
+  if (k_split < K)
+    for (int i = threadIdx.x; i < T * NJ; i += blockDim.x) s_prop[i] = prop[i];
   if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
   __syncthreads();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
-  S[k] = rollout_sample<STORE_NOISE>(P, s_in, s_plan, *iter_p, k, noise);
+  S[k] = rollout_sample<STORE_NOISE>(P, s_in, k < k_split ? s_plan : s_prop, *iter_p, k, noise);
 }
 
 // ---------------------------------------------------------------------------
@@ -309,7 +316,7 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
 
 // Dynamic shared memory of rollout_kernel_rolled for horizon T, block B.
 __host__ __device__ constexpr size_t rolled_smem_bytes(int T, int B) {
-  return sizeof(float) * (static_cast<size_t>((T * NJ + 3) / 4 * 4) + 32 +
+  return sizeof(float) * (2 * static_cast<size_t>((T * NJ + 3) / 4 * 4) + 32 +
                           static_cast<size_t>(ROLLED_FLOATS_PER_THREAD) * B);
 }
 
@@ -317,19 +324,26 @@ template <bool STORE_NOISE, int B>
 __global__ void __launch_bounds__(B)
 rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__ in,
                       const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
-                      float* __restrict__ S, float* __restrict__ noise) {
+                      float* __restrict__ S, float* __restrict__ noise,
+                      const float* __restrict__ prop = nullptr,
+                      const int* __restrict__ ksplit_p = nullptr) {
   extern __shared__ float dsm[];
   const int T = P.T, K = P.K;
+  const int k_split = ksplit_p ? *ksplit_p : K;
+  const int pstride = (T * NJ + 3) / 4 * 4;
   float* s_plan = dsm;
-  float* s_in = dsm + (T * NJ + 3) / 4 * 4;
+  float* s_prop = dsm + pstride;
+  float* s_in = s_prop + pstride;
   float* s_work = s_in + 32;
   for (int i = threadIdx.x; i < T * NJ; i += B) s_plan[i] = plan[i];
+  if (k_split < K)
+    for (int i = threadIdx.x; i < T * NJ; i += B) s_prop[i] = prop[i];
   if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
   __syncthreads();
   const int k = blockIdx.x * B + threadIdx.x;
   if (k >= K) return;
-  S[k] = rollout_sample_rolled<STORE_NOISE, B>(P, s_in, s_plan, *iter_p, k, noise, s_work,
-                                               threadIdx.x);
+  S[k] = rollout_sample_rolled<STORE_NOISE, B>(P, s_in, k < k_split ? s_plan : s_prop, *iter_p,
+                                               k, noise, s_work, threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -392,12 +406,13 @@ constexpr int UPDATE_THREADS = 512;
 
 template <typename Acc>
 __device__ __forceinline__ void weight_acc(float s, float n, float m, Acc inv_l, Acc& z, Acc& z2,
-                                           Acc& nacc) {
+                                           Acc& nacc, Acc& zb, bool second) {
   const Acc w = isfinite(s) ? acc_exp((static_cast<Acc>(m) - static_cast<Acc>(s)) * inv_l)
                             : Acc(0);
   z += w;
   z2 += w * w;
   nacc += w * static_cast<Acc>(n);
+  if (second) zb += w;
 }
 
 // Result of Eq. 4 for one plan entry, valid in thread 0 of the block.
@@ -411,12 +426,16 @@ struct EntryResult {
 };
 
 // Block-wide Eq. 4a-4b for one entry: plan value u, costs S[K], noise row
-// nrow[K].  Every thread of the block must call it.
+// nrow[K].  Samples k >= k_split were drawn around the second proposal p:
+// u* = sum_k wbar_k (u^(k) + dtau_k) = u + (Zb (p - u) + N) / Z, which is
+// exactly u + N / Z when no sample used p (Zb = 0).  Every thread of the
+// block must call it.
 template <typename Acc>
 __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
                                                           const float* __restrict__ S,
                                                           const float* __restrict__ nrow,
-                                                          float u, bool count_bad) {
+                                                          float u, bool count_bad, float p = 0.f,
+                                                          int k_split = 0x7fffffff) {
   __shared__ float sm_f[32];
   __shared__ Acc sm_a[3 * 32];
   const bool vec = (K % 4 == 0) && ((reinterpret_cast<uintptr_t>(S) & 15) == 0) &&
@@ -444,32 +463,40 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
   }
   m = block_min<UPDATE_THREADS>(m, sm_f);
   const bool ok = isfinite(m);
-  Acc z = Acc(0), z2 = Acc(0), nacc = Acc(0);
+  Acc z = Acc(0), z2 = Acc(0), nacc = Acc(0), zb = Acc(0);
   if (ok) {
     const Acc inv_l = Acc(1) / static_cast<Acc>(lambda);
     const float4* S4 = reinterpret_cast<const float4*>(S);
     const float4* N4 = reinterpret_cast<const float4*>(nrow);
     Acc za[4] = {Acc(0), Acc(0), Acc(0), Acc(0)}, z2a[4] = {Acc(0), Acc(0), Acc(0), Acc(0)},
-        na[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
+        na[4] = {Acc(0), Acc(0), Acc(0), Acc(0)}, zba[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
 #pragma unroll 2
     for (int i = threadIdx.x; i < K4; i += UPDATE_THREADS) {
       const float4 sv = S4[i];
       const float4 nv = N4[i];
-      weight_acc(sv.x, nv.x, m, inv_l, za[0], z2a[0], na[0]);
-      weight_acc(sv.y, nv.y, m, inv_l, za[1], z2a[1], na[1]);
-      weight_acc(sv.z, nv.z, m, inv_l, za[2], z2a[2], na[2]);
-      weight_acc(sv.w, nv.w, m, inv_l, za[3], z2a[3], na[3]);
+      const int k = 4 * i;
+      weight_acc(sv.x, nv.x, m, inv_l, za[0], z2a[0], na[0], zba[0], k >= k_split);
+      weight_acc(sv.y, nv.y, m, inv_l, za[1], z2a[1], na[1], zba[1], k + 1 >= k_split);
+      weight_acc(sv.z, nv.z, m, inv_l, za[2], z2a[2], na[2], zba[2], k + 2 >= k_split);
+      weight_acc(sv.w, nv.w, m, inv_l, za[3], z2a[3], na[3], zba[3], k + 3 >= k_split);
     }
     for (int k = 4 * K4 + threadIdx.x; k < K; k += UPDATE_THREADS)
-      weight_acc(S[k], nrow[k], m, inv_l, za[0], z2a[0], na[0]);
+      weight_acc(S[k], nrow[k], m, inv_l, za[0], z2a[0], na[0], zba[0], k >= k_split);
     z = (za[0] + za[1]) + (za[2] + za[3]);
     z2 = (z2a[0] + z2a[1]) + (z2a[2] + z2a[3]);
     nacc = (na[0] + na[1]) + (na[2] + na[3]);
+    zb = (zba[0] + zba[1]) + (zba[2] + zba[3]);
   }
   block_sum3<UPDATE_THREADS>(z, z2, nacc, sm_a);
-  Acc nbad = Acc(0), d1 = Acc(0), d2 = Acc(0);
+  Acc zbs = zb, d1 = Acc(0), d2 = Acc(0);
+  if (k_split < K) {
+    __syncthreads();
+    block_sum3<UPDATE_THREADS>(zbs, d1, d2, sm_a);
+  }
+  Acc nbad = Acc(0);
   if (count_bad) {
     nbad = static_cast<Acc>(bad);
+    d1 = d2 = Acc(0);
     __syncthreads();
     block_sum3<UPDATE_THREADS>(nbad, d1, d2, sm_a);
   }
@@ -481,7 +508,14 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
   r.z = z;
   r.z2 = z2;
   r.bad = static_cast<int>(nbad);
-  r.us = ok ? static_cast<float>(static_cast<Acc>(u) + nacc / z) : u;
+  if (!ok) {
+    r.us = u;
+  } else if (k_split < K) {
+    r.us = static_cast<float>(static_cast<Acc>(u) +
+                              (zbs * (static_cast<Acc>(p) - static_cast<Acc>(u)) + nacc) / z);
+  } else {
+    r.us = static_cast<float>(static_cast<Acc>(u) + nacc / z);
+  }
   return r;
 }
 
@@ -490,10 +524,13 @@ __global__ void __launch_bounds__(UPDATE_THREADS)
 update_kernel(int K, int T, float lambda, const float* __restrict__ S,
               const float* __restrict__ noise, const float* __restrict__ plan,
               float* __restrict__ ustar, float* __restrict__ plan_next, float* __restrict__ out,
-              unsigned long long* __restrict__ iter_p) {
+              unsigned long long* __restrict__ iter_p, const float* __restrict__ prop = nullptr,
+              const int* __restrict__ ksplit_p = nullptr) {
   const int e = blockIdx.x;
   const float* nrow = noise + static_cast<size_t>(e) * K;
-  const EntryResult<Acc> r = update_entry<Acc>(K, lambda, S, nrow, plan[e], e == 0);
+  const int k_split = ksplit_p ? *ksplit_p : K;
+  const EntryResult<Acc> r =
+      update_entry<Acc>(K, lambda, S, nrow, plan[e], e == 0, k_split < K ? prop[e] : 0.f, k_split);
   if (threadIdx.x != 0) return;
   const int t = e / NJ;
   const float us = r.us;
@@ -519,6 +556,54 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
       out[OUT_STATS + 3] = static_cast<float>(r.bad);
     }
     if (iter_p && r.ok) *iter_p += 1ull;
+  }
+}
+
+// The model itself as a plant: state i of n advanced by `substeps` steps of
+// dt / substeps under the constant torque tau[i] (zero-order hold), with
+// the same dynamics, contact and Euler step as the rollouts.  in: [n][25]
+// records (q, qd, goal, plane); out: [n][14] (q, qd).
+static __global__ void simulate_kernel(const __grid_constant__ ProbK P, int n, const float* __restrict__ in,
+                                const float* __restrict__ tau, int substeps, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* r = in + static_cast<size_t>(i) * IN_FLOATS;
+  float q[NJ], qd[NJ], u[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    q[j] = r[j];
+    qd[j] = r[NJ + j];
+    u[j] = tau[static_cast<size_t>(i) * NJ + j];
+  }
+  const float plane[4] = {r[21], r[22], r[23], r[24]};
+  const bool contact = P.cost.contact != 0;
+  const float h = P.dt / static_cast<float>(substeps);
+  for (int s = 0; s < substeps; ++s) {
+    LinkState ls[NJ];
+    EEState ee;
+    forward_sweep(P.rb, q, qd, ls, ee);
+    float hb[NJ], M[NJ * (NJ + 1) / 2];
+    backward_sweep(P.rb, qd, ls, hb, M);
+    float rhs[NJ];
+    const float f = contact ? contact_force(P.cost, plane, ee) : 0.f;
+    const float Fc[3] = {f * plane[0], f * plane[1], f * plane[2]};
+    float pxF[3];
+    cross3(ee.p, Fc, pxF);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) rhs[j] = u[j] + dot3(ls[j].z, pxF) + dot3(ls[j].w, Fc) - hb[j];
+    float qdd[NJ];
+    ldlt_solve(M, rhs, qdd);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      qd[j] = fmaf(qdd[j], h, qd[j]);
+      q[j] = fmaf(qd[j], h, q[j]);
+    }
+  }
+  float* o = out + static_cast<size_t>(i) * 2 * NJ;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    o[j] = q[j];
+    o[NJ + j] = qd[j];
   }
 }
 

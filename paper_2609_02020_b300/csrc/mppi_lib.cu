@@ -42,6 +42,8 @@ struct mppi_s {
   float* d_scratch_plan = nullptr;        // [2][T][7] for timing runs
   float* d_misc = nullptr;                // 32 floats for small helper kernels
   uint32_t* d_words = nullptr;            // 8 x 1024 words for mppi_noise_words
+  float* d_prop = nullptr;                // second proposal plan [T][7]
+  int* d_ctl = nullptr;                   // {k_split of the next update, K}
   unsigned long long* d_iter = nullptr;
   // pinned host staging
   float* h_in = nullptr;
@@ -252,37 +254,48 @@ cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float*
     const size_t smem = rolled_smem_bytes(h->P.T, ROLLOUT_BLOCK);
     if (noise)
       rollout_kernel_rolled<true, ROLLOUT_BLOCK><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, noise);
+          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl);
     else
       rollout_kernel_rolled<false, ROLLOUT_BLOCK><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, nullptr);
+          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl);
     return cudaGetLastError();
   }
   if (noise)
-    rollout_kernel<true><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S, noise);
+    rollout_kernel<true><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S, noise,
+                                                               h->d_prop, h->d_ctl);
   else
-    rollout_kernel<false><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S, nullptr);
+    rollout_kernel<false><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S,
+                                                                nullptr, h->d_prop, h->d_ctl);
   return cudaGetLastError();
 }
 
+// prop / ksplit null: plain Eq. 4 (every sample around plan)
 cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const float* plan,
-                          float* ustar, float* plan_next, float* out, unsigned long long* iter) {
+                          float* ustar, float* plan_next, float* out, unsigned long long* iter,
+                          const float* prop = nullptr, const int* ksplit = nullptr) {
   const int grid = h->P.T * NJ;
   if (h->reduce_fp64)
-    update_kernel<double><<<grid, UPDATE_THREADS, 0, h->stream>>>(h->P.K, h->P.T, h->P.lambda, S,
-                                                                noise, plan, ustar, plan_next, out, iter);
+    update_kernel<double><<<grid, UPDATE_THREADS, 0, h->stream>>>(
+        h->P.K, h->P.T, h->P.lambda, S, noise, plan, ustar, plan_next, out, iter, prop, ksplit);
   else
-    update_kernel<float><<<grid, UPDATE_THREADS, 0, h->stream>>>(h->P.K, h->P.T, h->P.lambda, S, noise,
-                                                               plan, ustar, plan_next, out, iter);
+    update_kernel<float><<<grid, UPDATE_THREADS, 0, h->stream>>>(
+        h->P.K, h->P.T, h->P.lambda, S, noise, plan, ustar, plan_next, out, iter, prop, ksplit);
   return cudaGetLastError();
 }
 
-// the whole update on device buffers: rollouts, then Eq. 4 into the other plan
+// the whole update on device buffers: rollouts, then Eq. 4 into the other
+// plan; a second proposal set for this update is consumed (k_split := K)
 cudaError_t enqueue_update(mppi_s* h, int cur) {
   cudaError_t e = launch_rollout(h, h->d_in, h->d_plan[cur], h->d_S, h->d_noise);
   if (e != cudaSuccess) return e;
-  return launch_update(h, h->d_S, h->d_noise, h->d_plan[cur], h->d_ustar, h->d_plan[cur ^ 1],
-                       h->d_out, h->d_iter);
+  e = launch_update(h, h->d_S, h->d_noise, h->d_plan[cur], h->d_ustar, h->d_plan[cur ^ 1],
+                    h->d_out, h->d_iter, h->d_prop, h->d_ctl);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(h->d_ctl, h->d_ctl + 1, sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
+}
+
+__global__ void set_int_kernel(int* dst, int v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
 }
 
 size_t out_bytes(const mppi_s* h) { return sizeof(float) * (OUT_PLAN + h->P.T * NJ); }
@@ -334,6 +347,17 @@ int read_status(mppi_s* h) {
 
 // Message for mppi_last_error(NULL) from the other translation units.
 void mppi_set_thread_error(const std::string& msg) { g_create_err = msg; }
+
+// Handle internals for the other translation units of the library.
+float* mppi_internal_plan(mppi_t h) { return h->d_plan[h->cur]; }
+int mppi_internal_T(mppi_t h) { return h->P.T; }
+cudaStream_t mppi_internal_stream(mppi_t h) { return h->stream; }
+float* mppi_internal_prop(mppi_t h) { return h->d_prop; }
+int mppi_internal_K(mppi_t h) { return h->P.K; }
+cudaError_t mppi_internal_set_split(mppi_t h, int k_split) {
+  set_int_kernel<<<1, 32, 0, h->stream>>>(h->d_ctl, k_split);
+  return cudaGetLastError();
+}
 
 // Parameter conversion shared with the other translation units of the library.
 int mppi_convert_params(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg,
@@ -394,6 +418,14 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
   if ((e = cudaMalloc(&h->d_misc, sizeof(float) * 32)) != cudaSuccess) return bail(e, "cudaMalloc misc");
   if ((e = cudaMalloc(&h->d_words, sizeof(uint32_t) * 8 * 1024)) != cudaSuccess)
     return bail(e, "cudaMalloc words");
+  if ((e = cudaMalloc(&h->d_prop, plan_b)) != cudaSuccess) return bail(e, "cudaMalloc prop");
+  if ((e = cudaMalloc(&h->d_ctl, 2 * sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc ctl");
+  {
+    const int ctl[2] = {K, K};
+    if ((e = cudaMemcpy(h->d_ctl, ctl, sizeof ctl, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e, "ctl");
+    if ((e = cudaMemset(h->d_prop, 0, plan_b)) != cudaSuccess) return bail(e, "memset prop");
+  }
   h->out_floats = OUT_PLAN + T * NJ;
   if ((e = cudaMalloc(&h->d_out, sizeof(float) * h->out_floats)) != cudaSuccess)
     return bail(e, "cudaMalloc out");
@@ -430,6 +462,8 @@ int mppi_destroy(mppi_t h) {
   cudaFree(h->d_in);
   cudaFree(h->d_misc);
   cudaFree(h->d_words);
+  cudaFree(h->d_prop);
+  cudaFree(h->d_ctl);
   cudaFree(h->d_out);
   cudaFree(h->d_iter);
   if (h->h_in) cudaFreeHost(h->h_in);
@@ -625,6 +659,47 @@ int mppi_ee_pose(mppi_t h, const float q[7], float pose_out[7]) {
   return MPPI_OK;
 }
 
+int mppi_simulate_device(mppi_t h, int n, const float* d_in, const float* d_tau, int substeps,
+                         float* d_out) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (!d_in || !d_tau || !d_out) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  if (n < 1 || substeps < 1 || substeps > 1000)
+    return fail(h, MPPI_ERR_INVALID_ARG, "n must be >= 1 and substeps in 1..1000");
+  simulate_kernel<<<(n + 63) / 64, 64, 0, h->stream>>>(h->P, n, d_in, d_tau, substeps, d_out);
+  CUDA_TRY(h, cudaGetLastError());
+  return MPPI_OK;
+}
+
+int mppi_set_plan_device(mppi_t h, const float* d_u) {
+  if (!h || !d_u) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_plan[h->cur], d_u, sizeof(float) * h->P.T * NJ,
+                              cudaMemcpyDeviceToDevice, h->stream));
+  return MPPI_OK;
+}
+
+int mppi_get_plan_device(mppi_t h, float* d_u) {
+  if (!h || !d_u) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, cudaMemcpyAsync(d_u, h->d_plan[h->cur], sizeof(float) * h->P.T * NJ,
+                              cudaMemcpyDeviceToDevice, h->stream));
+  return MPPI_OK;
+}
+
+int mppi_get_updated_plan_device(mppi_t h, float* d_u) {
+  if (!h || !d_u) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, cudaMemcpyAsync(d_u, h->d_ustar, sizeof(float) * h->P.T * NJ,
+                              cudaMemcpyDeviceToDevice, h->stream));
+  return MPPI_OK;
+}
+
+int mppi_set_proposal_device(mppi_t h, const float* d_prop, int n_plain) {
+  if (!h || !d_prop) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  if (n_plain < 0 || n_plain > h->P.K) return fail(h, MPPI_ERR_INVALID_ARG, "n_plain must be in 0..K");
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_prop, d_prop, sizeof(float) * h->P.T * NJ,
+                              cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(h, mppi_internal_set_split(h, n_plain));
+  return MPPI_OK;
+}
+
 int mppi_noise_words(mppi_t h, uint64_t iter, uint32_t k0, int count, uint32_t t, uint32_t* out) {
   if (!h || !out) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
   if (count < 1 || count > 1024) return fail(h, MPPI_ERR_INVALID_ARG, "count must be in 1..1024");
@@ -651,7 +726,7 @@ int mppi_time_kernels(mppi_t h, const float* d_in, int iters, float* ms_rollout,
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
     if (e == cudaSuccess)
       e = launch_update(h, h->d_S, h->d_noise, h->d_plan[h->cur], h->d_scratch_plan,
-                        h->d_scratch_plan + plan_f, nullptr, nullptr);
+                        h->d_scratch_plan + plan_f, nullptr, nullptr, h->d_prop, h->d_ctl);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
     float a = 0.f, b = 0.f;

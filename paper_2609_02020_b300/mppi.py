@@ -98,6 +98,20 @@ class ServerConfig(C.Structure):
     ]
 
 
+class MLPConfig(C.Structure):
+    _fields_ = [
+        ("n_in", C.c_int),
+        ("n_hidden", C.c_int),
+        ("n_layers", C.c_int),
+        ("n_out", C.c_int),
+        ("max_batch", C.c_int),
+        ("seed", C.c_uint64),
+        ("beta1", C.c_float),
+        ("beta2", C.c_float),
+        ("eps", C.c_float),
+    ]
+
+
 # every symbol include/*.h declares
 EXPORTS = [
     "mppi_create", "mppi_destroy", "mppi_step", "mppi_step_device", "mppi_sync",
@@ -105,6 +119,8 @@ EXPORTS = [
     "mppi_set_plan", "mppi_get_plan", "mppi_set_iter", "mppi_get_iter",
     "mppi_rollout_device", "mppi_update_device", "mppi_ee_pose", "mppi_time_kernels",
     "mppi_noise_words", "mppi_step_static", "mppi_last_error", "mppi_version",
+    "mppi_simulate_device", "mppi_set_plan_device", "mppi_get_plan_device",
+    "mppi_get_updated_plan_device", "mppi_set_proposal_device",
     # include/mppi_serve.h
     "mppi_pool_create", "mppi_pool_destroy", "mppi_pool_alloc", "mppi_pool_free",
     "mppi_pool_stats", "mppi_server_create", "mppi_server_destroy", "mppi_server_add_problem",
@@ -112,6 +128,10 @@ EXPORTS = [
     "mppi_server_poll", "mppi_server_wait", "mppi_server_start", "mppi_server_stop",
     "mppi_server_tick", "mppi_server_drain", "mppi_server_autotune", "mppi_server_stats",
     "mppi_server_set_input", "mppi_server_load_test",
+    # include/mppi_mlp.h
+    "mppi_mlp_create", "mppi_mlp_destroy", "mppi_mlp_num_params", "mppi_mlp_get_params",
+    "mppi_mlp_set_params", "mppi_mlp_set_normalization", "mppi_mlp_forward",
+    "mppi_mlp_loss_grad", "mppi_mlp_train_step", "mppi_mlp_propose",
 ]
 
 _lib = None
@@ -153,6 +173,11 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                               vp, vp, vp, vp, vp], C.c_int),
         "mppi_last_error": ([H], C.c_char_p),
         "mppi_version": ([], C.c_char_p),
+        "mppi_simulate_device": ([H, C.c_int, vp, vp, C.c_int, vp], C.c_int),
+        "mppi_set_plan_device": ([H, vp], C.c_int),
+        "mppi_get_plan_device": ([H, vp], C.c_int),
+        "mppi_get_updated_plan_device": ([H, vp], C.c_int),
+        "mppi_set_proposal_device": ([H, vp, C.c_int], C.c_int),
         "mppi_pool_create": ([C.c_size_t, C.POINTER(C.c_void_p)], C.c_int),
         "mppi_pool_destroy": ([H], C.c_int),
         "mppi_pool_alloc": ([H, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
@@ -176,6 +201,16 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_server_stats": ([H, dp], C.c_int),
         "mppi_server_set_input": ([H, C.c_int, fp], C.c_int),
         "mppi_server_load_test": ([H, C.c_double, C.c_double, C.c_uint64, dp], C.c_int),
+        "mppi_mlp_create": ([C.POINTER(MLPConfig), vp, C.POINTER(C.c_void_p)], C.c_int),
+        "mppi_mlp_destroy": ([H], C.c_int),
+        "mppi_mlp_num_params": ([H, C.POINTER(C.c_size_t)], C.c_int),
+        "mppi_mlp_get_params": ([H, fp], C.c_int),
+        "mppi_mlp_set_params": ([H, fp], C.c_int),
+        "mppi_mlp_set_normalization": ([H, fp, fp, fp, fp], C.c_int),
+        "mppi_mlp_forward": ([H, vp, C.c_int, vp], C.c_int),
+        "mppi_mlp_loss_grad": ([H, vp, vp, C.c_int, fp, fp], C.c_int),
+        "mppi_mlp_train_step": ([H, vp, vp, C.c_int, C.c_float, fp], C.c_int),
+        "mppi_mlp_propose": ([H, H, vp, C.c_int], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -370,6 +405,24 @@ class MPPI:
         out = np.zeros(7, dtype=np.float32)
         self._check(self.lib.mppi_ee_pose(self.h, _fp(_f32(q, NJ)), _fp(out)))
         return out
+
+    def simulate_device(self, d_in, d_tau, d_out, substeps: int = 10):
+        """Advance d_in's states ([n][25]) by dt under d_tau ([n][7]) into d_out ([n][14])."""
+        self._check(self.lib.mppi_simulate_device(self.h, int(d_in.shape[0]), _dptr(d_in), _dptr(d_tau),
+                                                  int(substeps), _dptr(d_out)))
+
+    def set_plan_device(self, d_u):
+        self._check(self.lib.mppi_set_plan_device(self.h, _dptr(d_u)))
+
+    def get_plan_device(self, d_u):
+        self._check(self.lib.mppi_get_plan_device(self.h, _dptr(d_u)))
+
+    def set_proposal_device(self, d_prop, n_plain: int):
+        """Second proposal for the next update: samples k >= n_plain around d_prop."""
+        self._check(self.lib.mppi_set_proposal_device(self.h, _dptr(d_prop), int(n_plain)))
+
+    def get_updated_plan_device(self, d_u):
+        self._check(self.lib.mppi_get_updated_plan_device(self.h, _dptr(d_u)))
 
     def noise_words(self, it: int, k0: int, count: int, t: int) -> np.ndarray:
         """Raw Philox words [count, 8] of the device generator."""
@@ -587,3 +640,76 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+class MLP:
+    """Learned-proposal network (include/mppi_mlp.h); device arrays are torch
+    CUDA float32 tensors."""
+
+    def __init__(self, n_in: int, n_hidden: int, n_layers: int, n_out: int, *,
+                 max_batch: int = 4096, seed: int = 0, beta1=0.9, beta2=0.999, eps=1e-8,
+                 stream=None):
+        self.lib = load()
+        cfg = MLPConfig()
+        cfg.n_in, cfg.n_hidden, cfg.n_layers, cfg.n_out = n_in, n_hidden, n_layers, n_out
+        cfg.max_batch, cfg.seed = int(max_batch), int(seed)
+        cfg.beta1, cfg.beta2, cfg.eps = beta1, beta2, eps
+        h = C.c_void_p()
+        sp = C.c_void_p(stream.cuda_stream) if stream is not None else None
+        rc = self.lib.mppi_mlp_create(C.byref(cfg), sp, C.byref(h))
+        if rc != OK:
+            raise MPPIError(rc, self.lib.mppi_last_error(None).decode())
+        self.h = h
+        self.dims = [n_in] + [n_hidden] * n_layers + [n_out]
+        n = C.c_size_t()
+        self.lib.mppi_mlp_num_params(self.h, C.byref(n))
+        self.n_params = int(n.value)
+
+    def _check(self, rc):
+        if rc != OK:
+            raise MPPIError(rc, self.lib.mppi_last_error(None).decode())
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.n_params, dtype=np.float32)
+        self._check(self.lib.mppi_mlp_get_params(self.h, _fp(p)))
+        return p
+
+    def set_params(self, p):
+        self._check(self.lib.mppi_mlp_set_params(self.h, _fp(_f32(p, self.n_params))))
+
+    def set_normalization(self, mean_in, std_in, mean_out, std_out):
+        self._check(self.lib.mppi_mlp_set_normalization(
+            self.h, _fp(_f32(mean_in, self.dims[0])), _fp(_f32(std_in, self.dims[0])),
+            _fp(_f32(mean_out, self.dims[-1])), _fp(_f32(std_out, self.dims[-1]))))
+
+    def forward(self, d_x, d_y):
+        self._check(self.lib.mppi_mlp_forward(self.h, _dptr(d_x), int(d_x.shape[0]), _dptr(d_y)))
+
+    def loss_grad(self, d_x, d_y):
+        loss = C.c_float()
+        g = np.zeros(self.n_params, dtype=np.float32)
+        self._check(self.lib.mppi_mlp_loss_grad(self.h, _dptr(d_x), _dptr(d_y), int(d_x.shape[0]),
+                                                C.byref(loss), _fp(g)))
+        return float(loss.value), g
+
+    def train_step(self, d_x, d_y, lr: float, want_loss: bool = False):
+        loss = C.c_float()
+        self._check(self.lib.mppi_mlp_train_step(self.h, _dptr(d_x), _dptr(d_y), int(d_x.shape[0]),
+                                                 float(lr), C.byref(loss) if want_loss else None))
+        return float(loss.value) if want_loss else None
+
+    def propose(self, ctl: "MPPI", d_in, n_plain: int = 0):
+        """Install the network's plan as ctl's second proposal for its next
+        update, keeping n_plain samples around ctl's warm start."""
+        self._check(self.lib.mppi_mlp_propose(self.h, ctl.h, _dptr(d_in), int(n_plain)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mppi_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -349,6 +349,65 @@ def test_rollout_device_matches_step_costs():
         assert np.array_equal(d_n.cpu().numpy(), g.noise())
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+def test_second_proposal_matches_oracle(variant):
+    """Learned-proposal form: samples k < n_plain around the warm start, the
+    rest around a second plan; the update is the weighted mean of the
+    sampled controls.  The split holds for one update only."""
+    import torch
+    c = make_case(5, cost=parity_cost(), K=600, T=12)
+    rng = np.random.default_rng(8)
+    plan0 = rng.normal(0, 2, (c["T"], 7)).astype(np.float32)
+    prop = rng.normal(0, 2, (c["T"], 7)).astype(np.float32)
+    with gpu_controller(c, variant=variant) as g:
+        g.set_plan(plan0)
+        g.set_proposal_device(torch.tensor(prop, device="cuda"), 250)
+        g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        S1, u1, p1 = g.costs(), g.updated_plan(), g.get_plan()
+        g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        u2 = g.updated_plan()
+    o = oracle.mixed_step(c["rb"], c["oc"], c["dt"], c["T"], c["K"], c["lam"], c["sigma"],
+                          c["seed"], 0, c["q"], c["qd"], c["goal"], c["plane"],
+                          plan0.astype(np.float64), prop.astype(np.float64), 250)
+    assert_costs(S1, o["S"])
+    assert np.abs(u1 - o["ustar"]).max() <= PLAN_TOL
+    assert np.abs(p1 - o["plan_next"]).max() <= PLAN_TOL
+    o2 = oracle_step(c, plan=p1, it=1)  # the next update is plain again
+    assert np.abs(u2 - o2["ustar"]).max() <= PLAN_TOL
+
+
+def test_simulate_matches_the_fp64_model():
+    """The model as a plant (zero-order hold over dt in Euler substeps),
+    with contact, against the oracle's forward dynamics."""
+    import torch
+    c = make_case(2, contact=True, K=64, T=4)
+    rng = np.random.default_rng(4)
+    n, sub = 48, 10
+    recs, taus = [], []
+    for i in range(n):
+        q = f32(c["q"] + rng.normal(0, 0.05, 7))
+        qd = f32(rng.normal(0, 0.3, 7))
+        recs.append(mppi.pack_inputs(q, qd, c["goal"], c["plane"]))
+        taus.append(f32(rng.normal(0, 5, 7)))
+    recs, taus = np.array(recs), np.array(taus, dtype=np.float32)
+    with gpu_controller(c) as g:
+        d_out = torch.zeros(n, 14, device="cuda")
+        g.simulate_device(torch.tensor(recs, device="cuda"), torch.tensor(taus, device="cuda"),
+                          d_out, substeps=sub)
+        g.sync()
+        out = d_out.cpu().numpy()
+    h = c["dt"] / sub
+    for i in range(n):
+        q, qd = recs[i, :7].astype(np.float64), recs[i, 7:14].astype(np.float64)
+        for _ in range(sub):
+            f, tex = oracle.contact(c["rb"], c["oc"], c["plane"], q, qd)
+            qdd = oracle.forward_dynamics(c["rb"], q, qd, taus[i].astype(np.float64) + tex)
+            qd = qd + qdd * h
+            q = q + qd * h
+        assert np.abs(out[i, :7] - q).max() <= 2e-5
+        assert np.abs(out[i, 7:] - qd).max() <= 2e-3
+
+
 def test_time_kernels_leaves_state():
     torch = torch_mod()
     c = make_case(3, contact=True, K=2048, T=18)
