@@ -63,9 +63,13 @@ def parse():
                     help="reference arm: wall-clock budget of the whole run [s]")
     ap.add_argument("--variant", type=int, default=0,
                     help="rollout kernel: 0 library default, 1 unrolled, 2 rolled")
-    ap.add_argument("--mode", default="update", choices=["update", "serve"],
+    ap.add_argument("--mode", default="update", choices=["update", "serve", "learned"],
                     help="update: the headline single-update benchmark; serve: batched "
-                         "serving of 256 problems under Poisson load")
+                         "serving of 256 problems under Poisson load; learned: train the "
+                         "learned proposal and compare it with plain MPPI")
+    ap.add_argument("--pairs", type=int, default=200_000, help="learned mode: training pairs")
+    ap.add_argument("--train-steps", type=int, default=12_000, help="learned mode: Adam steps")
+    ap.add_argument("--episodes", type=int, default=12, help="learned mode: eval episodes")
     ap.add_argument("--rates", default="2000,5000,10000,20000,100000",
                     help="serve mode: arrival rates [updates/s]")
     ap.add_argument("--seconds", type=float, default=2.0, help="serve mode: seconds per rate")
@@ -402,6 +406,49 @@ def run_serve(args, rank, world):
             "points": points}), flush=True)
 
 
+def run_learned(args, rank, world):
+    """Learned proposal: pairs from plain MPPI at K=16384, training on the GPU
+    with the library's BF16 tensor-core kernels, then closed-loop tracking
+    cost and update latency of plain MPPI (K=16384 and fewer samples) and of
+    MPPI with the learned proposal."""
+    import torch
+    from paper_2609_02020_b300 import learned, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cost = synth.cost_free_space()
+    cost["w_pos"] = np.full(3, 100.0)
+    cost["w_ori"] = np.full(3, 10.0)
+    prob = learned.Problem(arm=synth.arm(rank), cost=cost)
+    s = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    X, Y = learned.generate(prob, args.pairs, K=16384, seed=rank, stream=s)
+    t_gen = time.perf_counter() - t0
+    net, info = learned.train(X, Y, steps=args.train_steps, batch=1024, lr=1e-3, stream=s)
+    rows = []
+    for name, K, mk in (
+            [("plain", 16384, lambda K: learned.PlainMPPI(prob, K, seed=5, stream=s))] +
+            [("plain", K, lambda K: learned.PlainMPPI(prob, K, seed=5, stream=s)) for K in (512, 2048, 4096)] +
+            [("learned", K, lambda K: learned.LearnedMPPI(prob, net, K, seed=5, stream=s))
+             for K in (512, 2048, 4096)]):
+        c = mk(K)
+        r = learned.evaluate(prob, c, episodes=args.episodes, steps=150, seed=1, stream=s)
+        c.close()
+        r.pop("tracking_cost_per_episode")
+        rows.append({"controller": name, "K": K, **r})
+    if rank == 0:
+        print(json.dumps({
+            "mode": "learned",
+            "metric": "closed-loop tracking cost and update latency, learned proposal vs plain MPPI",
+            "unit": "cost (mean of W_pos|dp|^2 + W_ori theta^2) / ms", "n_gpus": world,
+            "dtype": "f32 rollouts, bf16 network", "data": "synthetic",
+            "config": {"workload": "7-DoF seeded arm, reachable goals, gravity-compensated start, "
+                                   "T=18 dt=0.01, W_pos=100, W_ori=10, 150-step episodes",
+                       "pairs": args.pairs, "pairs_K": 16384,
+                       "network": "147 -> 3 x 256 GELU -> 126, BF16 mma.sync, FP32 accumulate",
+                       "plain_fallback_fraction": 0.25},
+            "generation_s": t_gen, "training": {k: v for k, v in info.items()},
+            "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -418,6 +465,8 @@ def main():
             run_reference(args, rank, world)
         elif args.mode == "serve":
             run_serve(args, rank, world)
+        elif args.mode == "learned":
+            run_learned(args, rank, world)
         else:
             run_ours(args, rank, world)
     finally:

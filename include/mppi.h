@@ -220,6 +220,10 @@ MPPI_API int mppi_get_updated_plan_device(mppi_t h, float* d_u);
  * again.  Queued on the handle's stream. */
 MPPI_API int mppi_set_proposal_device(mppi_t h, const float* d_prop, int n_plain);
 
+/* Gravity-compensation torque g(q) = h(q, 0) of Eq. 5 (host arrays),
+ * computed on the device by the rollouts' own RNEA. */
+MPPI_API int mppi_gravity_torque(mppi_t h, const float q[7], float tau_out[7]);
+
 /* End-effector pose (p xyz, quaternion wxyz) at joint angles q, computed on
  * the device by the rollouts' own kinematics (host arrays). */
 MPPI_API int mppi_ee_pose(mppi_t h, const float q[7], float pose_out[7]);

@@ -58,8 +58,9 @@ MPPI_API int mppi_mlp_loss_grad(mppi_mlp_t m, const float* d_x, const float* d_y
 MPPI_API int mppi_mlp_train_step(mppi_mlp_t m, const float* d_x, const float* d_y, int n,
                                  float lr, float* loss);
 /* Learned proposal for an MPPI handle: x = (q, qd, goal from d_in [25
- * device floats], the handle's current nominal plan [T][7]) -> the network's
- * plan, installed as the second proposal of the handle's next update with
+ * device floats], the handle's current nominal plan u [T][7]); the network
+ * predicts the correction that plain MPPI would make to u, and u + net(x)
+ * is installed as the second proposal of the handle's next update with
  * n_plain samples kept around the plain warm start (mppi_set_proposal_device;
  * n_plain = 0 samples only around the network's plan).  Queued on the
  * handle's stream; the network's buffers must not be in use by a training

@@ -622,6 +622,24 @@ static __global__ void noise_words_kernel(uint32_t key0, uint32_t key1, uint64_t
   }
 }
 
+// Bias torque at rest, h(q, 0) = g(q) (gravity compensation), one thread.
+static __global__ void gravity_kernel(const __grid_constant__ ProbK P, const float* __restrict__ q_in,
+                                      float* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float q[NJ], qd[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    q[j] = q_in[j];
+    qd[j] = 0.f;
+  }
+  LinkState ls[NJ];
+  EEState ee;
+  forward_sweep(P.rb, q, qd, ls, ee);
+  float h[NJ], M[NJ * (NJ + 1) / 2];
+  backward_sweep(P.rb, qd, ls, h, M);
+  for (int j = 0; j < NJ; ++j) out[j] = h[j];
+}
+
 // End-effector pose at q (one thread): p (3) and R (9, row-major).
 static __global__ void ee_pose_kernel(const __grid_constant__ ProbK P, const float* __restrict__ q_in,
                                float* __restrict__ out) {

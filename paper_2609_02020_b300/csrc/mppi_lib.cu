@@ -712,6 +712,16 @@ int mppi_noise_words(mppi_t h, uint64_t iter, uint32_t k0, int count, uint32_t t
   return MPPI_OK;
 }
 
+int mppi_gravity_torque(mppi_t h, const float q[7], float tau_out[7]) {
+  if (!h || !q || !tau_out) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_misc, q, 7 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  gravity_kernel<<<1, 32, 0, h->stream>>>(h->P, h->d_misc, h->d_misc + 16);
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaMemcpyAsync(tau_out, h->d_misc + 16, 7 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPPI_OK;
+}
+
 int mppi_time_kernels(mppi_t h, const float* d_in, int iters, float* ms_rollout, float* ms_update) {
   if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
   if (!d_in || iters < 1 || !ms_rollout || !ms_update) return fail(h, MPPI_ERR_INVALID_ARG, "bad argument");

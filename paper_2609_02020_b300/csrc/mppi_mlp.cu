@@ -66,7 +66,8 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 }
 
 __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-  asm volatile(
+  // no side effects beyond its outputs: not volatile, so loads may be scheduled around it
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
       "{%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -232,10 +233,104 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, long long n, bf16*
   if (i < n) dst[i] = __float2bfloat16(src[i]);
 }
 
-// x = (q, qd, goal) of the 25-float input record, then the plan [T][7]
-__global__ void assemble_kernel(const float* __restrict__ in, const float* __restrict__ plan,
-                                int nplan, float* __restrict__ x) {
-  for (int i = threadIdx.x; i < 21 + nplan; i += blockDim.x) x[i] = i < 21 ? in[i] : plan[i - 21];
+// Fused inference for one row (the learned proposal of one handle): input
+// assembly (q, qd, goal of the input record, then the nominal plan), the
+// input standardisation, every layer on the tensor cores (the row padded to
+// an m16 tile; each warp owns n8 column tiles) with the same BF16 rounding
+// points as the batched path, and the output de-standardisation; the output
+// is the correction to the nominal plan, so dst = plan + net(x).  One block
+// of 1024 threads (one n8 column tile per warp for 256-wide layers, weight
+// loads of the unrolled K loop in flight together); layer widths <= MAXW.
+constexpr int PROP_THREADS = 1024;
+constexpr int MAXW = 1024;
+
+struct ProposeArgs {
+  const float* in;      // 25-float input record
+  const float* plan;    // nominal plan [7T]
+  int nplan;
+  const bf16* wb;       // BF16 weights, layer l at wb_off[l]
+  const float* p;       // FP32 parameters (biases at boff[l])
+  long long wb_off[MAX_LAYERS + 1], boff[MAX_LAYERS + 1];
+  int dims[MAX_LAYERS + 1];
+  int L;
+  const float *mean_in, *sd_in, *mean_out, *sd_out;
+  float* dst;           // [n_out]
+};
+
+__global__ void __launch_bounds__(PROP_THREADS) propose_kernel(const ProposeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // two activation rows (BF16), row 0 of the m16 tile; rows 1..15 are zero
+  bf16* act0 = reinterpret_cast<bf16*>(smem_raw);
+  bf16* act1 = act0 + MAXW;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const bf16 zero = __float2bfloat16(0.f);
+  const int n0 = a.dims[0];
+  for (int i = tid; i < MAXW; i += PROP_THREADS) {
+    float x = 0.f;
+    if (i < n0) x = ((i < 21 ? a.in[i] : a.plan[i - 21]) - a.mean_in[i]) / a.sd_in[i];
+    act0[i] = i < n0 ? __float2bfloat16(x) : zero;
+    act1[i] = zero;
+  }
+  __syncthreads();
+  bf16* cur = act0;
+  bf16* nxt = act1;
+  for (int l = 1; l <= a.L; ++l) {
+    const int in = a.dims[l - 1], out = a.dims[l];
+    const bf16* W = a.wb + a.wb_off[l];
+    const float* bias = a.p + a.boff[l];
+    const int ntiles = (out + 7) / 8;
+    for (int nt = warp; nt < ntiles; nt += PROP_THREADS / 32) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const int n = nt * 8 + gid;
+      const bf16* Wn = W + static_cast<long long>(n) * in;
+      // chunks of 8 K steps: issue all weight loads of the chunk, then the MMAs
+      for (int kc = 0; kc < in; kc += 128) {
+        uint32_t bfr[8][2];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c = kc + 16 * j + tig * 2;
+          __nv_bfloat162 b0, b1;
+          b0.x = (n < out && c < in) ? Wn[c] : zero;
+          b0.y = (n < out && c + 1 < in) ? Wn[c + 1] : zero;
+          b1.x = (n < out && c + 8 < in) ? Wn[c + 8] : zero;
+          b1.y = (n < out && c + 9 < in) ? Wn[c + 9] : zero;
+          bfr[j][0] = *reinterpret_cast<uint32_t*>(&b0);
+          bfr[j][1] = *reinterpret_cast<uint32_t*>(&b1);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c = kc + 16 * j + tig * 2;
+          if (kc + 16 * j >= in) break;
+          uint32_t af[4];
+          // A: only row 0 (gid == 0) is non-zero
+          af[0] = gid == 0 ? *reinterpret_cast<const uint32_t*>(&cur[c]) : 0u;
+          af[1] = 0u;
+          af[2] = gid == 0 ? *reinterpret_cast<const uint32_t*>(&cur[c + 8]) : 0u;
+          af[3] = 0u;
+          mma_bf16(acc, af, bfr[j]);
+        }
+      }
+      if (gid == 0) {  // c0, c1: row 0, columns 2 tig, 2 tig + 1
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = nt * 8 + tig * 2 + h;
+          if (col >= out) continue;
+          const float z = acc[h] + bias[col];
+          if (l < a.L) nxt[col] = __float2bfloat16(gelu_f(z));
+          else a.dst[col] = a.plan[col] + (z * a.sd_out[col] + a.mean_out[col]);
+        }
+      }
+    }
+    __syncthreads();
+    if (l < a.L) {
+      for (int i = out + tid; i < MAXW && i < ((out + 15) / 16) * 16 + 16; i += PROP_THREADS) nxt[i] = zero;
+      bf16* t = cur;
+      cur = nxt;
+      nxt = t;
+      __syncthreads();
+    }
+  }
 }
 
 int fail(int code, const std::string& msg) {
@@ -265,7 +360,6 @@ struct mppi_mlp_s {
   bf16* hb[MAX_LAYERS + 1] = {};      // BF16 gelu(z) of hidden layers
   bf16 *d0 = nullptr, *d1 = nullptr;  // deltas (ping-pong) [B][max width]
   float* loss = nullptr;
-  float* xin = nullptr;               // [B][n_in] staging for mppi_mlp_propose
 };
 
 namespace {
@@ -410,8 +504,7 @@ int mppi_mlp_create(const mppi_mlp_config* cfg, void* stream, mppi_mlp_t* out) {
       (e = cudaMalloc(&m->xb, sizeof(bf16) * B * cfg->n_in)) != cudaSuccess ||
       (e = cudaMalloc(&m->d0, sizeof(bf16) * B * maxw)) != cudaSuccess ||
       (e = cudaMalloc(&m->d1, sizeof(bf16) * B * maxw)) != cudaSuccess ||
-      (e = cudaMalloc(&m->loss, sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&m->xin, sizeof(float) * B * cfg->n_in)) != cudaSuccess)
+      (e = cudaMalloc(&m->loss, sizeof(float))) != cudaSuccess)
     return bail(e);
   for (int l = 1; l <= m->L; ++l) {
     if ((e = cudaMalloc(&m->z[l], sizeof(float) * B * m->dims[l])) != cudaSuccess) return bail(e);
@@ -445,7 +538,7 @@ int mppi_mlp_destroy(mppi_mlp_t m) {
   if (m->st) cudaStreamSynchronize(m->st);
   cudaFree(m->p); cudaFree(m->g); cudaFree(m->am); cudaFree(m->av); cudaFree(m->wb);
   cudaFree(m->mean_in); cudaFree(m->sd_in); cudaFree(m->mean_out); cudaFree(m->sd_out);
-  cudaFree(m->xb); cudaFree(m->d0); cudaFree(m->d1); cudaFree(m->loss); cudaFree(m->xin);
+  cudaFree(m->xb); cudaFree(m->d0); cudaFree(m->d1); cudaFree(m->loss);
   for (int l = 0; l <= MAX_LAYERS; ++l) {
     cudaFree(m->z[l]);
     cudaFree(m->hb[l]);
@@ -551,25 +644,29 @@ int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain) {
   if (n_plain < 0 || n_plain > mppi_internal_K(h)) return fail(MPPI_ERR_INVALID_ARG, "n_plain must be in 0..K");
   if (m->cfg.n_in != 21 + 7 * T || m->cfg.n_out != 7 * T)
     return fail(MPPI_ERR_INVALID_ARG, "network widths do not match 21 + 7T inputs and 7T outputs");
+  // queued on the handle's stream so that the proposal lands before its next update
   cudaStream_t hs = mppi_internal_stream(h);
-  float* plan = mppi_internal_plan(h);
-  // run on the handle's stream so that the proposal lands before its next update
-  cudaStream_t keep = m->st;
-  m->st = hs;
-  assemble_kernel<<<1, 256, 0, hs>>>(d_in, plan, 7 * T, m->xin);
+  ProposeArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.in = d_in;
+  a.plan = mppi_internal_plan(h);
+  a.nplan = 7 * T;
+  a.wb = m->wb;
+  a.p = m->p;
+  a.L = m->L;
+  for (int l = 0; l <= m->L; ++l) {
+    a.dims[l] = m->dims[l];
+    a.wb_off[l] = static_cast<long long>(m->wb_off[l]);
+    a.boff[l] = static_cast<long long>(m->boff[l]);
+  }
+  a.mean_in = m->mean_in;
+  a.sd_in = m->sd_in;
+  a.mean_out = m->mean_out;
+  a.sd_out = m->sd_out;
+  a.dst = mppi_internal_prop(h);
+  propose_kernel<<<1, PROP_THREADS, 2 * MAXW * sizeof(bf16), hs>>>(a);
   cudaError_t e = cudaGetLastError();
-  const int nin = m->dims[0], nout = m->dims[m->L];
-  if (e == cudaSuccess) {
-    normalize_in_kernel<<<blocks(nin), 256, 0, hs>>>(m->xin, 1, nin, m->mean_in, m->sd_in, m->xb);
-    e = forward_rows(m, 1);
-  }
-  if (e == cudaSuccess) {
-    denormalize_kernel<<<blocks(nout), 256, 0, hs>>>(m->z[m->L], 1, nout, m->mean_out, m->sd_out,
-                                                     mppi_internal_prop(h));
-    e = cudaGetLastError();
-  }
   if (e == cudaSuccess) e = mppi_internal_set_split(h, n_plain);
-  m->st = keep;
   return e == cudaSuccess ? MPPI_OK : fail(MPPI_ERR_CUDA, cudaGetErrorString(e));
 }
 

@@ -120,7 +120,7 @@ EXPORTS = [
     "mppi_rollout_device", "mppi_update_device", "mppi_ee_pose", "mppi_time_kernels",
     "mppi_noise_words", "mppi_step_static", "mppi_last_error", "mppi_version",
     "mppi_simulate_device", "mppi_set_plan_device", "mppi_get_plan_device",
-    "mppi_get_updated_plan_device", "mppi_set_proposal_device",
+    "mppi_get_updated_plan_device", "mppi_set_proposal_device", "mppi_gravity_torque",
     # include/mppi_serve.h
     "mppi_pool_create", "mppi_pool_destroy", "mppi_pool_alloc", "mppi_pool_free",
     "mppi_pool_stats", "mppi_server_create", "mppi_server_destroy", "mppi_server_add_problem",
@@ -178,6 +178,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_get_plan_device": ([H, vp], C.c_int),
         "mppi_get_updated_plan_device": ([H, vp], C.c_int),
         "mppi_set_proposal_device": ([H, vp, C.c_int], C.c_int),
+        "mppi_gravity_torque": ([H, fp, fp], C.c_int),
         "mppi_pool_create": ([C.c_size_t, C.POINTER(C.c_void_p)], C.c_int),
         "mppi_pool_destroy": ([H], C.c_int),
         "mppi_pool_alloc": ([H, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
@@ -400,6 +401,11 @@ class MPPI:
         v = C.c_uint64()
         self._check(self.lib.mppi_get_iter(self.h, C.byref(v)))
         return int(v.value)
+
+    def gravity_torque(self, q) -> np.ndarray:
+        out = np.zeros(7, dtype=np.float32)
+        self._check(self.lib.mppi_gravity_torque(self.h, _fp(_f32(q, NJ)), _fp(out)))
+        return out
 
     def ee_pose(self, q) -> np.ndarray:
         out = np.zeros(7, dtype=np.float32)

@@ -297,6 +297,16 @@ def test_ee_pose_matches_oracle():
             assert np.abs(Rg - Re).max() < 2e-6
 
 
+def test_gravity_torque_matches_oracle():
+    c = make_case(4)
+    with gpu_controller(c) as g:
+        for s in range(5):
+            q = f32(synth.state(70 + s, c["arm"])[0])
+            tau = g.gravity_torque(q)
+            ref = oracle.rnea(c["rb"], q, np.zeros(7), np.zeros(7))
+            assert np.abs(tau - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
 def test_paper_table1_workload():
     """Table I's contact-mode sizes and weights (K=128, T=30, dt=0.006)."""
     cfg = json.load(open(os.path.join(HERE, "golden", "table1_contact.json")))
