@@ -64,7 +64,8 @@ MPPI_API int mppi_mlp_train_step(mppi_mlp_t m, const float* d_x, const float* d_
  * n_plain samples kept around the plain warm start (mppi_set_proposal_device;
  * n_plain = 0 samples only around the network's plan).  Queued on the
  * handle's stream; the network's buffers must not be in use by a training
- * step at the same time.  Needs n_in = 21 + 7T and n_out = 7T. */
+ * step at the same time.  Needs n_in = 21 + 7T and n_out = 7T, at most 3
+ * hidden layers and widths <= 256 (MPPI_ERR_INVALID_ARG otherwise). */
 MPPI_API int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain);
 
 #ifdef __cplusplus

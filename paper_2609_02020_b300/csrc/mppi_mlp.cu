@@ -7,6 +7,7 @@
 // 32-deep K slices staged in shared memory as [row][k] for A and [n][k] for
 // B, and warp-level mma.sync.m16n8k16 (row.col, BF16 in, FP32 accumulate).
 // The epilogue fuses the bias, the GELU and the GELU derivative.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -30,6 +31,7 @@ cudaError_t mppi_internal_set_split(mppi_t h, int k_split);
 namespace {
 
 using bf16 = __nv_bfloat16;
+namespace cg = cooperative_groups;
 
 constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
 constexpr int MAX_LAYERS = 8;
@@ -238,97 +240,118 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, long long n, bf16*
 // input standardisation, every layer on the tensor cores (the row padded to
 // an m16 tile; each warp owns n8 column tiles) with the same BF16 rounding
 // points as the batched path, and the output de-standardisation; the output
-// is the correction to the nominal plan, so dst = plan + net(x).  One block
-// of 1024 threads (one n8 column tile per warp for 256-wide layers, weight
-// loads of the unrolled K loop in flight together); layer widths <= MAXW.
-constexpr int PROP_THREADS = 1024;
-constexpr int MAXW = 1024;
+// is the correction to the nominal plan, so dst = plan + net(x).  The layer's
+// n8 tiles are spread over the warps of PC_BLOCKS blocks so that the weights
+// stream through several SMs, each warp loading all of its weight fragments
+// up front; a cooperative launch's grid barrier separates the layers, whose
+// activations pass through a small global buffer.  Layer widths <= MAXW.
+constexpr int PC_THREADS = 128;
+constexpr int PC_BLOCKS = 8;    // 32 warps: one n8 tile of every layer each
+constexpr int PC_LMAX = 4;      // layers with weights
+constexpr int PC_KMAX = 16;     // k16 steps per layer (widths <= 256)
+constexpr int MAXW = 256;
 
 struct ProposeArgs {
   const float* in;      // 25-float input record
   const float* plan;    // nominal plan [7T]
-  int nplan;
   const bf16* wb;       // BF16 weights, layer l at wb_off[l]
   const float* p;       // FP32 parameters (biases at boff[l])
   long long wb_off[MAX_LAYERS + 1], boff[MAX_LAYERS + 1];
   int dims[MAX_LAYERS + 1];
   int L;
   const float *mean_in, *sd_in, *mean_out, *sd_out;
+  bf16* act;            // [2][MAXW] activations between layers
   float* dst;           // [n_out]
 };
 
-__global__ void __launch_bounds__(PROP_THREADS) propose_kernel(const ProposeArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // two activation rows (BF16), row 0 of the m16 tile; rows 1..15 are zero
-  bf16* act0 = reinterpret_cast<bf16*>(smem_raw);
-  bf16* act1 = act0 + MAXW;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// B fragments (W[n][k] pairs along k) of one n8 tile for k16 step j.
+__device__ __forceinline__ void load_wfrag(const bf16* W, int in, int out, int n, int j, int tig,
+                                           uint32_t b[2]) {
+  const bf16 zero = __float2bfloat16(0.f);
+  const int c = 16 * j + tig * 2;
+  const bf16* Wn = W + static_cast<long long>(n) * in;
+  if ((in % 2) == 0 && n < out && c + 9 < in) {  // rows start 4-byte aligned
+    b[0] = *reinterpret_cast<const uint32_t*>(Wn + c);
+    b[1] = *reinterpret_cast<const uint32_t*>(Wn + c + 8);
+  } else {
+    __nv_bfloat162 b0, b1;
+    b0.x = (n < out && c < in) ? Wn[c] : zero;
+    b0.y = (n < out && c + 1 < in) ? Wn[c + 1] : zero;
+    b1.x = (n < out && c + 8 < in) ? Wn[c + 8] : zero;
+    b1.y = (n < out && c + 9 < in) ? Wn[c + 9] : zero;
+    b[0] = *reinterpret_cast<uint32_t*>(&b0);
+    b[1] = *reinterpret_cast<uint32_t*>(&b1);
+  }
+}
+
+__global__ void __launch_bounds__(PC_THREADS) propose_kernel(const ProposeArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ __align__(16) bf16 xin[MAXW];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int gw = blockIdx.x * (PC_THREADS / 32) + (tid >> 5);  // this warp's n8 tile
   const int gid = lane >> 2, tig = lane & 3;
   const bf16 zero = __float2bfloat16(0.f);
+  const int n = gw * 8 + gid;
+  // every weight fragment this warp needs, all layers, loaded before any
+  // arithmetic: one memory latency for the whole network
+  uint32_t wf[PC_LMAX][PC_KMAX][2];
+#pragma unroll
+  for (int l = 0; l < PC_LMAX; ++l)
+#pragma unroll
+    for (int j = 0; j < PC_KMAX; ++j) {
+      if (l < a.L && 16 * j < a.dims[l]) {
+        load_wfrag(a.wb + a.wb_off[l + 1], a.dims[l], a.dims[l + 1], n, j, tig, wf[l][j]);
+      } else {
+        wf[l][j][0] = 0u;
+        wf[l][j][1] = 0u;
+      }
+    }
+  bf16* cur = a.act;
+  bf16* nxt = a.act + MAXW;
   const int n0 = a.dims[0];
-  for (int i = tid; i < MAXW; i += PROP_THREADS) {
+  for (int i = blockIdx.x * PC_THREADS + tid; i < MAXW; i += gridDim.x * PC_THREADS) {
     float x = 0.f;
     if (i < n0) x = ((i < 21 ? a.in[i] : a.plan[i - 21]) - a.mean_in[i]) / a.sd_in[i];
-    act0[i] = i < n0 ? __float2bfloat16(x) : zero;
-    act1[i] = zero;
+    cur[i] = i < n0 ? __float2bfloat16(x) : zero;
+    nxt[i] = zero;
   }
-  __syncthreads();
-  bf16* cur = act0;
-  bf16* nxt = act1;
-  for (int l = 1; l <= a.L; ++l) {
-    const int in = a.dims[l - 1], out = a.dims[l];
-    const bf16* W = a.wb + a.wb_off[l];
-    const float* bias = a.p + a.boff[l];
-    const int ntiles = (out + 7) / 8;
-    for (int nt = warp; nt < ntiles; nt += PROP_THREADS / 32) {
+  grid.sync();
+#pragma unroll
+  for (int l = 0; l < PC_LMAX; ++l) {
+    if (l >= a.L) break;
+    const int in = a.dims[l], out = a.dims[l + 1];
+    for (int i = tid; i < MAXW; i += PC_THREADS) xin[i] = cur[i];
+    __syncthreads();
+    if (gw * 8 < out) {
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      const int n = nt * 8 + gid;
-      const bf16* Wn = W + static_cast<long long>(n) * in;
-      // chunks of 8 K steps: issue all weight loads of the chunk, then the MMAs
-      for (int kc = 0; kc < in; kc += 128) {
-        uint32_t bfr[8][2];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int c = kc + 16 * j + tig * 2;
-          __nv_bfloat162 b0, b1;
-          b0.x = (n < out && c < in) ? Wn[c] : zero;
-          b0.y = (n < out && c + 1 < in) ? Wn[c + 1] : zero;
-          b1.x = (n < out && c + 8 < in) ? Wn[c + 8] : zero;
-          b1.y = (n < out && c + 9 < in) ? Wn[c + 9] : zero;
-          bfr[j][0] = *reinterpret_cast<uint32_t*>(&b0);
-          bfr[j][1] = *reinterpret_cast<uint32_t*>(&b1);
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int c = kc + 16 * j + tig * 2;
-          if (kc + 16 * j >= in) break;
-          uint32_t af[4];
-          // A: only row 0 (gid == 0) is non-zero
-          af[0] = gid == 0 ? *reinterpret_cast<const uint32_t*>(&cur[c]) : 0u;
-          af[1] = 0u;
-          af[2] = gid == 0 ? *reinterpret_cast<const uint32_t*>(&cur[c + 8]) : 0u;
-          af[3] = 0u;
-          mma_bf16(acc, af, bfr[j]);
-        }
+      for (int j = 0; j < PC_KMAX; ++j) {
+        if (16 * j >= in) break;
+        const int c = 16 * j + tig * 2;
+        uint32_t af[4];  // A: only row 0 (gid == 0) is non-zero
+        af[0] = gid == 0 ? *reinterpret_cast<const uint32_t*>(&xin[c]) : 0u;
+        af[1] = 0u;
+        af[2] = gid == 0 ? *reinterpret_cast<const uint32_t*>(&xin[c + 8]) : 0u;
+        af[3] = 0u;
+        mma_bf16(acc, af, wf[l][j]);
       }
       if (gid == 0) {  // c0, c1: row 0, columns 2 tig, 2 tig + 1
+        const float* bias = a.p + a.boff[l + 1];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int col = nt * 8 + tig * 2 + h;
+          const int col = gw * 8 + tig * 2 + h;
           if (col >= out) continue;
           const float z = acc[h] + bias[col];
-          if (l < a.L) nxt[col] = __float2bfloat16(gelu_f(z));
+          if (l + 1 < a.L) nxt[col] = __float2bfloat16(gelu_f(z));
           else a.dst[col] = a.plan[col] + (z * a.sd_out[col] + a.mean_out[col]);
         }
       }
     }
-    __syncthreads();
-    if (l < a.L) {
-      for (int i = out + tid; i < MAXW && i < ((out + 15) / 16) * 16 + 16; i += PROP_THREADS) nxt[i] = zero;
+    if (l + 1 < a.L) {
+      grid.sync();
       bf16* t = cur;
       cur = nxt;
       nxt = t;
-      __syncthreads();
     }
   }
 }
@@ -360,6 +383,7 @@ struct mppi_mlp_s {
   bf16* hb[MAX_LAYERS + 1] = {};      // BF16 gelu(z) of hidden layers
   bf16 *d0 = nullptr, *d1 = nullptr;  // deltas (ping-pong) [B][max width]
   float* loss = nullptr;
+  bf16* pact = nullptr;               // [2][MAXW] activations of mppi_mlp_propose
 };
 
 namespace {
@@ -504,7 +528,8 @@ int mppi_mlp_create(const mppi_mlp_config* cfg, void* stream, mppi_mlp_t* out) {
       (e = cudaMalloc(&m->xb, sizeof(bf16) * B * cfg->n_in)) != cudaSuccess ||
       (e = cudaMalloc(&m->d0, sizeof(bf16) * B * maxw)) != cudaSuccess ||
       (e = cudaMalloc(&m->d1, sizeof(bf16) * B * maxw)) != cudaSuccess ||
-      (e = cudaMalloc(&m->loss, sizeof(float))) != cudaSuccess)
+      (e = cudaMalloc(&m->loss, sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&m->pact, sizeof(bf16) * 2 * MAXW)) != cudaSuccess)
     return bail(e);
   for (int l = 1; l <= m->L; ++l) {
     if ((e = cudaMalloc(&m->z[l], sizeof(float) * B * m->dims[l])) != cudaSuccess) return bail(e);
@@ -538,7 +563,7 @@ int mppi_mlp_destroy(mppi_mlp_t m) {
   if (m->st) cudaStreamSynchronize(m->st);
   cudaFree(m->p); cudaFree(m->g); cudaFree(m->am); cudaFree(m->av); cudaFree(m->wb);
   cudaFree(m->mean_in); cudaFree(m->sd_in); cudaFree(m->mean_out); cudaFree(m->sd_out);
-  cudaFree(m->xb); cudaFree(m->d0); cudaFree(m->d1); cudaFree(m->loss);
+  cudaFree(m->xb); cudaFree(m->d0); cudaFree(m->d1); cudaFree(m->loss); cudaFree(m->pact);
   for (int l = 0; l <= MAX_LAYERS; ++l) {
     cudaFree(m->z[l]);
     cudaFree(m->hb[l]);
@@ -642,6 +667,9 @@ int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain) {
   if (!m || !h || !d_in) return fail(MPPI_ERR_INVALID_ARG, "null argument");
   const int T = mppi_internal_T(h);
   if (n_plain < 0 || n_plain > mppi_internal_K(h)) return fail(MPPI_ERR_INVALID_ARG, "n_plain must be in 0..K");
+  if (m->L > PC_LMAX) return fail(MPPI_ERR_INVALID_ARG, "propose supports at most 3 hidden layers");
+  for (int l = 0; l <= m->L; ++l)
+    if (m->dims[l] > MAXW) return fail(MPPI_ERR_INVALID_ARG, "propose supports layer widths <= 256");
   if (m->cfg.n_in != 21 + 7 * T || m->cfg.n_out != 7 * T)
     return fail(MPPI_ERR_INVALID_ARG, "network widths do not match 21 + 7T inputs and 7T outputs");
   // queued on the handle's stream so that the proposal lands before its next update
@@ -650,7 +678,6 @@ int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain) {
   std::memset(&a, 0, sizeof a);
   a.in = d_in;
   a.plan = mppi_internal_plan(h);
-  a.nplan = 7 * T;
   a.wb = m->wb;
   a.p = m->p;
   a.L = m->L;
@@ -663,9 +690,12 @@ int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain) {
   a.sd_in = m->sd_in;
   a.mean_out = m->mean_out;
   a.sd_out = m->sd_out;
+  a.act = m->pact;
   a.dst = mppi_internal_prop(h);
-  propose_kernel<<<1, PROP_THREADS, 2 * MAXW * sizeof(bf16), hs>>>(a);
-  cudaError_t e = cudaGetLastError();
+  if (!a.dst || !a.act) return fail(MPPI_ERR_INVALID_ARG, "proposal buffers missing");
+  void* kargs[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(propose_kernel),
+                                              dim3(PC_BLOCKS), dim3(PC_THREADS), kargs, 0, hs);
   if (e == cudaSuccess) e = mppi_internal_set_split(h, n_plain);
   return e == cudaSuccess ? MPPI_OK : fail(MPPI_ERR_CUDA, cudaGetErrorString(e));
 }
