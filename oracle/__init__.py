@@ -79,6 +79,10 @@ class Cost(C.Structure):
         ("contact", C.c_int),
         ("k_contact", C.c_double),
         ("d_contact", C.c_double),
+        ("force_estimate", C.c_int),
+        ("w_force6", C.c_double * 6),
+        ("f_des6", C.c_double * 6),
+        ("w_reg6", C.c_double * 6),
     ]
 
 
@@ -128,6 +132,10 @@ def _declare(L):
     L.orc_cholesky_solve.restype = C.c_int
     L.orc_forward_dynamics.argtypes = [RP, _dp, _dp, _dp, C.c_int, _dp]
     L.orc_forward_dynamics.restype = C.c_int
+    L.orc_force_estimate.argtypes = [RP, _dp, _dp, _dp]
+    L.orc_force_estimate.restype = C.c_int
+    L.orc_force_estimate_cost.argtypes = [RP, CP, _dp, _dp]
+    L.orc_force_estimate_cost.restype = C.c_double
     L.orc_contact.argtypes = [RP, CP, _dp, _dp, _dp, _dp]
     L.orc_contact.restype = C.c_double
     L.orc_so3_log.argtypes = [_dp, _dp]
@@ -227,6 +235,12 @@ def make_cost(d: dict) -> Cost:
     c.contact = int(d.get("contact", 0))
     c.k_contact = float(d.get("k_contact", 0.0))
     c.d_contact = float(d.get("d_contact", 0.0))
+    c.force_estimate = int(d.get("force_estimate", 0))
+    for name in ("w_force6", "f_des6", "w_reg6"):
+        v = np.asarray(d.get(name, np.zeros(6)), dtype=np.float64).reshape(6)
+        dst = getattr(c, name)
+        for a in range(6):
+            dst[a] = v[a]
     return c
 
 
@@ -363,6 +377,20 @@ def joint_cost(robot: Robot, cost: Cost, q, qd, v):
     n = robot.n
     return lib().orc_joint_cost(C.byref(robot), C.byref(cost), _p(_arr(q, n)), _p(_arr(qd, n)),
                                 _p(_arr(v, n)))
+
+
+def force_estimate(robot: Robot, q, v):
+    """Wrench estimate F_ee = Jbar^T (v - g(q)) (Eq. 13) -> (rc, F[6])."""
+    n = robot.n
+    F = np.zeros(6)
+    rc = lib().orc_force_estimate(C.byref(robot), _p(_arr(q, n)), _p(_arr(v, n)), _p(F))
+    return rc, F
+
+
+def force_estimate_cost(robot: Robot, cost: Cost, q, v):
+    n = robot.n
+    return lib().orc_force_estimate_cost(C.byref(robot), C.byref(cost), _p(_arr(q, n)),
+                                         _p(_arr(v, n)))
 
 
 def stage_cost(robot: Robot, cost: Cost, goal, plane, q, qd, v):

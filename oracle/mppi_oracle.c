@@ -73,6 +73,11 @@ typedef struct {
   double w_terminal;            /* phi(x_T) = w_terminal * C_motion(x_T)       */
   int contact;                  /* 0: free space, 1: plane spring-damper      */
   double k_contact, d_contact;  /* N/m, N s/m                                  */
+  /* Eq. 12-13 with the wrench estimate F_ee = Jbar^T (v - g(q)): when set,
+   * C_force uses these diagonal 6-axis weights on F_ee = (force; moment)
+   * instead of the contact normal force.                                    */
+  int force_estimate;
+  double w_force6[6], f_des6[6], w_reg6[6];
 } orc_cost;
 
 /* ------------------------------------------------------------------------ */
@@ -672,14 +677,78 @@ double orc_joint_cost(const orc_robot* rb, const orc_cost* c, const double* q, c
   return s;
 }
 
-/* Running cost l(x_{t+1}, v_t) = C_motion + C_force + C_joint (Eq. 9-12, 14). */
+/* End-effector wrench estimate of Eq. 12-13: F_ee = Jbar^T tau with the
+ * dynamically consistent generalised inverse Jbar = M^-1 J^T (J M^-1 J^T)^-1
+ * (Khatib 1987), so F_ee = Lambda J M^-1 tau with Lambda = (J M^-1 J^T)^-1.
+ * Reading of the torque: tau = v - g(q), the input net of the gravity torque
+ * g(q) = RNEA(q, 0, 0); M = CRBA + diag(armature); J is the world-frame
+ * geometric Jacobian of the end-effector point, so F = (force xyz; moment
+ * about the end-effector point xyz) in the world frame.  Each step is the
+ * definition written out: the columns of M^-1 J^T and M^-1 tau by Cholesky
+ * solves, then the 6x6 solve.  Returns -1 when M or J M^-1 J^T is not
+ * positive definite (a kinematic singularity), with F set to NaN. */
+int orc_force_estimate(const orc_robot* rb, const double* q, const double* v, double F[6]) {
+  int n = rb->n;
+  double M[NMAX * NMAX], J[6 * NMAX], g[NMAX], zero[NMAX] = {0}, tau[NMAX];
+  for (int a = 0; a < 6; a++) F[a] = NAN;
+  orc_crba(rb, q, M);
+  for (int j = 0; j < n; j++) M[j * n + j] += rb->armature[j];
+  orc_jacobian(rb, q, J);
+  orc_rnea(rb, q, zero, zero, g);
+  for (int j = 0; j < n; j++) tau[j] = v[j] - g[j];
+  /* X = M^-1 J^T, column by column (column a is M^-1 times row a of J) */
+  double X[NMAX][6], col[NMAX], x[NMAX];
+  for (int a = 0; a < 6; a++) {
+    for (int j = 0; j < n; j++) col[j] = J[a * n + j];
+    if (orc_cholesky_solve(n, M, col, x) != 0) return -1;
+    for (int j = 0; j < n; j++) X[j][a] = x[j];
+  }
+  /* Lambda^-1 = J M^-1 J^T and the task acceleration J M^-1 tau */
+  double A[36], b[6], y[NMAX];
+  for (int a = 0; a < 6; a++)
+    for (int c2 = 0; c2 < 6; c2++) {
+      double s = 0.0;
+      for (int j = 0; j < n; j++) s += J[a * n + j] * X[j][c2];
+      A[a * 6 + c2] = s;
+    }
+  if (orc_cholesky_solve(n, M, tau, y) != 0) return -1;
+  for (int a = 0; a < 6; a++) {
+    double s = 0.0;
+    for (int j = 0; j < n; j++) s += J[a * n + j] * y[j];
+    b[a] = s;
+  }
+  double Fx[6];
+  if (orc_cholesky_solve(6, A, b, Fx) != 0) return -1;
+  for (int a = 0; a < 6; a++) F[a] = Fx[a];
+  return 0;
+}
+
+/* C_force of Eq. 12 on the wrench estimate: diagonal W_force and W_reg over
+ * the six axes, sum_a w_force6[a] (f_des6[a] - F[a])^2 + w_reg6[a] F[a]^2,
+ * charged at the configuration q_t where the input v_t acts.  NaN at a
+ * kinematic singularity. */
+double orc_force_estimate_cost(const orc_robot* rb, const orc_cost* c, const double* q,
+                               const double* v) {
+  double F[6];
+  if (orc_force_estimate(rb, q, v, F) != 0) return NAN;
+  double s = 0.0;
+  for (int a = 0; a < 6; a++) {
+    double e = c->f_des6[a] - F[a];
+    s += c->w_force6[a] * e * e + c->w_reg6[a] * F[a] * F[a];
+  }
+  return s;
+}
+
+/* Running cost l(x_{t+1}, v_t) = C_motion + C_force + C_joint (Eq. 9-12, 14).
+ * With force_estimate set, C_force is the wrench-estimate term, which
+ * orc_rollout adds at (q_t, v_t); this function then leaves C_force out. */
 double orc_stage_cost(const orc_robot* rb, const orc_cost* c, const double goal[7],
                       const double plane[4], const double* q, const double* qd,
                       const double* v) {
   double R[NMAX][3][3], p[NMAX][3], Re[3][3], pe[3];
   orc_fk(rb, q, R, p, Re, pe);
   double s = orc_motion_cost(c, goal, pe, Re);
-  if (c->contact) {
+  if (c->contact && !c->force_estimate) {
     double f = orc_contact(rb, c, plane, q, qd, NULL);
     double e = c->f_des - f;
     s += c->w_force * e * e + c->w_reg * f * f;
@@ -693,7 +762,8 @@ double orc_stage_cost(const orc_robot* rb, const orc_cost* c, const double goal[
 
 /* One rollout k (Eq. 1-3 with Eq. 5-7): for t = 0..T-1 the noisy torque
  * v_t = u_t + dtau_{k,t} acts on x_t and gives x_{t+1}; l is charged on
- * (x_{t+1}, v_t); the terminal cost is w_terminal * C_motion(x_T).
+ * (x_{t+1}, v_t), the wrench-estimate C_force (when set) on (q_t, v_t); the
+ * terminal cost is w_terminal * C_motion(x_T).
  * noise_out (T*n, [t][j]) receives dtau when not NULL.  Returns S_k. */
 double orc_rollout(const orc_robot* rb, const orc_cost* c, double dt, int T, const double* sigma,
                    uint64_t seed, uint64_t iter, uint32_t k, const double* q0, const double* qd0,
@@ -712,6 +782,7 @@ double orc_rollout(const orc_robot* rb, const orc_cost* c, double dt, int T, con
       if (noise_out) noise_out[t * n + j] = du;
       v[j] = plan[t * n + j] + du;
     }
+    if (c->force_estimate) S += orc_force_estimate_cost(rb, c, q, v);
     for (int j = 0; j < n; j++) tex[j] = 0.0;
     if (c->contact) orc_contact(rb, c, plane, q, qd, tex);
     for (int j = 0; j < n; j++) tau[j] = v[j] + tex[j];
