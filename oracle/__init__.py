@@ -83,6 +83,13 @@ class Cost(C.Structure):
         ("w_force6", C.c_double * 6),
         ("f_des6", C.c_double * 6),
         ("w_reg6", C.c_double * 6),
+        ("collision", C.c_int),
+        ("w_collision", C.c_double),
+        ("d_th_self", C.c_double),
+        ("d_th_obs", C.c_double),
+        ("link_radius", C.c_double * NMAX),
+        ("n_obs", C.c_int),
+        ("obs", C.c_double * 7 * 8),
     ]
 
 
@@ -136,6 +143,13 @@ def _declare(L):
     L.orc_force_estimate.restype = C.c_int
     L.orc_force_estimate_cost.argtypes = [RP, CP, _dp, _dp]
     L.orc_force_estimate_cost.restype = C.c_double
+    L.orc_segment_distance.argtypes = [_dp, _dp, _dp, _dp]
+    L.orc_segment_distance.restype = C.c_double
+    L.orc_link_points.argtypes = [RP, _dp, _dp]
+    L.orc_collision_distances.argtypes = [RP, CP, _dp, _dp]
+    L.orc_collision_distances.restype = C.c_int
+    L.orc_collision_cost.argtypes = [RP, CP, _dp]
+    L.orc_collision_cost.restype = C.c_double
     L.orc_contact.argtypes = [RP, CP, _dp, _dp, _dp, _dp]
     L.orc_contact.restype = C.c_double
     L.orc_so3_log.argtypes = [_dp, _dp]
@@ -241,6 +255,19 @@ def make_cost(d: dict) -> Cost:
         dst = getattr(c, name)
         for a in range(6):
             dst[a] = v[a]
+    c.collision = int(d.get("collision", 0))
+    for name in ("w_collision", "d_th_self", "d_th_obs"):
+        setattr(c, name, float(d.get(name, 0.0)))
+    lr = np.asarray(d.get("link_radius", np.zeros(NMAX)), dtype=np.float64)
+    for j in range(min(NMAX, lr.size)):
+        c.link_radius[j] = lr[j]
+    obs = np.asarray(d.get("obstacles", np.zeros((0, 7))), dtype=np.float64).reshape(-1, 7)
+    if obs.shape[0] > 8:
+        raise ValueError("at most 8 obstacles")
+    c.n_obs = obs.shape[0]
+    for o in range(obs.shape[0]):
+        for a in range(7):
+            c.obs[o][a] = obs[o, a]
     return c
 
 
@@ -391,6 +418,27 @@ def force_estimate_cost(robot: Robot, cost: Cost, q, v):
     n = robot.n
     return lib().orc_force_estimate_cost(C.byref(robot), C.byref(cost), _p(_arr(q, n)),
                                          _p(_arr(v, n)))
+
+
+def segment_distance(p1, q1, p2, q2):
+    return lib().orc_segment_distance(_p(_arr(p1, 3)), _p(_arr(q1, 3)), _p(_arr(p2, 3)),
+                                      _p(_arr(q2, 3)))
+
+
+def link_points(robot: Robot, q):
+    P = np.zeros((NMAX + 1, 3))
+    lib().orc_link_points(C.byref(robot), _p(_arr(q, robot.n)), _p(P))
+    return P[: robot.n + 1]
+
+
+def collision_distances(robot: Robot, cost: Cost, q):
+    d = np.zeros(NMAX * NMAX + NMAX * 8)
+    m = lib().orc_collision_distances(C.byref(robot), C.byref(cost), _p(_arr(q, robot.n)), _p(d))
+    return d[:m]
+
+
+def collision_cost(robot: Robot, cost: Cost, q):
+    return lib().orc_collision_cost(C.byref(robot), C.byref(cost), _p(_arr(q, robot.n)))
 
 
 def stage_cost(robot: Robot, cost: Cost, goal, plane, q, qd, v):

@@ -78,6 +78,17 @@ typedef struct {
    * instead of the contact normal force.                                    */
   int force_estimate;
   double w_force6[6], f_des6[6], w_reg6[6];
+  /* Eq. 15 collision cost over link capsules: link i is the segment from
+   * joint i's origin to joint i+1's (the last ends at the end-effector
+   * point) with radius link_radius[i]; obstacles are capsules
+   * (a xyz, b xyz, radius); pairs are links at least two apart and every
+   * link with every obstacle.  collision: 0 off, 1 indicator (Eq. 15),
+   * 2 squared hinge w * max(0, d_th - d)^2 (a smooth reading).          */
+  int collision;
+  double w_collision, d_th_self, d_th_obs;
+  double link_radius[NMAX];
+  int n_obs;
+  double obs[8][7];
 } orc_cost;
 
 /* ------------------------------------------------------------------------ */
@@ -739,8 +750,98 @@ double orc_force_estimate_cost(const orc_robot* rb, const orc_cost* c, const dou
   return s;
 }
 
-/* Running cost l(x_{t+1}, v_t) = C_motion + C_force + C_joint (Eq. 9-12, 14).
- * With force_estimate set, C_force is the wrench-estimate term, which
+/* Minimum distance between the segments [p1, q1] and [p2, q2] (the
+ * quantity Lumelsky's method computes for Eq. 15).  Written as the
+ * definition: the squared distance |p1 + s d1 - p2 - t d2|^2 is a convex
+ * quadratic on the square (s, t) in [0, 1]^2, so its minimum is either the
+ * stationary point, when that lies inside the square, or on one of the four
+ * edges, each of which is an endpoint against the other segment (a clamped
+ * projection).  Every candidate is evaluated; the least is returned. */
+static double point_segment_dist2(const double x[3], const double a[3], const double b[3]) {
+  double d[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double w[3] = {x[0] - a[0], x[1] - a[1], x[2] - a[2]};
+  double dd = v3_dot(d, d);
+  double u = dd > 0.0 ? v3_dot(w, d) / dd : 0.0;
+  if (u < 0.0) u = 0.0;
+  if (u > 1.0) u = 1.0;
+  double e[3] = {w[0] - u * d[0], w[1] - u * d[1], w[2] - u * d[2]};
+  return v3_dot(e, e);
+}
+
+double orc_segment_distance(const double p1[3], const double q1[3], const double p2[3],
+                            const double q2[3]) {
+  double best = point_segment_dist2(p1, p2, q2);
+  double c;
+  if ((c = point_segment_dist2(q1, p2, q2)) < best) best = c;
+  if ((c = point_segment_dist2(p2, p1, q1)) < best) best = c;
+  if ((c = point_segment_dist2(q2, p1, q1)) < best) best = c;
+  double d1[3] = {q1[0] - p1[0], q1[1] - p1[1], q1[2] - p1[2]};
+  double d2[3] = {q2[0] - p2[0], q2[1] - p2[1], q2[2] - p2[2]};
+  double r[3] = {p1[0] - p2[0], p1[1] - p2[1], p1[2] - p2[2]};
+  double a = v3_dot(d1, d1), b = v3_dot(d1, d2), e = v3_dot(d2, d2);
+  double det = a * e - b * b;
+  if (det > 1e-14 * a * e) {
+    /* stationary point: a s - b t = -d1.r, b s - e t = -d2.r */
+    double f1 = -v3_dot(d1, r), f2 = -v3_dot(d2, r);
+    double det2 = b * b - a * e; /* determinant of [[a, -b], [b, -e]] */
+    double s_ = (b * f2 - e * f1) / det2;
+    double t_ = (a * f2 - b * f1) / det2;
+    if (s_ >= 0.0 && s_ <= 1.0 && t_ >= 0.0 && t_ <= 1.0) {
+      double g[3];
+      for (int k = 0; k < 3; k++) g[k] = r[k] + s_ * d1[k] - t_ * d2[k];
+      if ((c = v3_dot(g, g)) < best) best = c;
+    }
+  }
+  return sqrt(best);
+}
+
+/* End points of the link segments at q: P[i] = origin of joint i for
+ * i < n, P[n] = the end-effector point; link i spans P[i] .. P[i+1]. */
+void orc_link_points(const orc_robot* rb, const double* q, double P[][3]) {
+  double R[NMAX][3][3], p[NMAX][3], Re[3][3], pe[3];
+  orc_fk(rb, q, R, p, Re, pe);
+  for (int i = 0; i < rb->n; i++) memcpy(P[i], p[i], sizeof(double) * 3);
+  memcpy(P[rb->n], pe, sizeof(double) * 3);
+}
+
+/* Signed clearances d_i (segment distance minus both radii) of the
+ * collision pairs in a fixed order: self pairs (i, j), j >= i + 2, by i then
+ * j, then link i against obstacle o, by i then o.  Returns the count. */
+int orc_collision_distances(const orc_robot* rb, const orc_cost* c, const double* q, double* d) {
+  int n = rb->n, m = 0;
+  double P[NMAX + 1][3];
+  orc_link_points(rb, q, P);
+  for (int i = 0; i < n; i++)
+    for (int j = i + 2; j < n; j++)
+      d[m++] = orc_segment_distance(P[i], P[i + 1], P[j], P[j + 1]) - c->link_radius[i] -
+               c->link_radius[j];
+  for (int i = 0; i < n; i++)
+    for (int o = 0; o < c->n_obs; o++)
+      d[m++] = orc_segment_distance(P[i], P[i + 1], c->obs[o], c->obs[o] + 3) -
+               c->link_radius[i] - c->obs[o][6];
+  return m;
+}
+
+/* C_collision of Eq. 15 at configuration q. */
+double orc_collision_cost(const orc_robot* rb, const orc_cost* c, const double* q) {
+  double d[NMAX * NMAX + NMAX * 8];
+  int n = rb->n, m = orc_collision_distances(rb, c, q, d);
+  int n_self = 0;
+  for (int i = 0; i < n; i++)
+    for (int j = i + 2; j < n; j++) n_self++;
+  double s = 0.0;
+  for (int k = 0; k < m; k++) {
+    double th = k < n_self ? c->d_th_self : c->d_th_obs;
+    if (c->collision == 1)
+      s += d[k] < th ? 1.0 : 0.0;
+    else
+      s += d[k] < th ? (th - d[k]) * (th - d[k]) : 0.0;
+  }
+  return c->w_collision * s;
+}
+
+/* Running cost l(x_{t+1}, v_t) = C_motion + C_force + C_joint + C_collision
+ * (Eq. 9-12, 14-15).  With force_estimate set, C_force is the wrench-estimate term, which
  * orc_rollout adds at (q_t, v_t); this function then leaves C_force out. */
 double orc_stage_cost(const orc_robot* rb, const orc_cost* c, const double goal[7],
                       const double plane[4], const double* q, const double* qd,
@@ -754,6 +855,7 @@ double orc_stage_cost(const orc_robot* rb, const orc_cost* c, const double goal[
     s += c->w_force * e * e + c->w_reg * f * f;
   }
   s += orc_joint_cost(rb, c, q, qd, v);
+  if (c->collision) s += orc_collision_cost(rb, c, q);
   return s;
 }
 
