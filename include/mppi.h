@@ -100,7 +100,18 @@ typedef struct mppi_robot {
  *   phi(x_T) = w_terminal C_motion(x_T).
  * Contact (contact != 0): penetration delta = d - n . p_ee; when delta > 0,
  * f = max(0, k_contact delta - d_contact n . v_ee), else 0; the wrench
- * (f n, 0) enters the dynamics as tau_ext = J^T F_ext (Eq. 5). */
+ * (f n, 0) enters the dynamics as tau_ext = J^T F_ext (Eq. 5).
+ * Wrench estimate (force_estimate != 0; Eq. 12-13): C_force becomes
+ *   sum_a w_force6[a] (f_des6[a] - F_a)^2 + w_reg6[a] F_a^2,
+ *   F = Jbar^T (v_t - g(q_t)),  Jbar = M^-1 J^T (J M^-1 J^T)^-1,
+ * the end-effector wrench (force xyz; moment about the end-effector point
+ * xyz, world frame) that the input v_t, net of the gravity torque g, exerts
+ * at the configuration q_t where it acts (M with armature, J the geometric
+ * Jacobian of the end-effector point); charged at step t in place of the
+ * contact normal-force term.  A sample that meets a kinematic singularity
+ * (J M^-1 J^T not positive definite) gets a non-finite cost and weight 0.
+ * This cost runs in the rolled rollout kernel (variant 0 selects it;
+ * variant 1 is rejected); mppi_step_static and the server do not take it. */
 typedef struct mppi_cost {
   double w_pos[3], w_ori[3];
   double w_force, f_des, w_reg;
@@ -109,6 +120,8 @@ typedef struct mppi_cost {
   double w_terminal;
   int contact;
   double k_contact, d_contact;
+  int force_estimate;          /* 1: C_force on the wrench estimate below      */
+  double w_force6[6], f_des6[6], w_reg6[6];  /* its weights, (force; moment) */
 } mppi_cost;
 
 /* Problem sizes and sampler parameters (Eq. 2-4). */
@@ -152,9 +165,10 @@ MPPI_API int mppi_step(mppi_t h, const float q[7], const float qd[7], const floa
               const float plane[4], float tau0_out[7], float* plan_out);
 
 /* One MPPI update from device memory, queued on the handle's stream without
- * waiting.  d_in: 25 device floats (q[7], qd[7], goal[7], plane[4]).
+ * waiting.  d_in: 25 device floats (q[7], qd[7], goal[7], plane[4]), read by
+ * the rollouts in place (keep it unchanged until the update has run).
  * d_tau0 (7 floats) and d_plan ([T][7]) receive u*_0 and the shifted plan
- * when not NULL.  The status of the update is read by mppi_sync. */
+ * when not NULL.  The status of the last update is read by mppi_sync. */
 MPPI_API int mppi_step_device(mppi_t h, const float* d_in, float* d_tau0, float* d_plan);
 
 /* Wait for the handle's queued work; returns the status of the last update
@@ -223,6 +237,16 @@ MPPI_API int mppi_set_proposal_device(mppi_t h, const float* d_prop, int n_plain
 /* Gravity-compensation torque g(q) = h(q, 0) of Eq. 5 (host arrays),
  * computed on the device by the rollouts' own RNEA. */
 MPPI_API int mppi_gravity_torque(mppi_t h, const float q[7], float tau_out[7]);
+
+/* End-effector wrench estimates of Eq. 13, F = Jbar^T (v - g(q)), for n
+ * pairs (q_i, v_i) of device arrays d_q, d_v [n][7] into d_F [n][6]
+ * (force xyz; moment about the end-effector point xyz, world frame), by the
+ * rollouts' own kinematics, dynamics and estimate (see mppi_cost).  Rows at
+ * a kinematic singularity (J M^-1 J^T not positive definite) are NaN.
+ * n in 1..MPPI_K_MAX; queued on the handle's stream without waiting; the
+ * arrays are caller-owned and must stay valid until the stream reaches it. */
+MPPI_API int mppi_force_estimate_device(mppi_t h, const float* d_q, const float* d_v, int n,
+                                        float* d_F);
 
 /* End-effector pose (p xyz, quaternion wxyz) at joint angles q, computed on
  * the device by the rollouts' own kinematics (host arrays). */

@@ -49,6 +49,8 @@ struct CostK {
   float wterm;
   int contact;
   float kc, dc;
+  int fest;                            // C_force on the wrench estimate (Eq. 13)
+  float wf6[6], fdes6[6], wreg6[6];    // its diagonal weights, (force; moment)
 };
 
 struct ProbK {
@@ -316,20 +318,21 @@ __device__ __forceinline__ void backward_sweep(const RobotK& rb, const float qd[
   }
 }
 
-// Solve M x = b with M symmetric positive definite (packed lower triangle),
-// by LDL^T.  Overwrites M with the factors.  Every loop has a constant trip
-// count (bounds are guards) so that the factorisation unrolls completely and
-// M stays in registers.
-__device__ __forceinline__ void ldlt_solve(float M[NJ * (NJ + 1) / 2], const float b[NJ],
-                                           float x[NJ]) {
-  float D[NJ], invD[NJ];
+// LDL^T factorisation of an N x N symmetric positive definite matrix in
+// packed lower-triangle storage (M[i(i+1)/2 + j], j <= i): overwrites the
+// strict lower triangle with L (unit diagonal implied) and returns 1/D.
+// Every loop has a constant trip count (bounds are guards) so that the
+// factorisation unrolls completely and M stays in registers.
+template <int N>
+__device__ __forceinline__ void ldlt_factor(float M[N * (N + 1) / 2], float invD[N]) {
+  float D[N];
 #pragma unroll
-  for (int j = 0; j < NJ; ++j) {
+  for (int j = 0; j < N; ++j) {
     // column j: D_j = M_jj - sum_k L_jk^2 D_k ; L_ij = (M_ij - sum_k L_ik L_jk D_k) / D_j
-    float LD[NJ];  // L_jk D_k
+    float LD[N];  // L_jk D_k
     float d = M[j * (j + 1) / 2 + j];
 #pragma unroll
-    for (int k = 0; k < NJ; ++k) {
+    for (int k = 0; k < N; ++k) {
       if (k < j) {
         const float Ljk = M[j * (j + 1) / 2 + k];
         LD[k] = Ljk * D[k];
@@ -339,34 +342,55 @@ __device__ __forceinline__ void ldlt_solve(float M[NJ * (NJ + 1) / 2], const flo
     D[j] = d;
     invD[j] = 1.0f / d;
 #pragma unroll
-    for (int i = 0; i < NJ; ++i) {
+    for (int i = 0; i < N; ++i) {
       if (i > j) {
         float s = M[i * (i + 1) / 2 + j];
 #pragma unroll
-        for (int k = 0; k < NJ; ++k)
+        for (int k = 0; k < N; ++k)
           if (k < j) s = fmaf(-M[i * (i + 1) / 2 + k], LD[k], s);
         M[i * (i + 1) / 2 + j] = s * invD[j];
       }
     }
   }
-  float y[NJ];
+}
+
+// y = L^-1 b for the unit lower factor L of ldlt_factor.
+template <int N>
+__device__ __forceinline__ void unit_lower_solve(const float L[N * (N + 1) / 2], const float b[N],
+                                                 float y[N]) {
 #pragma unroll
-  for (int i = 0; i < NJ; ++i) {
+  for (int i = 0; i < N; ++i) {
     float s = b[i];
 #pragma unroll
-    for (int k = 0; k < NJ; ++k)
-      if (k < i) s = fmaf(-M[i * (i + 1) / 2 + k], y[k], s);
+    for (int k = 0; k < N; ++k)
+      if (k < i) s = fmaf(-L[i * (i + 1) / 2 + k], y[k], s);
     y[i] = s;
   }
+}
+
+// x = L^-T D^-1 y (the second half of an LDL^T solve).
+template <int N>
+__device__ __forceinline__ void ldlt_back(const float L[N * (N + 1) / 2], const float invD[N],
+                                          const float y[N], float x[N]) {
 #pragma unroll
-  for (int ii = 0; ii < NJ; ++ii) {
-    const int i = NJ - 1 - ii;
+  for (int ii = 0; ii < N; ++ii) {
+    const int i = N - 1 - ii;
     float s = y[i] * invD[i];
 #pragma unroll
-    for (int k = 0; k < NJ; ++k)
-      if (k > i) s = fmaf(-M[k * (k + 1) / 2 + i], x[k], s);
+    for (int k = 0; k < N; ++k)
+      if (k > i) s = fmaf(-L[k * (k + 1) / 2 + i], x[k], s);
     x[i] = s;
   }
+}
+
+// Solve M x = b with M symmetric positive definite (packed lower triangle),
+// by LDL^T.  Overwrites M with the factors.
+__device__ __forceinline__ void ldlt_solve(float M[NJ * (NJ + 1) / 2], const float b[NJ],
+                                           float x[NJ]) {
+  float invD[NJ], y[NJ];
+  ldlt_factor<NJ>(M, invD);
+  unit_lower_solve<NJ>(M, b, y);
+  ldlt_back<NJ>(M, invD, y, x);
 }
 
 // ---------------------------------------------------------------------------

@@ -198,8 +198,138 @@ __device__ __forceinline__ void forward_sweep_rolled(const RobotK& rb, const flo
   chain_ee(rb, c, ee);
 }
 
-// sm: this block's work area of ROLLED_FLOATS_PER_THREAD * B floats.
-template <bool STORE_NOISE, int B>
+// Extra per-thread shared floats of the wrench-estimate cost: J^T rows
+// [6][NJ] (overwritten by L^-1 J^T) and the gravity torque g [NJ].
+constexpr int FEST_FLOATS_PER_THREAD = 6 * NJ + NJ;
+
+// Wrench estimate of Eq. 13 at configuration q_t:
+// F = Lambda J M^-1 tau with Lambda = (J M^-1 J^T)^-1, tau = v - g(q_t).
+// With M = L D L^T (ldlt_factor) and Y = L^-1 J^T, J M^-1 J^T = Y^T D^-1 Y
+// and J M^-1 tau = Y^T D^-1 (L^-1 tau); the 6 x 6 system is factorised by
+// LDL^T as well.  J is the geometric Jacobian of the end-effector point p
+// (rows: linear velocity of p, angular velocity), built from the joint axes
+// (z_j, w_j = p_j x z_j) of the forward sweep: the linear row of joint j is
+// w_j + z_j x p.  F = (force; moment about p), world frame.  Returns false
+// when a pivot of the 6 x 6 factorisation is not positive (a kinematic
+// singularity).  sl: link axes at q_t; sg: g(q_t); sY: [6][NJ][B] scratch.
+template <int B>
+__device__ __forceinline__ bool force_estimate(const float* sl, int tid,
+                                               const float L[NJ * (NJ + 1) / 2],
+                                               const float invD[NJ], const float v[NJ],
+                                               const float* sg, const float p[3], float* sY,
+                                               float F[6]) {
+#pragma unroll 1
+  for (int j = 0; j < NJ; ++j) {
+    float z[3], w[3], zp[3];
+    load_axis<B>(sl, j, tid, z, w);
+    cross3(z, p, zp);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      sY[(a * NJ + j) * B + tid] = w[a] + zp[a];
+      sY[((3 + a) * NJ + j) * B + tid] = z[a];
+    }
+  }
+  float tau[NJ], lt[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) tau[j] = v[j] - sg[j * B + tid];
+  unit_lower_solve<NJ>(L, tau, lt);
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) lt[j] *= invD[j];  // D^-1 L^-1 tau
+  float b[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    float jr[NJ], y[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) jr[j] = sY[(r * NJ + j) * B + tid];
+    unit_lower_solve<NJ>(L, jr, y);
+    float br = 0.f;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      sY[(r * NJ + j) * B + tid] = y[j];
+      br = fmaf(y[j], lt[j], br);
+    }
+    b[r] = br;
+  }
+  float A[21];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    float u[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) u[j] = sY[(r * NJ + j) * B + tid] * invD[j];
+#pragma unroll
+    for (int c = 0; c <= r; ++c) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) acc = fmaf(u[j], sY[(c * NJ + j) * B + tid], acc);
+      A[r * (r + 1) / 2 + c] = acc;
+    }
+  }
+  float invDA[6], yb[6];
+  ldlt_factor<6>(A, invDA);
+  unit_lower_solve<6>(A, b, yb);
+  ldlt_back<6>(A, invDA, yb, F);
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) ok = ok && invDA[a] > 0.f && invDA[a] < INFINITY;
+  return ok;
+}
+
+// C_force of Eq. 12 on the wrench estimate (diagonal six-axis weights);
+// NaN at a kinematic singularity, so that the sample gets weight zero.
+template <int B>
+__device__ __forceinline__ float force_estimate_cost(const CostK& C, const float* sl, int tid,
+                                                     const float L[NJ * (NJ + 1) / 2],
+                                                     const float invD[NJ], const float v[NJ],
+                                                     const float* sg, const float p[3],
+                                                     float* sY) {
+  float F[6];
+  const bool ok = force_estimate<B>(sl, tid, L, invD, v, sg, p, sY, F);
+  float cf = 0.f;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const float e = C.fdes6[a] - F[a];
+    cf = fmaf(C.wf6[a], e * e, fmaf(C.wreg6[a], F[a] * F[a], cf));
+  }
+  return ok ? cf : NAN;
+}
+
+// Backward sweep of the rolled kernels: bias torque h -> sh, the packed
+// lower triangle of M (with armature) -> sM and, with FEST, the gravity
+// torque g -> sg, from the link states in sl.
+template <int B, bool FEST>
+__device__ __forceinline__ void backward_sweep_rolled(const RobotK& rb, const float* sl,
+                                                      const float* sqd, float* sh, float* sM,
+                                                      float* sg, int tid) {
+  float Fs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float Ic[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+  for (int ii = 0; ii < NJ; ++ii) {
+    const int i = NJ - 1 - ii;
+    LinkState S;
+    load_link<B>(sl, i, tid, S);
+    float H[3], Lm[3];
+    sh[i * B + tid] = backward_link(rb.L[i], sqd[i * B + tid], S, Fs, Ic, H, Lm);
+    if (FEST) {
+      // gravity torque from the subtree's mass and first moment (Ic[0],
+      // Ic[1..3]): g_i = -S_i . ((m c) x g, m g)
+      float mcg[3];
+      cross3(Ic + 1, rb.g, mcg);
+      sg[i * B + tid] = -(dot3(S.z, mcg) + Ic[0] * dot3(S.w, rb.g));
+    }
+    const int row = i * (i + 1) / 2;
+#pragma unroll 1
+    for (int j = 0; j < i; ++j) {
+      float zj[3], wj[3];
+      load_axis<B>(sl, j, tid, zj, wj);
+      sM[(row + j) * B + tid] = dot3(zj, H) + dot3(wj, Lm);
+    }
+    sM[(row + i) * B + tid] = dot3(S.z, H) + dot3(S.w, Lm) + rb.L[i].arm;
+  }
+}
+
+// sm: this block's work area of ROLLED_FLOATS_PER_THREAD * B floats, plus
+// FEST_FLOATS_PER_THREAD * B floats when FEST is set.
+template <bool STORE_NOISE, int B, bool FEST = false>
 __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const float* in,
                                                        const float* plan, uint64_t iter, int k,
                                                        float* __restrict__ noise, float* sm,
@@ -209,6 +339,8 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
   float* sq = sM + (NJ * (NJ + 1) / 2) * B;         // [7][B]
   float* sqd = sq + NJ * B;                         // [7][B]
   float* sh = sqd + NJ * B;                         // [7][B]
+  float* sY = sh + NJ * B;                          // [6][7][B] (FEST)
+  float* sg = sY + 6 * NJ * B;                      // [7][B]    (FEST)
   const int T = P.T, K = P.K;
   float q[NJ], qd[NJ];
 #pragma unroll
@@ -243,27 +375,8 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
       if (STORE_NOISE) noise[static_cast<size_t>(t * NJ + j) * K + k] = du;
       v[j] = plan[t * NJ + j] + du;
     }
-    // backward sweep: h and M into shared memory
-    {
-      float Fs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      float Ic[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-      for (int ii = 0; ii < NJ; ++ii) {
-        const int i = NJ - 1 - ii;
-        LinkState S;
-        load_link<B>(sl, i, tid, S);
-        float H[3], Lm[3];
-        sh[i * B + tid] = backward_link(P.rb.L[i], sqd[i * B + tid], S, Fs, Ic, H, Lm);
-        const int row = i * (i + 1) / 2;
-#pragma unroll 1
-        for (int j = 0; j < i; ++j) {
-          float zj[3], wj[3];
-          load_axis<B>(sl, j, tid, zj, wj);
-          sM[(row + j) * B + tid] = dot3(zj, H) + dot3(wj, Lm);
-        }
-        sM[(row + i) * B + tid] = dot3(S.z, H) + dot3(S.w, Lm) + P.rb.L[i].arm;
-      }
-    }
+    // backward sweep: h and M (and g) into shared memory
+    backward_sweep_rolled<B, FEST>(P.rb, sl, sqd, sh, sM, sg, tid);
     float M[NJ * (NJ + 1) / 2];
 #pragma unroll
     for (int a = 0; a < NJ * (NJ + 1) / 2; ++a) M[a] = sM[a * B + tid];
@@ -283,7 +396,17 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
       for (int j = 0; j < NJ; ++j) rhs[j] = v[j] - sh[j * B + tid];
     }
     float qdd[NJ];
-    ldlt_solve(M, rhs, qdd);
+    float cfest = 0.f;
+    if (FEST) {
+      // the wrench estimate at (q_t, v_t) reuses the factors of M(q_t)
+      float invD[NJ], y[NJ];
+      ldlt_factor<NJ>(M, invD);
+      cfest = force_estimate_cost<B>(C, sl, tid, M, invD, v, sg, ee.p, sY);
+      unit_lower_solve<NJ>(M, rhs, y);
+      ldlt_back<NJ>(M, invD, y, qdd);
+    } else {
+      ldlt_solve(M, rhs, qdd);
+    }
     const float dt = P.dt;
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
@@ -296,9 +419,12 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
     float cst = motion_cost(C, pdes, Rd, ee);
     if (contact) {
       f = contact_force(C, plane, ee);
-      const float e = C.fdes - f;
-      cst += C.wforce * e * e + C.wreg * f * f;
+      if (!FEST) {
+        const float e = C.fdes - f;
+        cst += C.wforce * e * e + C.wreg * f * f;
+      }
     }
+    if (FEST) cst += cfest;
     float cj = 0.f;
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
@@ -315,12 +441,13 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
 }
 
 // Dynamic shared memory of rollout_kernel_rolled for horizon T, block B.
-__host__ __device__ constexpr size_t rolled_smem_bytes(int T, int B) {
+__host__ __device__ constexpr size_t rolled_smem_bytes(int T, int B, bool fest = false) {
   return sizeof(float) * (2 * static_cast<size_t>((T * NJ + 3) / 4 * 4) + 32 +
-                          static_cast<size_t>(ROLLED_FLOATS_PER_THREAD) * B);
+                          static_cast<size_t>(ROLLED_FLOATS_PER_THREAD +
+                                              (fest ? FEST_FLOATS_PER_THREAD : 0)) * B);
 }
 
-template <bool STORE_NOISE, int B>
+template <bool STORE_NOISE, int B, bool FEST = false>
 __global__ void __launch_bounds__(B)
 rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__ in,
                       const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
@@ -342,8 +469,50 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
   __syncthreads();
   const int k = blockIdx.x * B + threadIdx.x;
   if (k >= K) return;
-  S[k] = rollout_sample_rolled<STORE_NOISE, B>(P, s_in, k < k_split ? s_plan : s_prop, *iter_p,
-                                               k, noise, s_work, threadIdx.x);
+  S[k] = rollout_sample_rolled<STORE_NOISE, B, FEST>(P, s_in, k < k_split ? s_plan : s_prop,
+                                                     *iter_p, k, noise, s_work, threadIdx.x);
+}
+
+// Wrench estimates F = Jbar^T (v - g(q)) (Eq. 13) for n pairs (q_i, v_i),
+// [n][7] each, into F [n][6] (NaN rows at kinematic singularities), with the
+// rollouts' own kinematics, dynamics and estimate.  Block B, dynamic shared
+// memory fest_smem_bytes(B).
+__host__ __device__ constexpr size_t fest_smem_bytes(int B) {
+  return sizeof(float) * static_cast<size_t>(ROLLED_FLOATS_PER_THREAD + FEST_FLOATS_PER_THREAD) * B;
+}
+
+template <int B>
+__global__ void __launch_bounds__(B)
+force_estimate_kernel(const __grid_constant__ ProbK P, const float* __restrict__ q_in,
+                      const float* __restrict__ v_in, int n, float* __restrict__ F_out) {
+  extern __shared__ float dsm[];
+  const int tid = threadIdx.x;
+  const int i = blockIdx.x * B + tid;
+  if (i >= n) return;  // no block-wide barrier below
+  float* sl = dsm;
+  float* sM = sl + NJ * LINK_FIELDS * B;
+  float* sq = sM + (NJ * (NJ + 1) / 2) * B;
+  float* sqd = sq + NJ * B;
+  float* sh = sqd + NJ * B;
+  float* sY = sh + NJ * B;
+  float* sg = sY + 6 * NJ * B;
+  float v[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    sq[j * B + tid] = q_in[static_cast<size_t>(i) * NJ + j];
+    sqd[j * B + tid] = 0.f;
+    v[j] = v_in[static_cast<size_t>(i) * NJ + j];
+  }
+  EEState ee;
+  forward_sweep_rolled<B>(P.rb, sq, sqd, sl, tid, ee);
+  backward_sweep_rolled<B, true>(P.rb, sl, sqd, sh, sM, sg, tid);
+  float M[NJ * (NJ + 1) / 2], invD[NJ], F[6];
+#pragma unroll
+  for (int a = 0; a < NJ * (NJ + 1) / 2; ++a) M[a] = sM[a * B + tid];
+  ldlt_factor<NJ>(M, invD);
+  const bool ok = force_estimate<B>(sl, tid, M, invD, v, sg, ee.p, sY, F);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) F_out[static_cast<size_t>(i) * 6 + a] = ok ? F[a] : NAN;
 }
 
 // ---------------------------------------------------------------------------
@@ -525,7 +694,8 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
               const float* __restrict__ noise, const float* __restrict__ plan,
               float* __restrict__ ustar, float* __restrict__ plan_next, float* __restrict__ out,
               unsigned long long* __restrict__ iter_p, const float* __restrict__ prop = nullptr,
-              const int* __restrict__ ksplit_p = nullptr) {
+              const int* __restrict__ ksplit_p = nullptr, float* __restrict__ tau_dst = nullptr,
+              float* __restrict__ plan_dst = nullptr) {
   const int e = blockIdx.x;
   const float* nrow = noise + static_cast<size_t>(e) * K;
   const int k_split = ksplit_p ? *ksplit_p : K;
@@ -541,12 +711,18 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
       if (t >= 1) out[OUT_PLAN + e - NJ] = us;
       if (t == T - 1) out[OUT_PLAN + e] = us;
     }
+    if (plan_dst) {
+      if (t >= 1) plan_dst[e - NJ] = us;
+      if (t == T - 1) plan_dst[e] = us;
+    }
   } else {
     plan_next[e] = us;
     if (out) out[OUT_PLAN + e] = us;
+    if (plan_dst) plan_dst[e] = us;
   }
   ustar[e] = us;
   if (out && e < NJ) out[OUT_TAU0 + e] = us;
+  if (tau_dst && e < NJ) tau_dst[e] = us;
   if (e == 0) {
     if (out) {
       reinterpret_cast<int*>(out)[OUT_STATUS] = r.ok ? 0 : 1;

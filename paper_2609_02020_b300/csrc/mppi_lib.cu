@@ -166,6 +166,11 @@ int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, Pr
     *why = "contact stiffness and damping must be finite and >= 0";
     return -1;
   }
+  if (c->force_estimate && (!finite_all(c->w_force6, 6) || !finite_all(c->f_des6, 6) ||
+                            !finite_all(c->w_reg6, 6))) {
+    *why = "wrench-estimate weights must be finite";
+    return -1;
+  }
 
   std::memset(P, 0, sizeof(*P));
   M3 Pprev = m3_identity();
@@ -235,6 +240,12 @@ int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, Pr
   k.contact = c->contact ? 1 : 0;
   k.kc = static_cast<float>(c->k_contact);
   k.dc = static_cast<float>(c->d_contact);
+  k.fest = c->force_estimate ? 1 : 0;
+  for (int a = 0; a < 6; ++a) {
+    k.wf6[a] = static_cast<float>(c->w_force6[a]);
+    k.fdes6[a] = static_cast<float>(c->f_des6[a]);
+    k.wreg6[a] = static_cast<float>(c->w_reg6[a]);
+  }
   P->dt = static_cast<float>(cfg->dt);
   P->lambda = static_cast<float>(cfg->lambda);
   for (int j = 0; j < 7; ++j) P->sigma[j] = static_cast<float>(cfg->sigma[j]);
@@ -250,6 +261,17 @@ int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, Pr
 
 cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float* S, float* noise) {
   const int grid = (h->P.K + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
+  if (h->P.cost.fest) {
+    // the wrench-estimate cost runs in the rolled kernel only
+    const size_t smem = rolled_smem_bytes(h->P.T, ROLLOUT_BLOCK, true);
+    if (noise)
+      rollout_kernel_rolled<true, ROLLOUT_BLOCK, true><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
+          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl);
+    else
+      rollout_kernel_rolled<false, ROLLOUT_BLOCK, true><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
+          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl);
+    return cudaGetLastError();
+  }
   if (h->variant == 2) {
     const size_t smem = rolled_smem_bytes(h->P.T, ROLLOUT_BLOCK);
     if (noise)
@@ -272,24 +294,29 @@ cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float*
 // prop / ksplit null: plain Eq. 4 (every sample around plan)
 cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const float* plan,
                           float* ustar, float* plan_next, float* out, unsigned long long* iter,
-                          const float* prop = nullptr, const int* ksplit = nullptr) {
+                          const float* prop = nullptr, const int* ksplit = nullptr,
+                          float* tau_dst = nullptr, float* plan_dst = nullptr) {
   const int grid = h->P.T * NJ;
   if (h->reduce_fp64)
     update_kernel<double><<<grid, UPDATE_THREADS, 0, h->stream>>>(
-        h->P.K, h->P.T, h->P.lambda, S, noise, plan, ustar, plan_next, out, iter, prop, ksplit);
+        h->P.K, h->P.T, h->P.lambda, S, noise, plan, ustar, plan_next, out, iter, prop, ksplit,
+        tau_dst, plan_dst);
   else
     update_kernel<float><<<grid, UPDATE_THREADS, 0, h->stream>>>(
-        h->P.K, h->P.T, h->P.lambda, S, noise, plan, ustar, plan_next, out, iter, prop, ksplit);
+        h->P.K, h->P.T, h->P.lambda, S, noise, plan, ustar, plan_next, out, iter, prop, ksplit,
+        tau_dst, plan_dst);
   return cudaGetLastError();
 }
 
-// the whole update on device buffers: rollouts, then Eq. 4 into the other
-// plan; a second proposal set for this update is consumed (k_split := K)
-cudaError_t enqueue_update(mppi_s* h, int cur) {
-  cudaError_t e = launch_rollout(h, h->d_in, h->d_plan[cur], h->d_S, h->d_noise);
+// the whole update on device buffers: rollouts from the inputs at `in`, then
+// Eq. 4 into the other plan (and into tau_dst / plan_dst when given); a
+// second proposal set for this update is consumed (k_split := K)
+cudaError_t enqueue_update(mppi_s* h, int cur, const float* in = nullptr, float* tau_dst = nullptr,
+                           float* plan_dst = nullptr) {
+  cudaError_t e = launch_rollout(h, in ? in : h->d_in, h->d_plan[cur], h->d_S, h->d_noise);
   if (e != cudaSuccess) return e;
   e = launch_update(h, h->d_S, h->d_noise, h->d_plan[cur], h->d_ustar, h->d_plan[cur ^ 1],
-                    h->d_out, h->d_iter, h->d_prop, h->d_ctl);
+                    h->d_out, h->d_iter, h->d_prop, h->d_ctl, tau_dst, plan_dst);
   if (e != cudaSuccess) return e;
   return cudaMemcpyAsync(h->d_ctl, h->d_ctl + 1, sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
 }
@@ -391,7 +418,12 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
     delete h;
     return fail(nullptr, MPPI_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
   }
-  h->variant = cfg->variant == 0 ? default_variant(cfg->K) : cfg->variant;
+  if (h->P.cost.fest && cfg->variant == 1) {
+    delete h;
+    return fail(nullptr, MPPI_ERR_INVALID_ARG,
+                "the wrench-estimate cost needs the rolled rollout kernel (variant 0 or 2)");
+  }
+  h->variant = h->P.cost.fest ? 2 : cfg->variant == 0 ? default_variant(cfg->K) : cfg->variant;
   const int T = cfg->T, K = cfg->K;
   auto bail = [&](cudaError_t e, const char* what) {
     std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
@@ -517,24 +549,18 @@ int mppi_step(mppi_t h, const float q[7], const float qd[7], const float goal[7]
 int mppi_step_device(mppi_t h, const float* d_in, float* d_tau0, float* d_plan) {
   if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
   if (!d_in) return fail(h, MPPI_ERR_INVALID_ARG, "null d_in");
+  // the kernels read the caller's inputs and write tau0 and the shifted plan
+  // straight into the caller's buffers: two kernels and one 4-byte copy
   const int cur = h->cur;
-  CUDA_TRY(h, cudaMemcpyAsync(h->d_in, d_in, sizeof(float) * IN_FLOATS, cudaMemcpyDeviceToDevice,
-                              h->stream));
-  CUDA_TRY(h, enqueue_update(h, cur));
+  CUDA_TRY(h, enqueue_update(h, cur, d_in, d_tau0, d_plan));
   h->cur = cur ^ 1;
-  if (d_tau0)
-    CUDA_TRY(h, cudaMemcpyAsync(d_tau0, h->d_out + OUT_TAU0, 7 * sizeof(float),
-                                cudaMemcpyDeviceToDevice, h->stream));
-  if (d_plan)
-    CUDA_TRY(h, cudaMemcpyAsync(d_plan, h->d_plan[h->cur], sizeof(float) * h->P.T * NJ,
-                                cudaMemcpyDeviceToDevice, h->stream));
-  CUDA_TRY(h, cudaMemcpyAsync(h->h_out + OUT_STATUS, h->d_out + OUT_STATUS, 5 * sizeof(float),
-                              cudaMemcpyDeviceToHost, h->stream));
   return MPPI_OK;
 }
 
 int mppi_sync(mppi_t h) {
   if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_out + OUT_STATUS, h->d_out + OUT_STATUS, 5 * sizeof(float),
+                              cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return read_status(h);
 }
@@ -719,6 +745,17 @@ int mppi_gravity_torque(mppi_t h, const float q[7], float tau_out[7]) {
   CUDA_TRY(h, cudaGetLastError());
   CUDA_TRY(h, cudaMemcpyAsync(tau_out, h->d_misc + 16, 7 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPPI_OK;
+}
+
+int mppi_force_estimate_device(mppi_t h, const float* d_q, const float* d_v, int n, float* d_F) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (!d_q || !d_v || !d_F) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  if (n < 1 || n > MPPI_K_MAX) return fail(h, MPPI_ERR_INVALID_ARG, "n must be in 1..2^22");
+  const int grid = (n + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
+  force_estimate_kernel<ROLLOUT_BLOCK><<<grid, ROLLOUT_BLOCK, fest_smem_bytes(ROLLOUT_BLOCK),
+                                         h->stream>>>(h->P, d_q, d_v, n, d_F);
+  CUDA_TRY(h, cudaGetLastError());
   return MPPI_OK;
 }
 

@@ -70,6 +70,10 @@ class Cost(C.Structure):
         ("contact", C.c_int),
         ("k_contact", C.c_double),
         ("d_contact", C.c_double),
+        ("force_estimate", C.c_int),
+        ("w_force6", C.c_double * 6),
+        ("f_des6", C.c_double * 6),
+        ("w_reg6", C.c_double * 6),
     ]
 
 
@@ -121,6 +125,7 @@ EXPORTS = [
     "mppi_noise_words", "mppi_step_static", "mppi_last_error", "mppi_version",
     "mppi_simulate_device", "mppi_set_plan_device", "mppi_get_plan_device",
     "mppi_get_updated_plan_device", "mppi_set_proposal_device", "mppi_gravity_torque",
+    "mppi_force_estimate_device",
     # include/mppi_serve.h
     "mppi_pool_create", "mppi_pool_destroy", "mppi_pool_alloc", "mppi_pool_free",
     "mppi_pool_stats", "mppi_server_create", "mppi_server_destroy", "mppi_server_add_problem",
@@ -179,6 +184,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_get_updated_plan_device": ([H, vp], C.c_int),
         "mppi_set_proposal_device": ([H, vp, C.c_int], C.c_int),
         "mppi_gravity_torque": ([H, fp, fp], C.c_int),
+        "mppi_force_estimate_device": ([H, vp, vp, C.c_int, vp], C.c_int),
         "mppi_pool_create": ([C.c_size_t, C.POINTER(C.c_void_p)], C.c_int),
         "mppi_pool_destroy": ([H], C.c_int),
         "mppi_pool_alloc": ([H, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
@@ -274,6 +280,12 @@ def cost_struct(d: dict) -> Cost:
     for j in range(NJ):
         c.q_posture[j] = qp[j]
     c.contact = int(d.get("contact", 0))
+    c.force_estimate = int(d.get("force_estimate", 0))
+    for name in ("w_force6", "f_des6", "w_reg6"):
+        v = np.asarray(d.get(name, np.zeros(6)), dtype=np.float64).reshape(6)
+        dst = getattr(c, name)
+        for a in range(6):
+            dst[a] = v[a]
     return c
 
 
@@ -406,6 +418,13 @@ class MPPI:
         out = np.zeros(7, dtype=np.float32)
         self._check(self.lib.mppi_gravity_torque(self.h, _fp(_f32(q, NJ)), _fp(out)))
         return out
+
+    def force_estimate_device(self, d_q, d_v, d_F):
+        """Wrench estimates F = Jbar^T (v - g(q)) (Eq. 13): d_q, d_v [n][7] ->
+        d_F [n][6] (device tensors; queued on the handle's stream)."""
+        n = int(d_q.shape[0])
+        self._check(self.lib.mppi_force_estimate_device(self.h, _dptr(d_q), _dptr(d_v), n,
+                                                        _dptr(d_F)))
 
     def ee_pose(self, q) -> np.ndarray:
         out = np.zeros(7, dtype=np.float32)

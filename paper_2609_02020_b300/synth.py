@@ -129,6 +129,18 @@ def cost_contact() -> dict:
     return c
 
 
+def cost_force_estimate(w_fz: float = 1e-3, base: dict | None = None) -> dict:
+    """C_force on the wrench estimate of Eq. 13 added to a free-space cost:
+    push 10 N along -z at the end-effector (W_force on the z force only)
+    with a light regulariser on all six axes."""
+    c = dict(cost_free_space() if base is None else base)
+    c.update(force_estimate=1,
+             w_force6=np.array([0.0, 0.0, w_fz, 0.0, 0.0, 0.0]),
+             f_des6=np.array([0.0, 0.0, -10.0, 0.0, 0.0, 0.0]),
+             w_reg6=np.full(6, 1e-2 * w_fz))
+    return c
+
+
 def plane_through(point_z: float, penetration: float = 0.02) -> np.ndarray:
     """Horizontal plane n = (0, 0, 1) with offset d placed `penetration` above
     a given height (so a point at that height starts inside the contact)."""

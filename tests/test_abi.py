@@ -70,3 +70,13 @@ def test_create_rejects_bad_robot_and_cost():
     c["w_tau"] = float("inf")
     with pytest.raises(mppi.MPPIError, match="finite"):
         _create(cost=c)
+
+
+def test_create_rejects_bad_wrench_estimate_cost():
+    c = dict(synth.cost_free_space(), force_estimate=1, w_force6=np.array([0, 0, np.nan, 0, 0, 0]))
+    with pytest.raises(mppi.MPPIError, match="wrench-estimate weights"):
+        _create(cost=c)
+    # the estimate runs in the rolled rollout kernel only
+    c = dict(synth.cost_free_space(), force_estimate=1, w_force6=np.ones(6))
+    with pytest.raises(mppi.MPPIError, match="rolled"):
+        _create(cost=c, variant=1)
