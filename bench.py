@@ -5,6 +5,7 @@ and costs, then the Eq. 4 update and the shift) of a seeded 7-joint arm with
 plane contact, dt = 0.01 s.  Prints one JSON line on rank 0.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--cost contact|force_estimate|collision] [--mode update|serve|learned]
 
 `value` times the update on device-resident inputs with CUDA events on the
 library's stream, L2 flushed between steps; `e2e` times the public host call
@@ -12,6 +13,9 @@ mppi_step (inputs copied from pinned host memory, tau0 and the plan read back)
 with a host clock.  `--impl reference` times the FP64 CPU oracle on the host
 cores on a bounded sample of the same workload.  With N > 1 (torchrun) every
 rank solves its own independent problem (replicas, weak scaling).
+`--cost` swaps the update's cost for the same workload with C_force on the
+wrench estimate of Eq. 13, or with the collision indicator of Eq. 15 against
+three obstacles near the end-effector (the default line is the contact cost).
 """
 from __future__ import annotations
 
@@ -37,15 +41,21 @@ L2_FLUSH_BYTES = 256 << 20  # twice the 126 MB L2
 
 # FP32 floating-point operations of one rollout-step (one sample advanced by
 # one step: noise, kinematics, RNEA, CRBA, LDL^T solve, Euler step, contact
-# and costs): FADD + FMUL + 2 x FFMA executed by rollout_kernel, counted by
-# ncu (smsp__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on) on the
-# contact workload at K=4096, T=18 and divided by K*T.
-FLOP_PER_ROLLOUT_STEP = 4811.0
-# DRAM read + write bytes of one rollout_kernel launch at K=16384, T=18
-# (ncu dram__bytes_{read,write}.sum, mean of two launches).  The 8.3 MB of
-# stored noise stays in L2 for update_kernel and is not written back inside
-# the launch.
-ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = 115456
+# and costs) per cost workload: FADD + FMUL + 2 x FFMA executed by the
+# rollout kernel, counted by ncu
+# (smsp__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on) and divided
+# by K*T, on rollout_kernel_rolled at K=16384, T=18 (bench.py's own
+# workloads, two launches each).
+FLOP_PER_ROLLOUT_STEP = {"contact": 4808.1, "force_estimate": 6004.6, "collision": 6692.8}
+# DRAM read + write bytes of one rollout launch at K=16384, T=18 per (cost,
+# kernel) (ncu dram__bytes_{read,write}.sum, mean of two launches).  The
+# 8.3 MB of stored noise stays in L2 for update_kernel and is not written
+# back inside the launch.
+ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel"): 115456,
+                                    ("contact", "rollout_kernel_rolled"): 55680,
+                                    ("force_estimate", "rollout_kernel_rolled"): 66432,
+                                    ("collision", "rollout_kernel_rolled"): 70400}
+COSTS = ("contact", "force_estimate", "collision")
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 
@@ -63,6 +73,10 @@ def parse():
                     help="reference arm: wall-clock budget of the whole run [s]")
     ap.add_argument("--variant", type=int, default=0,
                     help="rollout kernel: 0 library default, 1 unrolled, 2 rolled")
+    ap.add_argument("--cost", default="contact", choices=list(COSTS),
+                    help="update mode: the plane-contact workload (default), or the same with "
+                         "C_force on the wrench estimate of Eq. 13, or with the collision "
+                         "indicator of Eq. 15 against 3 obstacles")
     ap.add_argument("--mode", default="update", choices=["update", "serve", "learned"],
                     help="update: the headline single-update benchmark; serve: batched "
                          "serving of 256 problems under Poisson load; learned: train the "
@@ -90,19 +104,51 @@ def max_over_ranks(values, world: int, device: str):
     return [float(x) for x in t.cpu()]
 
 
-def workload(rank: int):
+def workload(rank: int, cost_name: str = "contact"):
+    """Arm, cost (without obstacles), state and goal of one rank's problem."""
     from paper_2609_02020_b300 import synth
     arm = synth.arm(rank)
     q, qd = synth.state(1000 + rank, arm)
     goal = synth.goal(1000 + rank, arm)
-    return arm, synth.cost_contact(), q, qd, goal
+    cost = synth.cost_contact()
+    if cost_name == "force_estimate":
+        cost = synth.cost_force_estimate(base=cost)
+    elif cost_name == "collision":
+        cost = synth.cost_collision(1, base=cost)
+    return arm, cost, q, qd, goal
 
 
-def config_dict(K, T, n):
-    return {"workload": f"7-DoF seeded arm, one MPPI update with plane contact, K={K} T={T} "
-                        f"dt={DT} s, sigma={SIGMA} N m, lambda={LAMBDA}",
-            "K": K, "T": T, "dt": DT, "robots": "synthetic 7-joint arms (seeded)",
+def obstacles(rank: int, arm: dict, p_ee):
+    """Three capsule obstacles 0.12-0.3 m from the end-effector point."""
+    from paper_2609_02020_b300 import synth
+    pts = np.array([[0.0, 0.0, synth.BASE_HEIGHT], np.asarray(p_ee, float)])
+    return synth.obstacles_near(pts, 1000 + rank, 3)
+
+
+COST_TEXT = {"contact": "plane contact",
+             "force_estimate": "plane contact and C_force on the wrench estimate (Eq. 13)",
+             "collision": "plane contact and the collision indicator (Eq. 15), 3 obstacles"}
+
+
+def config_dict(K, T, n, cost_name="contact"):
+    return {"workload": f"7-DoF seeded arm, one MPPI update with {COST_TEXT[cost_name]}, "
+                        f"K={K} T={T} dt={DT} s, sigma={SIGMA} N m, lambda={LAMBDA}",
+            "K": K, "T": T, "dt": DT, "cost": cost_name,
+            "robots": "synthetic 7-joint arms (seeded)",
             "l2": "flushed between timed steps", "parallelism": f"replicas x{n}"}
+
+
+def oracle_problem(K: int, T: int, cost_name: str):
+    """The oracle's records of rank 0's problem (plane, obstacles included)."""
+    import oracle
+    from paper_2609_02020_b300 import synth
+    arm, cost, q, qd, goal = workload(0, cost_name)
+    rb = oracle.make_robot(arm)
+    pe = oracle.fk(rb, q)[3]
+    if cost_name == "collision":
+        cost = dict(cost, obstacles=obstacles(0, arm, pe))
+    plane = synth.plane_through(pe[2])
+    return rb, oracle.make_cost(cost), q, qd, goal, plane
 
 
 # ---------------------------------------------------------------------------
@@ -171,15 +217,11 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on the host cores
 
-def cpu_baseline(K: int, T: int, budget_s: float = 10.0):
+def cpu_baseline(K: int, T: int, budget_s: float = 10.0, cost_name: str = "contact"):
     """The oracle, as it stands, on the host cores: full FP64 updates of the
     same workload repeated until about `budget_s` seconds have passed."""
     import oracle
-    from paper_2609_02020_b300 import synth
-    arm, cost, q, qd, goal = workload(0)
-    rb, oc = oracle.make_robot(arm), oracle.make_cost(cost)
-    pe = oracle.fk(rb, q)[3]
-    plane = synth.plane_through(pe[2])
+    rb, oc, q, qd, goal, plane = oracle_problem(K, T, cost_name)
     cores = os.cpu_count() or 1
     nth = min(cores, oracle.max_threads())
     plan = np.zeros((T, 7))
@@ -191,7 +233,7 @@ def cpu_baseline(K: int, T: int, budget_s: float = 10.0):
         reps += 1
     dt = time.perf_counter() - t0
     return {"value": K * T * reps / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
-            "sample": f"{reps} full FP64 updates at K={K}, T={T} (same arm and contact cost), "
+            "sample": f"{reps} full FP64 updates at K={K}, T={T} (same arm and cost), "
                       f"OpenMP over samples on {nth} threads, {dt:.1f} s",
             "seconds": dt}
 
@@ -201,10 +243,7 @@ def run_reference(args, rank, world):
         return
     K, T = args.K, args.T
     import oracle
-    from paper_2609_02020_b300 import synth
-    arm, cost, q, qd, goal = workload(0)
-    rb, oc = oracle.make_robot(arm), oracle.make_cost(cost)
-    plane = synth.plane_through(oracle.fk(rb, q)[3][2])
+    rb, oc, q, qd, goal, plane = oracle_problem(K, T, args.cost)
     nth = min(os.cpu_count() or 1, oracle.max_threads())
     plan = np.zeros((T, 7))
     # size each step's sample so the whole run takes about --budget-s seconds
@@ -230,7 +269,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": float(times.mean() * 1e3 * scale), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(K, T, 1),
+            "config": config_dict(K, T, 1, args.cost),
             "p50_ms": float(np.percentile(times, 50) * 1e3 * scale),
             "p99_ms": float(np.percentile(times, 99) * 1e3 * scale),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": nth, "kind": "oracle",
@@ -251,12 +290,18 @@ def run_ours(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     K, T = args.K, args.T
-    arm, cost, q, qd, goal = workload(rank)
+    arm, cost, q, qd, goal = workload(rank, args.cost)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctl = mppi.MPPI(arm, cost, dt=DT, T=T, K=K, lam=LAMBDA, sigma=SIGMA, seed=SEED + rank,
                     variant=args.variant, stream=stream)
     pose = ctl.ee_pose(q)
+    if args.cost == "collision":
+        ctl.set_obstacles(obstacles(rank, arm, pose[:3]))
+    # the optional cost terms run in the rolled kernel; otherwise variant 0
+    # picks it for K <= 32768
+    rolled = args.variant == 2 or (args.variant == 0 and (args.cost != "contact" or K <= 32768))
+    kname = "rollout_kernel_rolled" if rolled else "rollout_kernel"
     plane = synth.plane_through(float(pose[2]))
     d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, plane), device="cuda")
     d_tau = torch.zeros(7, device="cuda")
@@ -329,22 +374,24 @@ def run_ours(args, rank, world):
     sm_mhz = clocks.get("sm_mhz") or 2032.0
     peak_max = SM_COUNT * FP32_LANES_PER_SM * 2 * 2032e6 / 1e12
     roof = None
-    if FLOP_PER_ROLLOUT_STEP:
-        achieved = FLOP_PER_ROLLOUT_STEP * K * T / (ms_roll * 1e-3) / 1e12
-        traffic = ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH if (K, T) == (K_DEFAULT, T_DEFAULT) else None
+    flop = FLOP_PER_ROLLOUT_STEP[args.cost]
+    if flop:
+        achieved = flop * K * T / (ms_roll * 1e-3) / 1e12
+        traffic = (ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH.get((args.cost, kname))
+                   if (K, T) == (K_DEFAULT, T_DEFAULT) else None)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
                 "frac": achieved / peak_max, "traffic": traffic,
-                "kernel": "rollout_kernel", "kernel_ms": ms_roll,
+                "kernel": kname, "kernel_ms": ms_roll,
                 "peak_note": "FP32 peak of 148 SMs x 128 lanes x 2 FLOP at the 2032 MHz "
                              "maximum SM clock (derived; no measured FP32 peak)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(K, T, world),
+            "config": config_dict(K, T, world, args.cost),
             "p50_ms": float(np.percentile(step_ms, 50)),
             "p99_ms": float(np.percentile(step_ms, 99)),
             "update_hz": 1e3 / mean_ms,
-            "kernels_ms": {"rollout_kernel": ms_roll, "update_kernel": ms_upd},
+            "kernels_ms": {kname: ms_roll, "update_kernel": ms_upd},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 25 * 4,
                     "d2h_bytes_per_step": (16 + T * 7) * 4,
                     "p50_ms": float(np.percentile(e2e_ms, 50)),
@@ -355,7 +402,7 @@ def run_ours(args, rank, world):
             "gpu_launches": launches,
             "wall_s": t_wall}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(K, T)
+        line["cpu_baseline"] = cpu_baseline(K, T, cost_name=args.cost)
     ctl.close()
     print(json.dumps(line), flush=True)
 

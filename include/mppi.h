@@ -88,7 +88,8 @@ typedef struct mppi_robot {
   double gravity[3];          /* world gravity [m/s^2]                         */
 } mppi_robot;
 
-/* Running cost l(x_{t+1}, v_t) = C_motion + C_force + C_joint (Eq. 9-12, 14):
+/* Running cost l(x_{t+1}, v_t) = C_motion + C_force + C_joint [+ C_collision]
+ * (Eq. 9-12, 14-15):
  *   C_motion = sum_a w_pos[a] (p_des - p_ee)_a^2 + sum_a w_ori[a] r_a^2,
  *              r = log(R_des^T R_ee) as a rotation vector (Eq. 11);
  *   C_force  = w_force (f_des - f)^2 + w_reg f^2 on the contact normal force
@@ -110,8 +111,20 @@ typedef struct mppi_robot {
  * Jacobian of the end-effector point); charged at step t in place of the
  * contact normal-force term.  A sample that meets a kinematic singularity
  * (J M^-1 J^T not positive definite) gets a non-finite cost and weight 0.
- * This cost runs in the rolled rollout kernel (variant 0 selects it;
- * variant 1 is rejected); mppi_step_static and the server do not take it. */
+ * Collision (collision != 0; Eq. 15): link i is the capsule around the
+ * segment from joint i's origin to joint i+1's (link 7 ends at the
+ * end-effector point) with radius link_radius[i]; obstacles are capsules
+ * (segment a-b, radius; a = b gives a sphere).  The pairs are links i, j
+ * with j >= i + 2 (15 pairs) and every link with every obstacle.  For each
+ * pair the clearance d is the segment distance (Lumelsky's method) minus
+ * both radii, and the pair adds w_collision * [d < d_th] (collision = 1, the
+ * indicator of Eq. 15) or w_collision * max(0, d_th - d)^2 (collision = 2, a
+ * smooth reading), with d_th = d_th_self or d_th_obs; charged on x_{t+1}.
+ * The obstacles are read by every update from a device buffer of the handle,
+ * set at creation from n_obstacles / obstacles and replaced by
+ * mppi_set_obstacles[_device] between updates (also under CUDA graphs).
+ * These two costs run in the rolled rollout kernel (variant 0 selects it;
+ * variant 1 is rejected); mppi_step_static and the server take neither. */
 typedef struct mppi_cost {
   double w_pos[3], w_ori[3];
   double w_force, f_des, w_reg;
@@ -122,7 +135,15 @@ typedef struct mppi_cost {
   double k_contact, d_contact;
   int force_estimate;          /* 1: C_force on the wrench estimate below      */
   double w_force6[6], f_des6[6], w_reg6[6];  /* its weights, (force; moment) */
+  int collision;               /* C_collision: 0 off, 1 indicator, 2 hinge     */
+  double w_collision;          /* its weight                                   */
+  double d_th_self, d_th_obs;  /* clearance thresholds [m]: link-link, -object */
+  double link_radius[7];       /* link capsule radii [m], >= 0                 */
+  int n_obstacles;             /* initial obstacles, 0..MPPI_OBS_MAX           */
+  double obstacles[8][7];      /* capsules: a xyz, b xyz, radius [m]           */
 } mppi_cost;
+
+#define MPPI_OBS_MAX 8
 
 /* Problem sizes and sampler parameters (Eq. 2-4). */
 typedef struct mppi_config {
@@ -237,6 +258,16 @@ MPPI_API int mppi_set_proposal_device(mppi_t h, const float* d_prop, int n_plain
 /* Gravity-compensation torque g(q) = h(q, 0) of Eq. 5 (host arrays),
  * computed on the device by the rollouts' own RNEA. */
 MPPI_API int mppi_gravity_torque(mppi_t h, const float q[7], float tau_out[7]);
+
+/* Replaces the obstacle capsules that the following updates read (Eq. 15):
+ * n in 0..MPPI_OBS_MAX rows of (a xyz, b xyz, radius), finite, radius >= 0.
+ * Host array; copied in the handle's stream order (the caller may reuse the
+ * array when the call returns). */
+MPPI_API int mppi_set_obstacles(mppi_t h, int n, const float* obs);
+/* The same from a device array d_obs [n][7] (not validated: non-finite
+ * obstacles make every cost non-finite and the update keeps its plan);
+ * queued on the handle's stream. */
+MPPI_API int mppi_set_obstacles_device(mppi_t h, int n, const float* d_obs);
 
 /* End-effector wrench estimates of Eq. 13, F = Jbar^T (v - g(q)), for n
  * pairs (q_i, v_i) of device arrays d_q, d_v [n][7] into d_F [n][6]

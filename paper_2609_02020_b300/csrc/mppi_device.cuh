@@ -51,6 +51,19 @@ struct CostK {
   float kc, dc;
   int fest;                            // C_force on the wrench estimate (Eq. 13)
   float wf6[6], fdes6[6], wreg6[6];    // its diagonal weights, (force; moment)
+  int coll;                            // C_collision (Eq. 15): 0 off, 1 indicator, 2 hinge
+  float wcoll, dth_self, dth_obs;
+  float lrad[NJ];                      // link capsule radii
+  float seg_a[NJ], seg_ia[NJ];         // squared link segment lengths and reciprocals
+};
+
+// Obstacle capsules read by the rollouts at every launch (device memory, so
+// that they can change between updates without touching kernel parameters).
+constexpr int OBS_MAX = 8;
+struct ObsK {
+  int n;
+  int pad[3];
+  float o[OBS_MAX][7];  // a xyz, b xyz, radius
 };
 
 struct ProbK {
@@ -448,6 +461,43 @@ __device__ __forceinline__ float motion_cost(const CostK& c, const float pdes[3]
 }
 
 // Plane contact normal force at the end-effector (0 without contact).
+// Squared distance between the segments p1 + s d1 and p2 + t d2, s, t in
+// [0, 1], for Eq. 15 by Lumelsky's method (Inf. Process. Lett. 21, 1985):
+// the closest point of the infinite lines, s clamped to [0, 1]; t follows
+// from s and, when it leaves [0, 1], is clamped and s recomputed against
+// that end point.  a = |d1|^2, e = |d2|^2 and their reciprocals ia, ie are
+// given (0 for a point segment, which takes the one-sided projection), so
+// that one division remains per pair.
+__device__ __forceinline__ float segment_dist2(const float p1[3], const float d1[3], float a,
+                                               float ia, const float p2[3], const float d2[3],
+                                               float e, float ie) {
+  const float r[3] = {p1[0] - p2[0], p1[1] - p2[1], p1[2] - p2[2]};
+  const float f = dot3(d2, r), c = dot3(d1, r), b = dot3(d1, d2);
+  float s, t;
+  if (ia == 0.f) {
+    s = 0.f;
+    t = __saturatef(f * ie);
+  } else if (ie == 0.f) {
+    t = 0.f;
+    s = __saturatef(-c * ia);
+  } else {
+    const float den = fmaf(a, e, -b * b);
+    s = den > 0.f ? __saturatef(__fdividef(fmaf(b, f, -c * e), den)) : 0.f;
+    t = fmaf(b, s, f) * ie;
+    if (t < 0.f) {
+      t = 0.f;
+      s = __saturatef(-c * ia);
+    } else if (t > 1.f) {
+      t = 1.f;
+      s = __saturatef((b - c) * ia);
+    }
+  }
+  float g[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g[k] = fmaf(s, d1[k], r[k]) - t * d2[k];
+  return dot3(g, g);
+}
+
 __device__ __forceinline__ float contact_force(const CostK& c, const float plane[4],
                                                const EEState& ee) {
   const float delta = plane[3] - dot3(plane, ee.p);

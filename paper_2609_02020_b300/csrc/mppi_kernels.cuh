@@ -183,10 +183,12 @@ __device__ __forceinline__ void load_axis(const float* sl, int j, int tid, float
   }
 }
 
-template <int B>
+// With STORE_P, also the link capsule end points into sP [NJ + 1][3][B]:
+// joint origins p_0 .. p_6 and the end-effector point.
+template <int B, bool STORE_P = false>
 __device__ __forceinline__ void forward_sweep_rolled(const RobotK& rb, const float* sq,
                                                      const float* sqd, float* sl, int tid,
-                                                     EEState& ee) {
+                                                     EEState& ee, float* sP = nullptr) {
   ChainState c;
   chain_init(rb, c);
 #pragma unroll 1
@@ -194,8 +196,16 @@ __device__ __forceinline__ void forward_sweep_rolled(const RobotK& rb, const flo
     LinkState S;
     forward_link(rb.L[i], sq[i * B + tid], sqd[i * B + tid], c, S);
     store_link<B>(sl, i, tid, S);
+    if (STORE_P) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) sP[(3 * i + a) * B + tid] = c.p[a];
+    }
   }
   chain_ee(rb, c, ee);
+  if (STORE_P) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sP[(3 * NJ + a) * B + tid] = ee.p[a];
+  }
 }
 
 // Extra per-thread shared floats of the wrench-estimate cost: J^T rows
@@ -327,13 +337,102 @@ __device__ __forceinline__ void backward_sweep_rolled(const RobotK& rb, const fl
   }
 }
 
-// sm: this block's work area of ROLLED_FLOATS_PER_THREAD * B floats, plus
-// FEST_FLOATS_PER_THREAD * B floats when FEST is set.
-template <bool STORE_NOISE, int B, bool FEST = false>
+// Optional cost terms of the rolled kernel, as template feature bits.
+constexpr int FEAT_FEST = 1;  // C_force on the wrench estimate (Eq. 13)
+constexpr int FEAT_COLL = 2;  // C_collision (Eq. 15)
+constexpr int COLL_FLOATS_PER_THREAD = 3 * (NJ + 1);  // link capsule end points
+constexpr int OBS_SMEM_FLOATS = OBS_MAX * 9 + 8;      // block copy: obstacles, link radii
+
+__host__ __device__ constexpr int rolled_floats_per_thread(int feat) {
+  return ROLLED_FLOATS_PER_THREAD + ((feat & FEAT_FEST) ? FEST_FLOATS_PER_THREAD : 0) +
+         ((feat & FEAT_COLL) ? COLL_FLOATS_PER_THREAD : 0);
+}
+
+template <int B>
+__device__ __forceinline__ void load_point(const float* sP, int i, int tid, float x[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) x[a] = sP[(3 * i + a) * B + tid];
+}
+
+// Block copy of the obstacles: per obstacle a xyz, b - a xyz, |b - a|^2, its
+// reciprocal (0 for a sphere) and the radius; then the NJ link radii.
+constexpr int OBS_FIELDS = 9;
+
+// One pair's term of Eq. 15 from the squared segment distance g2: the
+// indicator [d < th] compares g2 with (th + r1 + r2)^2 (d = sqrt(g2) - r1 -
+// r2), the hinge takes (th - d)^2.
+__device__ __forceinline__ float collision_term(int mode, float g2, float rsum, float th) {
+  if (mode == 1) {
+    const float R = th + rsum;
+    return (R > 0.f && g2 < R * R) ? 1.f : 0.f;
+  }
+  const float d = sqrtf(g2) - rsum;
+  return d < th ? (th - d) * (th - d) : 0.f;
+}
+
+// C_collision of Eq. 15 at the link points in sP: self pairs (i, j >= i + 2)
+// by i then j, then every link against every obstacle (s_obs, n_obs of
+// them) by link then obstacle; indicator (mode 1) or squared hinge (mode 2)
+// against the pair's threshold, times w_collision.  The inner loops have
+// constant trip counts (bounds are guards) so that independent pairs
+// interleave.
+template <int B>
+__device__ __forceinline__ float collision_cost(const CostK& C, const float* sP, int tid,
+                                                const float* s_obs, int n_obs) {
+  const float* lrad = s_obs + OBS_FIELDS * OBS_MAX;
+  float acc = 0.f;
+#pragma unroll 1
+  for (int i = 0; i < NJ - 2; ++i) {
+    float pi[3], di[3];
+    load_point<B>(sP, i, tid, pi);
+    load_point<B>(sP, i + 1, tid, di);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) di[a] -= pi[a];
+    const float ai = C.seg_a[i], iai = C.seg_ia[i], ri = lrad[i];
+#pragma unroll
+    for (int jj = 0; jj < NJ - 2; ++jj) {
+      const int j = i + 2 + jj;
+      if (j < NJ) {
+        float pj[3], dj[3];
+        load_point<B>(sP, j, tid, pj);
+        load_point<B>(sP, j + 1, tid, dj);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dj[a] -= pj[a];
+        const float g2 = segment_dist2(pi, di, ai, iai, pj, dj, C.seg_a[j], C.seg_ia[j]);
+        acc += collision_term(C.coll, g2, ri + lrad[j], C.dth_self);
+      }
+    }
+  }
+#pragma unroll 1
+  for (int i = 0; i < NJ; ++i) {
+    float pi[3], di[3];
+    load_point<B>(sP, i, tid, pi);
+    load_point<B>(sP, i + 1, tid, di);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) di[a] -= pi[a];
+    const float ai = C.seg_a[i], iai = C.seg_ia[i], ri = lrad[i];
+#pragma unroll
+    for (int o = 0; o < OBS_MAX; ++o) {
+      if (o < n_obs) {
+        const float* ob = s_obs + OBS_FIELDS * o;
+        const float g2 = segment_dist2(pi, di, ai, iai, ob, ob + 3, ob[6], ob[7]);
+        acc += collision_term(C.coll, g2, ri + ob[8], C.dth_obs);
+      }
+    }
+  }
+  return C.wcoll * acc;
+}
+
+// sm: this block's work area of rolled_floats_per_thread(FEAT) * B floats;
+// s_obs: the block's copy of the n_obs obstacles (FEAT_COLL).
+template <bool STORE_NOISE, int B, int FEAT = 0>
 __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const float* in,
                                                        const float* plan, uint64_t iter, int k,
                                                        float* __restrict__ noise, float* sm,
-                                                       int tid) {
+                                                       int tid, const float* s_obs = nullptr,
+                                                       int n_obs = 0) {
+  constexpr bool FEST = (FEAT & FEAT_FEST) != 0;
+  constexpr bool COLL = (FEAT & FEAT_COLL) != 0;
   float* sl = sm;                                   // [7][22][B]
   float* sM = sl + NJ * LINK_FIELDS * B;            // [28][B]
   float* sq = sM + (NJ * (NJ + 1) / 2) * B;         // [7][B]
@@ -341,6 +440,7 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
   float* sh = sqd + NJ * B;                         // [7][B]
   float* sY = sh + NJ * B;                          // [6][7][B] (FEST)
   float* sg = sY + 6 * NJ * B;                      // [7][B]    (FEST)
+  float* sP = sh + NJ * B + (FEST ? FEST_FLOATS_PER_THREAD * B : 0);  // [8][3][B] (COLL)
   const int T = P.T, K = P.K;
   float q[NJ], qd[NJ];
 #pragma unroll
@@ -361,7 +461,7 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
   const bool contact = C.contact != 0;
 
   EEState ee;
-  forward_sweep_rolled<B>(P.rb, sq, sqd, sl, tid, ee);
+  forward_sweep_rolled<B, COLL>(P.rb, sq, sqd, sl, tid, ee, sP);
   float f = contact ? contact_force(C, plane, ee) : 0.f;
   double Sacc = 0.0;
 
@@ -415,7 +515,7 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
       sq[j * B + tid] = q[j];
       sqd[j * B + tid] = qd[j];
     }
-    forward_sweep_rolled<B>(P.rb, sq, sqd, sl, tid, ee);
+    forward_sweep_rolled<B, COLL>(P.rb, sq, sqd, sl, tid, ee, sP);
     float cst = motion_cost(C, pdes, Rd, ee);
     if (contact) {
       f = contact_force(C, plane, ee);
@@ -425,6 +525,7 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
       }
     }
     if (FEST) cst += cfest;
+    if (COLL) cst += collision_cost<B>(C, sP, tid, s_obs, n_obs);
     float cj = 0.f;
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
@@ -440,20 +541,23 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
   return static_cast<float>(Sacc);
 }
 
-// Dynamic shared memory of rollout_kernel_rolled for horizon T, block B.
-__host__ __device__ constexpr size_t rolled_smem_bytes(int T, int B, bool fest = false) {
+// Dynamic shared memory of rollout_kernel_rolled for horizon T, block B and
+// feature bits feat.
+__host__ __device__ constexpr size_t rolled_smem_bytes(int T, int B, int feat = 0) {
   return sizeof(float) * (2 * static_cast<size_t>((T * NJ + 3) / 4 * 4) + 32 +
-                          static_cast<size_t>(ROLLED_FLOATS_PER_THREAD +
-                                              (fest ? FEST_FLOATS_PER_THREAD : 0)) * B);
+                          ((feat & FEAT_COLL) ? OBS_SMEM_FLOATS : 0) +
+                          static_cast<size_t>(rolled_floats_per_thread(feat)) * B);
 }
 
-template <bool STORE_NOISE, int B, bool FEST = false>
+template <bool STORE_NOISE, int B, int FEAT = 0>
 __global__ void __launch_bounds__(B)
 rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__ in,
                       const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
                       float* __restrict__ S, float* __restrict__ noise,
                       const float* __restrict__ prop = nullptr,
-                      const int* __restrict__ ksplit_p = nullptr) {
+                      const int* __restrict__ ksplit_p = nullptr,
+                      const ObsK* __restrict__ obs = nullptr) {
+  constexpr bool COLL = (FEAT & FEAT_COLL) != 0;
   extern __shared__ float dsm[];
   const int T = P.T, K = P.K;
   const int k_split = ksplit_p ? *ksplit_p : K;
@@ -461,16 +565,37 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
   float* s_plan = dsm;
   float* s_prop = dsm + pstride;
   float* s_in = s_prop + pstride;
-  float* s_work = s_in + 32;
+  float* s_obs = s_in + 32;
+  float* s_work = s_obs + (COLL ? OBS_SMEM_FLOATS : 0);
   for (int i = threadIdx.x; i < T * NJ; i += B) s_plan[i] = plan[i];
   if (k_split < K)
     for (int i = threadIdx.x; i < T * NJ; i += B) s_prop[i] = prop[i];
   if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
+  int n_obs = 0;
+  if (COLL) {
+    n_obs = min(max(obs->n, 0), OBS_MAX);
+    if (threadIdx.x < n_obs) {
+      const float* o = obs->o[threadIdx.x];
+      float* so = s_obs + OBS_FIELDS * threadIdx.x;
+      float e = 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        so[a] = o[a];
+        so[3 + a] = o[3 + a] - o[a];
+        e = fmaf(so[3 + a], so[3 + a], e);
+      }
+      so[6] = e;
+      so[7] = e > 1e-12f ? 1.f / e : 0.f;
+      so[8] = o[6];
+    }
+    if (threadIdx.x < NJ) s_obs[OBS_FIELDS * OBS_MAX + threadIdx.x] = P.cost.lrad[threadIdx.x];
+  }
   __syncthreads();
   const int k = blockIdx.x * B + threadIdx.x;
   if (k >= K) return;
-  S[k] = rollout_sample_rolled<STORE_NOISE, B, FEST>(P, s_in, k < k_split ? s_plan : s_prop,
-                                                     *iter_p, k, noise, s_work, threadIdx.x);
+  S[k] = rollout_sample_rolled<STORE_NOISE, B, FEAT>(P, s_in, k < k_split ? s_plan : s_prop,
+                                                     *iter_p, k, noise, s_work, threadIdx.x,
+                                                     s_obs, n_obs);
 }
 
 // Wrench estimates F = Jbar^T (v - g(q)) (Eq. 13) for n pairs (q_i, v_i),

@@ -25,6 +25,8 @@ using namespace mppi_dev;
 constexpr int kRolledMaxK = 32768;
 static int default_variant(int K) { return K <= kRolledMaxK ? 2 : 1; }
 
+static_assert(MPPI_OBS_MAX == OBS_MAX, "obstacle capacity of the ABI and the kernels");
+
 struct mppi_s {
   ProbK P;
   int reduce_fp64 = 0;
@@ -44,6 +46,8 @@ struct mppi_s {
   uint32_t* d_words = nullptr;            // 8 x 1024 words for mppi_noise_words
   float* d_prop = nullptr;                // second proposal plan [T][7]
   int* d_ctl = nullptr;                   // {k_split of the next update, K}
+  ObsK* d_obs = nullptr;                  // obstacle capsules of Eq. 15
+  int feat = 0;                           // FEAT_* cost terms of the rollouts
   unsigned long long* d_iter = nullptr;
   // pinned host staging
   float* h_in = nullptr;
@@ -138,6 +142,15 @@ bool finite_all(const double* x, int n) {
   return true;
 }
 
+// Host image of the obstacle buffer from n capsules (a xyz, b xyz, radius).
+template <typename R>
+void fill_obs(int n, const R* obs, ObsK* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->n = n;
+  for (int o = 0; o < n; ++o)
+    for (int a = 0; a < 7; ++a) out->o[o][a] = static_cast<float>(obs[7 * o + a]);
+}
+
 int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, ProbK* P,
             std::string* why) {
   if (rb->n != MPPI_NJ) { *why = "robot.n must be 7"; return -1; }
@@ -170,6 +183,26 @@ int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, Pr
                             !finite_all(c->w_reg6, 6))) {
     *why = "wrench-estimate weights must be finite";
     return -1;
+  }
+  if (c->collision < 0 || c->collision > 2) { *why = "collision must be 0, 1 or 2"; return -1; }
+  if (c->collision) {
+    if (!std::isfinite(c->w_collision) || !std::isfinite(c->d_th_self) ||
+        !std::isfinite(c->d_th_obs) || !finite_all(c->link_radius, 7)) {
+      *why = "collision weights, thresholds and radii must be finite";
+      return -1;
+    }
+    for (int j = 0; j < 7; ++j)
+      if (c->link_radius[j] < 0.0) { *why = "link radii must be >= 0"; return -1; }
+    if (c->n_obstacles < 0 || c->n_obstacles > MPPI_OBS_MAX) {
+      *why = "n_obstacles must be in 0..8";
+      return -1;
+    }
+    if (!finite_all(&c->obstacles[0][0], 7 * c->n_obstacles)) {
+      *why = "obstacles must be finite";
+      return -1;
+    }
+    for (int o = 0; o < c->n_obstacles; ++o)
+      if (c->obstacles[o][6] < 0.0) { *why = "obstacle radii must be >= 0"; return -1; }
   }
 
   std::memset(P, 0, sizeof(*P));
@@ -240,6 +273,19 @@ int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, Pr
   k.contact = c->contact ? 1 : 0;
   k.kc = static_cast<float>(c->k_contact);
   k.dc = static_cast<float>(c->d_contact);
+  k.coll = c->collision;
+  k.wcoll = static_cast<float>(c->w_collision);
+  k.dth_self = static_cast<float>(c->d_th_self);
+  k.dth_obs = static_cast<float>(c->d_th_obs);
+  for (int j = 0; j < 7; ++j) {
+    k.lrad[j] = static_cast<float>(c->link_radius[j]);
+    // link j's segment runs from joint j's origin to joint j+1's (the
+    // end-effector point for the last link): a rigid length
+    const double* v = j + 1 < 7 ? rb->joint_xyz[j + 1] : rb->ee_xyz;
+    const double a = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    k.seg_a[j] = static_cast<float>(a);
+    k.seg_ia[j] = a > 1e-12 ? static_cast<float>(1.0 / a) : 0.f;
+  }
   k.fest = c->force_estimate ? 1 : 0;
   for (int a = 0; a < 6; ++a) {
     k.wf6[a] = static_cast<float>(c->w_force6[a]);
@@ -259,29 +305,54 @@ int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, Pr
 // ---------------------------------------------------------------------------
 // launches
 
+template <int FEAT>
+cudaError_t launch_rolled(mppi_s* h, int grid, const float* in, const float* plan, float* S,
+                          float* noise) {
+  const size_t smem = rolled_smem_bytes(h->P.T, ROLLOUT_BLOCK, FEAT);
+  if (noise)
+    rollout_kernel_rolled<true, ROLLOUT_BLOCK, FEAT><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
+        h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, h->d_obs);
+  else
+    rollout_kernel_rolled<false, ROLLOUT_BLOCK, FEAT><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
+        h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, h->d_obs);
+  return cudaGetLastError();
+}
+
+// Opt the rolled kernels of feature set FEAT in to more than 48 KB of
+// dynamic shared memory when horizon T needs it.
+template <int FEAT>
+cudaError_t prepare_rolled(int T) {
+  const size_t smem = rolled_smem_bytes(T, ROLLOUT_BLOCK, FEAT);
+  if (smem <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(rollout_kernel_rolled<true, ROLLOUT_BLOCK, FEAT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(rollout_kernel_rolled<false, ROLLOUT_BLOCK, FEAT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(smem));
+}
+
+cudaError_t prepare_rollout(mppi_s* h) {
+  switch (h->feat) {
+    case FEAT_FEST: return prepare_rolled<FEAT_FEST>(h->P.T);
+    case FEAT_COLL: return prepare_rolled<FEAT_COLL>(h->P.T);
+    case FEAT_FEST | FEAT_COLL: return prepare_rolled<FEAT_FEST | FEAT_COLL>(h->P.T);
+    default: return h->variant == 2 ? prepare_rolled<0>(h->P.T) : cudaSuccess;
+  }
+}
+
 cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float* S, float* noise) {
   const int grid = (h->P.K + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
-  if (h->P.cost.fest) {
-    // the wrench-estimate cost runs in the rolled kernel only
-    const size_t smem = rolled_smem_bytes(h->P.T, ROLLOUT_BLOCK, true);
-    if (noise)
-      rollout_kernel_rolled<true, ROLLOUT_BLOCK, true><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl);
-    else
-      rollout_kernel_rolled<false, ROLLOUT_BLOCK, true><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl);
-    return cudaGetLastError();
+  // the optional cost terms run in the rolled kernel only
+  switch (h->feat) {
+    case FEAT_FEST: return launch_rolled<FEAT_FEST>(h, grid, in, plan, S, noise);
+    case FEAT_COLL: return launch_rolled<FEAT_COLL>(h, grid, in, plan, S, noise);
+    case FEAT_FEST | FEAT_COLL:
+      return launch_rolled<FEAT_FEST | FEAT_COLL>(h, grid, in, plan, S, noise);
+    default: break;
   }
-  if (h->variant == 2) {
-    const size_t smem = rolled_smem_bytes(h->P.T, ROLLOUT_BLOCK);
-    if (noise)
-      rollout_kernel_rolled<true, ROLLOUT_BLOCK><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl);
-    else
-      rollout_kernel_rolled<false, ROLLOUT_BLOCK><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl);
-    return cudaGetLastError();
-  }
+  if (h->variant == 2) return launch_rolled<0>(h, grid, in, plan, S, noise);
   if (noise)
     rollout_kernel<true><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S, noise,
                                                                h->d_prop, h->d_ctl);
@@ -418,12 +489,14 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
     delete h;
     return fail(nullptr, MPPI_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
   }
-  if (h->P.cost.fest && cfg->variant == 1) {
+  h->feat = (h->P.cost.fest ? FEAT_FEST : 0) | (h->P.cost.coll ? FEAT_COLL : 0);
+  if (h->feat && cfg->variant == 1) {
     delete h;
     return fail(nullptr, MPPI_ERR_INVALID_ARG,
-                "the wrench-estimate cost needs the rolled rollout kernel (variant 0 or 2)");
+                "the wrench-estimate and collision costs need the rolled rollout kernel "
+                "(variant 0 or 2)");
   }
-  h->variant = h->P.cost.fest ? 2 : cfg->variant == 0 ? default_variant(cfg->K) : cfg->variant;
+  h->variant = h->feat ? 2 : cfg->variant == 0 ? default_variant(cfg->K) : cfg->variant;
   const int T = cfg->T, K = cfg->K;
   auto bail = [&](cudaError_t e, const char* what) {
     std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
@@ -452,6 +525,14 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
     return bail(e, "cudaMalloc words");
   if ((e = cudaMalloc(&h->d_prop, plan_b)) != cudaSuccess) return bail(e, "cudaMalloc prop");
   if ((e = cudaMalloc(&h->d_ctl, 2 * sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc ctl");
+  if ((e = cudaMalloc(&h->d_obs, sizeof(ObsK))) != cudaSuccess) return bail(e, "cudaMalloc obs");
+  {
+    ObsK ob;
+    fill_obs(cost->n_obstacles, &cost->obstacles[0][0], &ob);
+    if ((e = cudaMemcpy(h->d_obs, &ob, sizeof ob, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e, "obs");
+  }
+  if ((e = prepare_rollout(h)) != cudaSuccess) return bail(e, "rollout shared memory");
   {
     const int ctl[2] = {K, K};
     if ((e = cudaMemcpy(h->d_ctl, ctl, sizeof ctl, cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -496,6 +577,7 @@ int mppi_destroy(mppi_t h) {
   cudaFree(h->d_words);
   cudaFree(h->d_prop);
   cudaFree(h->d_ctl);
+  cudaFree(h->d_obs);
   cudaFree(h->d_out);
   cudaFree(h->d_iter);
   if (h->h_in) cudaFreeHost(h->h_in);
@@ -745,6 +827,33 @@ int mppi_gravity_torque(mppi_t h, const float q[7], float tau_out[7]) {
   CUDA_TRY(h, cudaGetLastError());
   CUDA_TRY(h, cudaMemcpyAsync(tau_out, h->d_misc + 16, 7 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPPI_OK;
+}
+
+int mppi_set_obstacles(mppi_t h, int n, const float* obs) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (n < 0 || n > MPPI_OBS_MAX || (n > 0 && !obs))
+    return fail(h, MPPI_ERR_INVALID_ARG, "n must be in 0..8 with obstacles given");
+  for (int i = 0; i < 7 * n; ++i)
+    if (!std::isfinite(obs[i])) return fail(h, MPPI_ERR_INVALID_ARG, "obstacles must be finite");
+  for (int o = 0; o < n; ++o)
+    if (obs[7 * o + 6] < 0.f) return fail(h, MPPI_ERR_INVALID_ARG, "obstacle radii must be >= 0");
+  ObsK ob;
+  fill_obs(n, obs, &ob);
+  // pageable source: the call returns once the image has been staged
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_obs, &ob, sizeof ob, cudaMemcpyHostToDevice, h->stream));
+  return MPPI_OK;
+}
+
+int mppi_set_obstacles_device(mppi_t h, int n, const float* d_obs) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (n < 0 || n > MPPI_OBS_MAX || (n > 0 && !d_obs))
+    return fail(h, MPPI_ERR_INVALID_ARG, "n must be in 0..8 with obstacles given");
+  if (n > 0)
+    CUDA_TRY(h, cudaMemcpyAsync(&h->d_obs->o[0][0], d_obs, sizeof(float) * 7 * n,
+                                cudaMemcpyDeviceToDevice, h->stream));
+  set_int_kernel<<<1, 32, 0, h->stream>>>(&h->d_obs->n, n);
+  CUDA_TRY(h, cudaGetLastError());
   return MPPI_OK;
 }
 

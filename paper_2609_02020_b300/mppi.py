@@ -15,6 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmppi.so")
 
 NJ = 7
+OBS_MAX = 8  # MPPI_OBS_MAX
 IN_FLOATS = 25
 
 OK = 0
@@ -74,6 +75,13 @@ class Cost(C.Structure):
         ("w_force6", C.c_double * 6),
         ("f_des6", C.c_double * 6),
         ("w_reg6", C.c_double * 6),
+        ("collision", C.c_int),
+        ("w_collision", C.c_double),
+        ("d_th_self", C.c_double),
+        ("d_th_obs", C.c_double),
+        ("link_radius", C.c_double * NJ),
+        ("n_obstacles", C.c_int),
+        ("obstacles", C.c_double * 7 * OBS_MAX),
     ]
 
 
@@ -125,7 +133,7 @@ EXPORTS = [
     "mppi_noise_words", "mppi_step_static", "mppi_last_error", "mppi_version",
     "mppi_simulate_device", "mppi_set_plan_device", "mppi_get_plan_device",
     "mppi_get_updated_plan_device", "mppi_set_proposal_device", "mppi_gravity_torque",
-    "mppi_force_estimate_device",
+    "mppi_force_estimate_device", "mppi_set_obstacles", "mppi_set_obstacles_device",
     # include/mppi_serve.h
     "mppi_pool_create", "mppi_pool_destroy", "mppi_pool_alloc", "mppi_pool_free",
     "mppi_pool_stats", "mppi_server_create", "mppi_server_destroy", "mppi_server_add_problem",
@@ -185,6 +193,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_set_proposal_device": ([H, vp, C.c_int], C.c_int),
         "mppi_gravity_torque": ([H, fp, fp], C.c_int),
         "mppi_force_estimate_device": ([H, vp, vp, C.c_int, vp], C.c_int),
+        "mppi_set_obstacles": ([H, C.c_int, fp], C.c_int),
+        "mppi_set_obstacles_device": ([H, C.c_int, vp], C.c_int),
         "mppi_pool_create": ([C.c_size_t, C.POINTER(C.c_void_p)], C.c_int),
         "mppi_pool_destroy": ([H], C.c_int),
         "mppi_pool_alloc": ([H, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
@@ -286,6 +296,19 @@ def cost_struct(d: dict) -> Cost:
         dst = getattr(c, name)
         for a in range(6):
             dst[a] = v[a]
+    c.collision = int(d.get("collision", 0))
+    for name in ("w_collision", "d_th_self", "d_th_obs"):
+        setattr(c, name, float(d.get(name, 0.0)))
+    lr = np.asarray(d.get("link_radius", np.zeros(NJ)), dtype=np.float64).reshape(NJ)
+    for j in range(NJ):
+        c.link_radius[j] = lr[j]
+    obs = np.asarray(d.get("obstacles", np.zeros((0, 7))), dtype=np.float64).reshape(-1, 7)
+    if obs.shape[0] > OBS_MAX:
+        raise ValueError(f"at most {OBS_MAX} obstacles")
+    c.n_obstacles = obs.shape[0]
+    for o in range(obs.shape[0]):
+        for a in range(7):
+            c.obstacles[o][a] = obs[o, a]
     return c
 
 
@@ -418,6 +441,15 @@ class MPPI:
         out = np.zeros(7, dtype=np.float32)
         self._check(self.lib.mppi_gravity_torque(self.h, _fp(_f32(q, NJ)), _fp(out)))
         return out
+
+    def set_obstacles(self, obs):
+        """Obstacle capsules [n][7] (a xyz, b xyz, radius) for the following updates."""
+        o = np.ascontiguousarray(np.asarray(obs, dtype=np.float32).reshape(-1, 7))
+        self._check(self.lib.mppi_set_obstacles(self.h, int(o.shape[0]), _fp(o.reshape(-1))))
+
+    def set_obstacles_device(self, d_obs):
+        """The same from a device tensor [n][7] (stream-ordered)."""
+        self._check(self.lib.mppi_set_obstacles_device(self.h, int(d_obs.shape[0]), _dptr(d_obs)))
 
     def force_estimate_device(self, d_q, d_v, d_F):
         """Wrench estimates F = Jbar^T (v - g(q)) (Eq. 13): d_q, d_v [n][7] ->

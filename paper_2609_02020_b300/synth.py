@@ -141,6 +141,37 @@ def cost_force_estimate(w_fz: float = 1e-3, base: dict | None = None) -> dict:
     return c
 
 
+def cost_collision(mode: int = 1, w: float = 10.0, base: dict | None = None,
+                   th_self: float = 0.05, th_obs: float = 0.2, obstacles=None) -> dict:
+    """C_collision of Eq. 15 added to a free-space cost: link capsules of the
+    rod radius, link-link threshold th_self, link-object threshold th_obs
+    (0.2 m as in the paper's obstacle experiment); mode 1 indicator, 2
+    squared hinge."""
+    c = dict(cost_free_space() if base is None else base)
+    c.update(collision=mode, w_collision=w, d_th_self=th_self, d_th_obs=th_obs,
+             link_radius=np.full(N_JOINTS, ROD_RADIUS),
+             obstacles=np.zeros((0, 7)) if obstacles is None else np.asarray(obstacles, float))
+    return c
+
+
+def obstacles_near(points: np.ndarray, seed: int, count: int = 3, dist=(0.12, 0.3),
+                   radius: float = 0.05) -> np.ndarray:
+    """`count` capsule obstacles (a xyz, b xyz, radius) beside seeded
+    choices of the given link points, at a distance drawn from `dist`, each
+    0.05-0.2 m long in a random direction."""
+    g = _rng(seed, _BATCH + 1)
+    out = np.zeros((count, 7))
+    for o in range(count):
+        p = points[g.integers(1, len(points))]
+        u = g.normal(size=3)
+        u /= np.linalg.norm(u)
+        c = p + g.uniform(*dist) * u
+        a = g.normal(size=3)
+        a *= g.uniform(0.05, 0.2) / (2 * np.linalg.norm(a))
+        out[o, :3], out[o, 3:6], out[o, 6] = c - a, c + a, radius
+    return out
+
+
 def plane_through(point_z: float, penetration: float = 0.02) -> np.ndarray:
     """Horizontal plane n = (0, 0, 1) with offset d placed `penetration` above
     a given height (so a point at that height starts inside the contact)."""

@@ -80,3 +80,18 @@ def test_create_rejects_bad_wrench_estimate_cost():
     c = dict(synth.cost_free_space(), force_estimate=1, w_force6=np.ones(6))
     with pytest.raises(mppi.MPPIError, match="rolled"):
         _create(cost=c, variant=1)
+
+
+def test_create_rejects_bad_collision_cost():
+    ok = synth.cost_collision(1, obstacles=np.array([[0, 0, 1, 0, 0, 1.2, 0.05]]))
+    for bad, msg in [(dict(collision=3), "collision must"),
+                     (dict(w_collision=float("nan")), "finite"),
+                     (dict(link_radius=np.full(7, -0.01)), "radii"),
+                     (dict(obstacles=np.array([[0, 0, 1, 0, 0, 1.2, -0.05]])), "obstacle radii"),
+                     (dict(obstacles=np.array([[0, 0, np.inf, 0, 0, 1.2, 0.05]])), "finite")]:
+        with pytest.raises(mppi.MPPIError, match=msg):
+            _create(cost=dict(ok, **bad))
+    with pytest.raises(mppi.MPPIError, match="rolled"):
+        _create(cost=ok, variant=1)
+    with pytest.raises(ValueError):
+        _create(cost=dict(ok, obstacles=np.zeros((9, 7))))
