@@ -72,7 +72,8 @@ def parse():
     ap.add_argument("--budget-s", type=float, default=120.0,
                     help="reference arm: wall-clock budget of the whole run [s]")
     ap.add_argument("--variant", type=int, default=0,
-                    help="rollout kernel: 0 library default, 1 unrolled, 2 rolled")
+                    help="rollout kernel: 0 library default, 1 unrolled, 2 rolled, "
+                         "3 warp-specialised")
     ap.add_argument("--cost", default="contact", choices=list(COSTS),
                     help="update mode: the plane-contact workload (default), or the same with "
                          "C_force on the wrench estimate of Eq. 13, or with the collision "
@@ -301,7 +302,8 @@ def run_ours(args, rank, world):
     # the optional cost terms run in the rolled kernel; otherwise variant 0
     # picks it for K <= 32768
     rolled = args.variant == 2 or (args.variant == 0 and (args.cost != "contact" or K <= 32768))
-    kname = "rollout_kernel_rolled" if rolled else "rollout_kernel"
+    kname = ("rollout_kernel_ws" if args.variant == 3 else
+             "rollout_kernel_rolled" if rolled else "rollout_kernel")
     plane = synth.plane_through(float(pose[2]))
     d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, plane), device="cuda")
     d_tau = torch.zeros(7, device="cuda")

@@ -156,7 +156,9 @@ typedef struct mppi_config {
   int reduce_fp64;  /* 0: FP32 weight reduction; 1: FP64 accumulators       */
   int use_graph;    /* 1: mppi_step replays a captured CUDA graph            */
   int variant;      /* rollout kernel: 0 default, 1 links unrolled in registers,
-                       2 link loops rolled through shared memory             */
+                       2 link loops rolled through shared memory, 3 three
+                       warps per 32 samples (kinematic chain / link forces and
+                       costs / link forces and noise)                        */
 } mppi_config;
 
 #define MPPI_T_MAX 256

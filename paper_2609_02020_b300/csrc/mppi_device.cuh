@@ -196,10 +196,10 @@ __device__ __forceinline__ void chain_init(const RobotK& rb, ChainState& c) {
   }
 }
 
-// One link of the forward sweep: joint transform, link spatial inertia about
-// O, velocity, bias acceleration and the RNEA link force.
-__device__ __forceinline__ void forward_link(const LinkK& L, float qi, float qdi, ChainState& c,
-                                             LinkState& S) {
+// Frame of link i in the forward sweep: world rotation and origin of link
+// i's frame, joint axis z and w = p x z.
+__device__ __forceinline__ void forward_link_frame(const LinkK& L, float qi, ChainState& c,
+                                                   float z[3], float w[3]) {
   float d[3];
   mv3(c.R, L.r, d);
   c.p[0] += d[0]; c.p[1] += d[1]; c.p[2] += d[2];
@@ -215,12 +215,46 @@ __device__ __forceinline__ void forward_link(const LinkK& L, float qi, float qdi
     c.R[3 * r + 1] = fmaf(co, c1, -s * c0);
     c.R[3 * r + 2] = RF[3 * r + 2];
   }
-  const float* R = c.R;
-  const float* p = c.p;
-  S.z[0] = R[2]; S.z[1] = R[5]; S.z[2] = R[8];
-  cross3(p, S.z, S.w);
+  z[0] = c.R[2]; z[1] = c.R[5]; z[2] = c.R[8];
+  cross3(c.p, z, w);
+}
 
-  // spatial inertia of the link about O
+// Spatial velocity and bias acceleration after a joint with motion axis
+// (z, w) and speed qdi.
+__device__ __forceinline__ void forward_link_motion(const float z[3], const float w[3], float qdi,
+                                                    float Vw[3], float Vv[3], float Aw[3],
+                                                    float Av[3]) {
+  const float jw[3] = {z[0] * qdi, z[1] * qdi, z[2] * qdi};
+  const float jv[3] = {w[0] * qdi, w[1] * qdi, w[2] * qdi};
+  float t0[3], t1[3], t2[3];
+  cross3(Vw, jw, t0);  // (V x S qd) angular
+  cross3(Vw, jv, t1);
+  cross3(Vv, jw, t2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Aw[a] += t0[a];
+    Av[a] += t1[a] + t2[a];
+    Vw[a] += jw[a];
+    Vv[a] += jv[a];
+  }
+}
+
+// Chain part of one link of the forward sweep: the frame, then the velocity
+// and bias acceleration after link i.
+__device__ __forceinline__ void forward_link_chain(const LinkK& L, float qi, float qdi,
+                                                   ChainState& c, float z[3], float w[3]) {
+  forward_link_frame(L, qi, c, z, w);
+  forward_link_motion(z, w, qdi, c.Vw, c.Vv, c.Aw, c.Av);
+}
+
+// Force part of one link of the forward sweep, from the link frame (R, p)
+// and the link's spatial velocity V = (Vw, Vv) and bias acceleration
+// A = (Aw, Av): the link spatial inertia about O and the RNEA link force
+// F = I A + V x* (I V).
+__device__ __forceinline__ void forward_link_force(const LinkK& L, const float R[9],
+                                                   const float p[3], const float Vw[3],
+                                                   const float Vv[3], const float Aw[3],
+                                                   const float Av[3], float In[10], float F[6]) {
   float cw[3];
   mv3(R, L.c, cw);
   cw[0] += p[0]; cw[1] += p[1]; cw[2] += p[2];
@@ -234,7 +268,6 @@ __device__ __forceinline__ void forward_link(const LinkK& L, float qi, float qdi
   }
   const float m = L.m;
   const float cc = dot3(cw, cw);
-  float* In = S.In;
   In[0] = m;
   In[1] = m * cw[0]; In[2] = m * cw[1]; In[3] = m * cw[2];
   In[4] = fmaf(Tm[0], R[0], fmaf(Tm[1], R[1], Tm[2] * R[2])) + m * (cc - cw[0] * cw[0]);
@@ -243,34 +276,27 @@ __device__ __forceinline__ void forward_link(const LinkK& L, float qi, float qdi
   In[7] = fmaf(Tm[0], R[3], fmaf(Tm[1], R[4], Tm[2] * R[5])) - m * cw[0] * cw[1];
   In[8] = fmaf(Tm[0], R[6], fmaf(Tm[1], R[7], Tm[2] * R[8])) - m * cw[0] * cw[2];
   In[9] = fmaf(Tm[3], R[6], fmaf(Tm[4], R[7], Tm[5] * R[8])) - m * cw[1] * cw[2];
-
-  // velocity and bias acceleration
-  const float jw[3] = {S.z[0] * qdi, S.z[1] * qdi, S.z[2] * qdi};
-  const float jv[3] = {S.w[0] * qdi, S.w[1] * qdi, S.w[2] * qdi};
-  float t0[3], t1[3], t2[3];
-  cross3(c.Vw, jw, t0);  // (V x S qd) angular
-  cross3(c.Vw, jv, t1);
-  cross3(c.Vv, jw, t2);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    c.Aw[a] += t0[a];
-    c.Av[a] += t1[a] + t2[a];
-    c.Vw[a] += jw[a];
-    c.Vv[a] += jv[a];
-  }
   // F = I A + V x* (I V)
   float HA[3], LA[3], HV[3], LV[3];
-  inertia_apply(In, c.Aw, c.Av, HA, LA);
-  inertia_apply(In, c.Vw, c.Vv, HV, LV);
+  inertia_apply(In, Aw, Av, HA, LA);
+  inertia_apply(In, Vw, Vv, HV, LV);
   float a0[3], a1[3], a2[3];
-  cross3(c.Vw, HV, a0);
-  cross3(c.Vv, LV, a1);
-  cross3(c.Vw, LV, a2);
+  cross3(Vw, HV, a0);
+  cross3(Vv, LV, a1);
+  cross3(Vw, LV, a2);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    S.F[a] = HA[a] + a0[a] + a1[a];
-    S.F[3 + a] = LA[a] + a2[a];
+    F[a] = HA[a] + a0[a] + a1[a];
+    F[3 + a] = LA[a] + a2[a];
   }
+}
+
+// One link of the forward sweep: joint transform, link spatial inertia about
+// O, velocity, bias acceleration and the RNEA link force.
+__device__ __forceinline__ void forward_link(const LinkK& L, float qi, float qdi, ChainState& c,
+                                             LinkState& S) {
+  forward_link_chain(L, qi, qdi, c, S.z, S.w);
+  forward_link_force(L, c.R, c.p, c.Vw, c.Vv, c.Aw, c.Av, S.In, S.F);
 }
 
 // End-effector pose and linear velocity from the last link's chain state.

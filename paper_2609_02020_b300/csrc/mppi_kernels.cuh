@@ -598,6 +598,377 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
                                                      s_obs, n_obs);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised rollout: three warps share 32 samples (lane l of every
+// warp works on the block's sample l) so that one sample's step no longer
+// runs on a single dependency chain.  For each state x_s (s = 0..T):
+//   link phase: warp 0 walks the kinematic chain (link frames, joint axes,
+//     velocities and bias accelerations) and hands each link over; warp 1
+//     forms the link inertias and RNEA forces of the even links, warp 2 of
+//     the odd ones, and warp 2 then forms the end-effector point and contact
+//     force for the dynamics.
+//   For s < T, after the forces: h and the rows of M are split over the
+//     three warps (each forms the composite inertias it needs); warp 0
+//     factorises M, waits for the step's inputs, solves for qdd and takes the
+//     Euler step to x_{s+1}; warp 1 copies x_s and then charges
+//     l(x_s, v_{s-1}); warp 2 draws v_{s+1} one step ahead (v_0 at s = 0).
+//   At s = T warp 1 charges l(x_T, v_{T-1}) and phi(x_T).
+// Hand-offs go through shared memory under named barriers with fixed
+// arrival counts.  Per state every barrier sees the same arrivals, and each
+// slot is rewritten only after its readers have passed a barrier that the
+// writer waits on first, so no wait depends on data.  Same arithmetic as
+// rollout_sample, in the same order per quantity.
+
+constexpr int WS_B = 32;              // samples per block
+constexpr int WS_THREADS = 3 * WS_B;  // three warps
+constexpr int CHAIN_FIELDS = 24;      // R 9, p 3, Vw 3, Vv 3, Aw 3, Av 3
+constexpr int EE_FIELDS = 4;          // end-effector point 3, contact force
+constexpr int V_SLOTS = 3;            // ring of inputs v_s, slot s % 3
+// named barriers (0 is __syncthreads): one per link, link forces complete,
+// rows of M complete, inputs of the step complete
+constexpr int BAR_LINK0 = 1, BAR_FORCES = 8, BAR_MROWS = 9, BAR_STEP = 10;
+constexpr int WS_FLOATS_PER_SAMPLE = NJ * LINK_FIELDS + NJ * CHAIN_FIELDS + NJ * (NJ + 1) / 2 +
+                                     NJ /* h */ + 2 * NJ /* q, qd */ +
+                                     V_SLOTS * NJ /* v ring */ + EE_FIELDS;
+
+__device__ __forceinline__ void bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Threads at link i's barrier: warp 0 and the force warp of link i, and for
+// the last link also the other force warp (it forms the end-effector state)
+// while s < T; at s = T only the last link's barrier runs, for warp 1.
+__host__ __device__ constexpr int ws_link_count(int i, bool last_state) {
+  return last_state ? 2 * WS_B : (i == NJ - 1 ? 3 * WS_B : 2 * WS_B);
+}
+
+// Dynamic shared memory of rollout_kernel_ws for horizon T.
+__host__ __device__ constexpr size_t ws_smem_bytes(int T) {
+  return sizeof(float) * (2 * static_cast<size_t>((T * NJ + 3) / 4 * 4) + 32 +
+                          static_cast<size_t>(WS_FLOATS_PER_SAMPLE) * WS_B);
+}
+
+struct WsSmem {
+  float *sl, *sc, *sM, *sh, *sq, *sqd, *sv, *se;
+};
+
+__device__ __forceinline__ WsSmem ws_carve(float* base) {
+  constexpr int B = WS_B;
+  WsSmem m;
+  m.sl = base;                              // [7][22][B]: z, w (warp 0); F, In (warps 1, 2)
+  m.sc = m.sl + NJ * LINK_FIELDS * B;       // [7][24][B]: link frame and motion hand-off
+  m.sM = m.sc + NJ * CHAIN_FIELDS * B;      // [28][B]
+  m.sh = m.sM + (NJ * (NJ + 1) / 2) * B;    // [7][B]
+  m.sq = m.sh + NJ * B;                     // [7][B]
+  m.sqd = m.sq + NJ * B;                    // [7][B]
+  m.sv = m.sqd + NJ * B;                    // [3][7][B]: v_s in slot s % 3
+  m.se = m.sv + V_SLOTS * NJ * B;           // [4][B]: end-effector point, contact force
+  return m;
+}
+
+// Rows [i] of M and, with H_OUT, h: the backward sweep of backward_link
+// down to the lowest listed row.  rows: bit i set for row i.
+template <bool H_OUT>
+__device__ __forceinline__ void ws_backward(const RobotK& rb, const WsSmem& m, unsigned rows,
+                                            int tid) {
+  constexpr int B = WS_B;
+  float Fs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float Ic[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int lowest = H_OUT ? 0 : __ffs(rows) - 1;
+#pragma unroll 1
+  for (int i = NJ - 1; i >= lowest; --i) {
+    LinkState S;
+    load_link<B>(m.sl, i, tid, S);
+    float H[3], Lm[3];
+    const float hi = backward_link(rb.L[i], m.sqd[i * B + tid], S, Fs, Ic, H, Lm);
+    if (H_OUT) m.sh[i * B + tid] = hi;
+    if (rows & (1u << i)) {
+      const int row = i * (i + 1) / 2;
+#pragma unroll 1
+      for (int j = 0; j < i; ++j) {
+        float zj[3], wj[3];
+        load_axis<B>(m.sl, j, tid, zj, wj);
+        m.sM[(row + j) * B + tid] = dot3(zj, H) + dot3(wj, Lm);
+      }
+      m.sM[(row + i) * B + tid] = dot3(S.z, H) + dot3(S.w, Lm) + rb.L[i].arm;
+    }
+  }
+}
+
+// Rows of M per warp (each costs about 30 + 6 i, plus the composite inertias
+// down to the lowest row); warp 0 also forms h.
+constexpr unsigned WS_ROWS0 = 1u << 6;
+constexpr unsigned WS_ROWS1 = (1u << 5) | (1u << 2) | (1u << 1);
+constexpr unsigned WS_ROWS2 = (1u << 4) | (1u << 3) | (1u << 0);
+
+__device__ __forceinline__ void ws_load_chain(const WsSmem& m, int i, int tid, ChainState& c) {
+  constexpr int B = WS_B;
+  const float* h = m.sc + i * CHAIN_FIELDS * B + tid;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) c.R[a] = h[a * B];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    c.p[a] = h[(9 + a) * B];
+    c.Vw[a] = h[(12 + a) * B];
+    c.Vv[a] = h[(15 + a) * B];
+    c.Aw[a] = h[(18 + a) * B];
+    c.Av[a] = h[(21 + a) * B];
+  }
+}
+
+// warp 0
+__device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, const WsSmem& m,
+                                            int tid) {
+  constexpr int B = WS_B;
+  const int T = P.T;
+  const CostK& C = P.cost;
+  const bool contact = C.contact != 0;
+  const float plane[4] = {in[21], in[22], in[23], in[24]};
+  float q[NJ], qd[NJ];
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    q[j] = in[j];
+    qd[j] = in[NJ + j];
+    m.sq[j * B + tid] = q[j];
+    m.sqd[j * B + tid] = qd[j];
+  }
+  for (int s = 0; s <= T; ++s) {
+    const bool last = s == T;
+    // link phase: the chain at x_s, handed over link by link
+    ChainState c;
+    chain_init(P.rb, c);
+#pragma unroll 1
+    for (int i = 0; i < NJ; ++i) {
+      float z[3], w[3];
+      forward_link_chain(P.rb.L[i], m.sq[i * B + tid], m.sqd[i * B + tid], c, z, w);
+      float* l = m.sl + i * LINK_FIELDS * B + tid;
+      float* h = m.sc + i * CHAIN_FIELDS * B + tid;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        l[a * B] = z[a];
+        l[(3 + a) * B] = w[a];
+        h[(9 + a) * B] = c.p[a];
+        h[(12 + a) * B] = c.Vw[a];
+        h[(15 + a) * B] = c.Vv[a];
+        h[(18 + a) * B] = c.Aw[a];
+        h[(21 + a) * B] = c.Av[a];
+      }
+#pragma unroll
+      for (int a = 0; a < 9; ++a) h[a * B] = c.R[a];
+      if (!last || i == NJ - 1) bar_arrive(BAR_LINK0 + i, ws_link_count(i, last));
+    }
+    if (last) break;
+    bar_sync(BAR_FORCES, 3 * B);
+    ws_backward<true>(P.rb, m, WS_ROWS0, tid);
+    bar_sync(BAR_MROWS, 3 * B);
+    float M[NJ * (NJ + 1) / 2], invD[NJ];
+#pragma unroll
+    for (int a = 0; a < NJ * (NJ + 1) / 2; ++a) M[a] = m.sM[a * B + tid];
+    ldlt_factor<NJ>(M, invD);
+    bar_sync(BAR_STEP, 3 * B);
+    const float* v = m.sv + (s % V_SLOTS) * NJ * B + tid;
+    const float f = m.se[3 * B + tid];
+    float rhs[NJ];
+    if (contact && f > 0.f) {
+      const float pe[3] = {m.se[tid], m.se[B + tid], m.se[2 * B + tid]};
+      const float Fc[3] = {f * plane[0], f * plane[1], f * plane[2]};
+      float pxF[3];
+      cross3(pe, Fc, pxF);
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        float zj[3], wj[3];
+        load_axis<B>(m.sl, j, tid, zj, wj);
+        rhs[j] = v[j * B] + dot3(zj, pxF) + dot3(wj, Fc) - m.sh[j * B + tid];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) rhs[j] = v[j * B] - m.sh[j * B + tid];
+    }
+    float y[NJ], qdd[NJ];
+    unit_lower_solve<NJ>(M, rhs, y);
+    ldlt_back<NJ>(M, invD, y, qdd);
+    const float dt = P.dt;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      qd[j] = fmaf(qdd[j], dt, qd[j]);
+      q[j] = fmaf(qd[j], dt, q[j]);
+      m.sq[j * B + tid] = q[j];
+      m.sqd[j * B + tid] = qd[j];
+    }
+  }
+}
+
+// warps 1 and 2, link phase: inertias and forces of links first, first + 2, ...
+__device__ __forceinline__ void ws_forces(const ProbK& P, const WsSmem& m, int first, int tid) {
+  constexpr int B = WS_B;
+#pragma unroll 1
+  for (int i = first; i < NJ; i += 2) {
+    bar_sync(BAR_LINK0 + i, ws_link_count(i, false));
+    ChainState c;
+    ws_load_chain(m, i, tid, c);
+    float In[10], F[6];
+    forward_link_force(P.rb.L[i], c.R, c.p, c.Vw, c.Vv, c.Aw, c.Av, In, F);
+    float* l = m.sl + i * LINK_FIELDS * B + tid;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) l[(6 + a) * B] = F[a];
+#pragma unroll
+    for (int a = 0; a < 10; ++a) l[(12 + a) * B] = In[a];
+  }
+}
+
+// warp 1: forces of the even links and the running cost; returns S_k
+__device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const WsSmem& m,
+                                          int tid) {
+  constexpr int B = WS_B;
+  const int T = P.T;
+  const CostK& C = P.cost;
+  const bool contact = C.contact != 0;
+  const float pdes[3] = {in[14], in[15], in[16]};
+  float Rd[9];
+  {
+    const float qt[4] = {in[17], in[18], in[19], in[20]};
+    quat_to_R(qt, Rd);
+  }
+  const float plane[4] = {in[21], in[22], in[23], in[24]};
+  double Sacc = 0.0;
+  for (int s = 0; s <= T; ++s) {
+    ChainState c;
+    if (s < T) {
+      ws_forces(P, m, 0, tid);  // ends with the last link (even)
+      ws_load_chain(m, NJ - 1, tid, c);
+      bar_sync(BAR_FORCES, 3 * B);
+      ws_backward<false>(P.rb, m, WS_ROWS1, tid);
+      bar_arrive(BAR_MROWS, 3 * B);
+    } else {
+      bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, true));
+      ws_load_chain(m, NJ - 1, tid, c);
+    }
+    // x_s and v_{s-1}, copied before warp 0 may overwrite them
+    float q[NJ], qd[NJ], v[NJ];
+    const float* vp = m.sv + ((s + V_SLOTS - 1) % V_SLOTS) * NJ * B + tid;  // v_{s-1}
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      q[j] = m.sq[j * B + tid];
+      qd[j] = m.sqd[j * B + tid];
+      v[j] = vp[j * B];
+    }
+    if (s < T) bar_arrive(BAR_STEP, 3 * B);
+    if (s == 0) continue;
+    // running cost l(x_s, v_{s-1}), Eq. 9-14
+    EEState ee;
+    chain_ee(P.rb, c, ee);
+    float cst = motion_cost(C, pdes, Rd, ee);
+    if (contact) {
+      const float f = contact_force(C, plane, ee);
+      const float ef = C.fdes - f;
+      cst += C.wforce * ef * ef + C.wreg * f * f;
+    }
+    float cj = 0.f;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      cj += C.wqlim * (hinge2(q[j] - P.rb.qmax[j]) + hinge2(P.rb.qmin[j] - q[j]));
+      cj += C.wqdlim * hinge2(fabsf(qd[j]) - P.rb.qdmax[j]);
+      const float ep = q[j] - C.qpost[j];
+      cj += C.wpost * ep * ep;
+      cj += C.wtau * hinge2(fabsf(v[j]) - P.rb.taumax[j]);
+    }
+    Sacc += static_cast<double>(cst) + static_cast<double>(cj);
+    if (s == T && C.wterm != 0.f)
+      Sacc += static_cast<double>(C.wterm * motion_cost(C, pdes, Rd, ee));
+  }
+  return static_cast<float>(Sacc);
+}
+
+// warp 2: the inputs v_s = u_s + dtau_s (Eq. 2) into slot s % 3
+template <bool STORE_NOISE>
+__device__ __forceinline__ void ws_draw(const ProbK& P, const float* plan, uint64_t iter, int k,
+                                        bool live, float* __restrict__ noise, const WsSmem& m,
+                                        int s, int tid) {
+  constexpr int B = WS_B;
+  const int K = P.K;
+  float z[8];
+  normals8(P.key0, P.key1, iter, static_cast<uint32_t>(k), static_cast<uint32_t>(s), z);
+  float* v = m.sv + (s % V_SLOTS) * NJ * B + tid;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const float du = P.sigma[j] * z[j];
+    if (STORE_NOISE && live) noise[static_cast<size_t>(s * NJ + j) * K + k] = du;
+    v[j * B] = plan[s * NJ + j] + du;
+  }
+}
+
+// warp 2: forces of the odd links, the end-effector point and contact force
+// for the dynamics, and the inputs one step ahead
+template <bool STORE_NOISE>
+__device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const float* plan,
+                                         uint64_t iter, int k, bool live,
+                                         float* __restrict__ noise, const WsSmem& m, int tid) {
+  constexpr int B = WS_B;
+  const int T = P.T;
+  const CostK& C = P.cost;
+  const bool contact = C.contact != 0;
+  const float plane[4] = {in[21], in[22], in[23], in[24]};
+  for (int s = 0; s < T; ++s) {
+    ws_forces(P, m, 1, tid);
+    {
+      bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, false));
+      ChainState c;
+      ws_load_chain(m, NJ - 1, tid, c);
+      EEState ee;
+      chain_ee(P.rb, c, ee);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) m.se[a * B + tid] = ee.p[a];
+      m.se[3 * B + tid] = contact ? contact_force(C, plane, ee) : 0.f;
+    }
+    bar_sync(BAR_FORCES, 3 * B);
+    ws_backward<false>(P.rb, m, WS_ROWS2, tid);
+    bar_arrive(BAR_MROWS, 3 * B);
+    if (s == 0) ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, 0, tid);
+    bar_arrive(BAR_STEP, 3 * B);
+    if (s + 1 < T) ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, s + 1, tid);
+  }
+}
+
+template <bool STORE_NOISE>
+__global__ void __launch_bounds__(WS_THREADS)
+rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
+                  const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
+                  float* __restrict__ S, float* __restrict__ noise,
+                  const float* __restrict__ prop = nullptr,
+                  const int* __restrict__ ksplit_p = nullptr) {
+  extern __shared__ float dsm[];
+  const int T = P.T, K = P.K;
+  const int k_split = ksplit_p ? *ksplit_p : K;
+  const int pstride = (T * NJ + 3) / 4 * 4;
+  float* s_plan = dsm;
+  float* s_prop = dsm + pstride;
+  float* s_in = s_prop + pstride;
+  for (int i = threadIdx.x; i < T * NJ; i += WS_THREADS) s_plan[i] = plan[i];
+  if (k_split < K)
+    for (int i = threadIdx.x; i < T * NJ; i += WS_THREADS) s_prop[i] = prop[i];
+  if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
+  __syncthreads();
+  const WsSmem m = ws_carve(s_in + 32);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // lanes past K run sample K - 1 so that every warp meets every barrier;
+  // they write nothing
+  const int k_raw = blockIdx.x * WS_B + lane;
+  const bool live = k_raw < K;
+  const int k = live ? k_raw : K - 1;
+  if (warp == 0) {
+    ws_dynamics(P, s_in, m, lane);
+  } else if (warp == 1) {
+    const float Sk = ws_costs(P, s_in, m, lane);
+    if (live) S[k] = Sk;
+  } else {
+    ws_noise<STORE_NOISE>(P, s_in, k < k_split ? s_plan : s_prop, *iter_p, k, live, noise, m,
+                          lane);
+  }
+}
+
 // Wrench estimates F = Jbar^T (v - g(q)) (Eq. 13) for n pairs (q_i, v_i),
 // [n][7] each, into F [n][6] (NaN rows at kinematic singularities), with the
 // rollouts' own kinematics, dynamics and estimate.  Block B, dynamic shared

@@ -338,8 +338,19 @@ cudaError_t prepare_rollout(mppi_s* h) {
     case FEAT_FEST: return prepare_rolled<FEAT_FEST>(h->P.T);
     case FEAT_COLL: return prepare_rolled<FEAT_COLL>(h->P.T);
     case FEAT_FEST | FEAT_COLL: return prepare_rolled<FEAT_FEST | FEAT_COLL>(h->P.T);
-    default: return h->variant == 2 ? prepare_rolled<0>(h->P.T) : cudaSuccess;
+    default: break;
   }
+  if (h->variant == 2) return prepare_rolled<0>(h->P.T);
+  if (h->variant == 3) {
+    const size_t smem = ws_smem_bytes(h->P.T);
+    cudaError_t e = cudaFuncSetAttribute(rollout_kernel_ws<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(rollout_kernel_ws<false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float* S, float* noise) {
@@ -353,6 +364,17 @@ cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float*
     default: break;
   }
   if (h->variant == 2) return launch_rolled<0>(h, grid, in, plan, S, noise);
+  if (h->variant == 3) {
+    const int wgrid = (h->P.K + WS_B - 1) / WS_B;
+    const size_t smem = ws_smem_bytes(h->P.T);
+    if (noise)
+      rollout_kernel_ws<true><<<wgrid, WS_THREADS, smem, h->stream>>>(
+          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl);
+    else
+      rollout_kernel_ws<false><<<wgrid, WS_THREADS, smem, h->stream>>>(
+          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl);
+    return cudaGetLastError();
+  }
   if (noise)
     rollout_kernel<true><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S, noise,
                                                                h->d_prop, h->d_ctl);
@@ -485,12 +507,12 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
   }
   h->reduce_fp64 = cfg->reduce_fp64 ? 1 : 0;
   h->use_graph = cfg->use_graph ? 1 : 0;
-  if (cfg->variant < 0 || cfg->variant > 2) {
+  if (cfg->variant < 0 || cfg->variant > 3) {
     delete h;
-    return fail(nullptr, MPPI_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+    return fail(nullptr, MPPI_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   }
   h->feat = (h->P.cost.fest ? FEAT_FEST : 0) | (h->P.cost.coll ? FEAT_COLL : 0);
-  if (h->feat && cfg->variant == 1) {
+  if (h->feat && (cfg->variant == 1 || cfg->variant == 3)) {
     delete h;
     return fail(nullptr, MPPI_ERR_INVALID_ARG,
                 "the wrench-estimate and collision costs need the rolled rollout kernel "

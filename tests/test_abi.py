@@ -42,6 +42,7 @@ def _create(arm=None, cost=None, **kw):
     (dict(K=0), "K must"), (dict(K=(1 << 22) + 1), "K must"), (dict(T=0), "T must"),
     (dict(T=257), "T must"), (dict(lam=0.0), "lambda"), (dict(lam=-1.0), "lambda"),
     (dict(dt=0.0), "dt"), (dict(sigma=-1.0), "sigma"), (dict(lam=float("nan")), "lambda"),
+    (dict(variant=4), "variant"), (dict(variant=-1), "variant"),
 ])
 def test_create_rejects_bad_config(kw, msg):
     with pytest.raises(mppi.MPPIError) as e:

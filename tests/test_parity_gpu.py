@@ -78,7 +78,7 @@ def test_noise_matches_oracle():
 # ---------------------------------------------------------------------------
 # per-sample costs (Eq. 3) and the plan (Eq. 4)
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("seed", range(5))
 @pytest.mark.parametrize("contact", [False, True])
 def test_costs_match_oracle(seed, contact, variant):
@@ -87,7 +87,7 @@ def test_costs_match_oracle(seed, contact, variant):
     assert_costs(g["S"], o["S"])
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("seed", range(6))
 def test_plan_matches_oracle(seed, variant):
     c = make_case(seed, cost=parity_cost())
@@ -187,7 +187,7 @@ def test_step_with_no_finite_cost_keeps_plan():
 # ---------------------------------------------------------------------------
 # sizes: ragged tails of the 128-thread rollout blocks, K = 1, T = 1
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("K,T", [(1, 18), (2, 3), (31, 1), (33, 2), (129, 7), (1000, 5),
                                  (128, 18), (64, 256)])
 def test_sizes(K, T, variant):
@@ -215,18 +215,20 @@ def test_fp64_reduction_matches():
 # execution modes are bitwise identical; resume from a checkpoint
 
 def test_rollout_variants_agree():
-    """The register-unrolled and the shared-memory-rolled rollout kernels do
-    the same arithmetic in the same order."""
+    """The register-unrolled, the shared-memory-rolled and the
+    warp-specialised rollout kernels do the same arithmetic in the same
+    order."""
     c = make_case(3, contact=True, K=1500, T=11)
     res = []
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         with gpu_controller(c, variant=variant) as g:
             g.step(c["q"], c["qd"], c["goal"], c["plane"])
             res.append((g.costs(), g.noise()))
-    assert np.array_equal(res[0][1], res[1][1])
-    # the two kernels are compiled separately, so FMA contraction may differ;
-    # contact costs here are ~1e5, so allow a few FP32 ulps of drift
-    assert np.max(np.abs(res[0][0] - res[1][0]) / np.abs(res[0][0])) <= 2e-5
+    for other in res[1:]:
+        assert np.array_equal(res[0][1], other[1])
+        # the kernels are compiled separately, so FMA contraction may differ;
+        # contact costs here are ~1e5, so allow a few FP32 ulps of drift
+        assert np.max(np.abs(res[0][0] - other[0]) / np.abs(res[0][0])) <= 2e-5
 
 
 def test_graph_eager_device_paths_identical():
@@ -324,7 +326,7 @@ def test_paper_table1_workload():
         assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_full_size_workload_sampled(variant):
     """K=16384, T=18 with contact (the benchmark's workload): sampled costs
     and noise against single oracle rollouts; the update against the FP64
@@ -359,7 +361,7 @@ def test_rollout_device_matches_step_costs():
         assert np.array_equal(d_n.cpu().numpy(), g.noise())
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_second_proposal_matches_oracle(variant):
     """Learned-proposal form: samples k < n_plain around the warm start, the
     rest around a second plan; the update is the weighted mean of the

@@ -1,0 +1,128 @@
+"""The named-barrier protocol of the warp-specialised rollout kernel
+(rollout_kernel_ws, variant 3), checked on the CPU as a model.
+
+Each warp's barrier operations are listed in program order, as the kernel
+issues them for states s = 0..T.  Warp 0 arrives at one barrier per link
+once the link's frame and motion are written (at s = T only at the last
+link's), then, for s < T, waits for the link forces, the rows of M and the
+step's inputs.  Warp 1 waits for the even links (the last one included),
+then for the forces, arrives with its rows of M and with its copy of x_s;
+at s = T it waits for the last link only.  Warp 2 waits for the odd links
+and for the last link (it forms the end-effector state for the dynamics),
+then for the forces, and arrives with its rows of M and with the step's
+input.  The model runs the three programs under named-barrier semantics (a
+phase completes when `count` threads have arrived or waited) in random
+interleavings and checks that every run ends with all barriers complete,
+that no phase mixes operations of two different states, and that no wait is
+left pending: no interleaving can hang the kernel, and no hand-off slot is
+reused before its readers have passed.
+"""
+import random
+
+import pytest
+
+NJ = 7
+BAR_LINK0, BAR_FORCES, BAR_MROWS, BAR_STEP = 1, 8, 9, 10
+B = 32
+
+
+def link_count(i, last):
+    return 2 * B if last else (3 * B if i == NJ - 1 else 2 * B)
+
+
+def warp0(T):
+    for s in range(T + 1):
+        last = s == T
+        for i in range(NJ):
+            if not last or i == NJ - 1:
+                yield ("arrive", BAR_LINK0 + i, link_count(i, last), s)
+        if last:
+            return
+        yield ("sync", BAR_FORCES, 3 * B, s)
+        yield ("sync", BAR_MROWS, 3 * B, s)
+        yield ("sync", BAR_STEP, 3 * B, s)
+
+
+def warp1(T):
+    for s in range(T + 1):
+        if s < T:
+            for i in range(0, NJ, 2):
+                yield ("sync", BAR_LINK0 + i, link_count(i, False), s)
+            yield ("sync", BAR_FORCES, 3 * B, s)
+            yield ("arrive", BAR_MROWS, 3 * B, s)
+            yield ("arrive", BAR_STEP, 3 * B, s)
+        else:
+            yield ("sync", BAR_LINK0 + NJ - 1, link_count(NJ - 1, True), s)
+
+
+def warp2(T):
+    for s in range(T):
+        for i in range(1, NJ, 2):
+            yield ("sync", BAR_LINK0 + i, link_count(i, False), s)
+        yield ("sync", BAR_LINK0 + NJ - 1, link_count(NJ - 1, False), s)
+        yield ("sync", BAR_FORCES, 3 * B, s)
+        yield ("arrive", BAR_MROWS, 3 * B, s)
+        yield ("arrive", BAR_STEP, 3 * B, s)
+
+
+def run(T, seed):
+    rng = random.Random(seed)
+    progs = [warp0(T), warp1(T), warp2(T)]
+    pend = [next(p, None) for p in progs]
+    waiting = [False] * 3
+    bars = {}
+    while any(p is not None for p in pend):
+        runnable = [w for w in range(3) if pend[w] is not None and not waiting[w]]
+        if not runnable:
+            return "deadlock"
+        w = rng.choice(runnable)
+        op, bid, count, s = pend[w]
+        n, expect, waiters, tag = bars.get(bid, (0, count, set(), s))
+        if expect != count:
+            return f"count mismatch on barrier {bid}"
+        if tag != s:
+            return f"barrier {bid} mixes states {tag} and {s}"
+        n += B
+        if op == "sync":
+            waiters = waiters | {w}
+            waiting[w] = True
+        if n == expect:
+            for x in waiters:
+                waiting[x] = False
+                pend[x] = next(progs[x], None)
+            if op == "arrive":
+                pend[w] = next(progs[w], None)
+            del bars[bid]
+        else:
+            bars[bid] = (n, expect, waiters, tag)
+            if op == "arrive":
+                pend[w] = next(progs[w], None)
+    return "ok" if not bars else f"incomplete barriers {sorted(bars)}"
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 18, 64])
+def test_protocol_completes_in_every_interleaving_tried(T):
+    for seed in range(200):
+        assert run(T, seed) == "ok", (T, seed)
+
+
+def test_model_detects_a_broken_protocol():
+    # the checker itself: a consumer that skips one link wait must be caught
+    global warp2
+    good = warp2
+
+    def bad(T):
+        for s in range(T):
+            for i in range(3, NJ, 2):
+                yield ("sync", BAR_LINK0 + i, link_count(i, False), s)
+            yield ("sync", BAR_LINK0 + NJ - 1, link_count(NJ - 1, False), s)
+            yield ("sync", BAR_FORCES, 3 * B, s)
+            yield ("arrive", BAR_MROWS, 3 * B, s)
+            yield ("arrive", BAR_STEP, 3 * B, s)
+
+    warp2 = bad
+    try:
+        results = {run(3, seed) for seed in range(50)}
+    finally:
+        warp2 = good
+    assert results != {"ok"}
