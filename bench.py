@@ -45,7 +45,9 @@ L2_FLUSH_BYTES = 256 << 20  # twice the 126 MB L2
 # rollout kernel, counted by ncu
 # (smsp__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on) and divided
 # by K*T, on rollout_kernel_rolled at K=16384, T=18 (bench.py's own
-# workloads, two launches each).
+# workloads, two launches each).  The same count serves every kernel of a
+# workload: it is the method's arithmetic (the warp-specialised kernel
+# repeats 0.3 % of it, 4824.6).
 FLOP_PER_ROLLOUT_STEP = {"contact": 4808.1, "force_estimate": 6004.6, "collision": 6692.8}
 # DRAM read + write bytes of one rollout launch at K=16384, T=18 per (cost,
 # kernel) (ncu dram__bytes_{read,write}.sum, mean of two launches).  The
@@ -53,6 +55,7 @@ FLOP_PER_ROLLOUT_STEP = {"contact": 4808.1, "force_estimate": 6004.6, "collision
 # back inside the launch.
 ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel"): 115456,
                                     ("contact", "rollout_kernel_rolled"): 55680,
+                                    ("contact", "rollout_kernel_ws"): 57216,
                                     ("force_estimate", "rollout_kernel_rolled"): 66432,
                                     ("collision", "rollout_kernel_rolled"): 70400}
 COSTS = ("contact", "force_estimate", "collision")
@@ -301,9 +304,8 @@ def run_ours(args, rank, world):
         ctl.set_obstacles(obstacles(rank, arm, pose[:3]))
     # the optional cost terms run in the rolled kernel; otherwise variant 0
     # picks it for K <= 32768
-    rolled = args.variant == 2 or (args.variant == 0 and (args.cost != "contact" or K <= 32768))
-    kname = ("rollout_kernel_ws" if args.variant == 3 else
-             "rollout_kernel_rolled" if rolled else "rollout_kernel")
+    kname = {1: "rollout_kernel", 2: "rollout_kernel_rolled",
+             3: "rollout_kernel_ws"}[ctl.variant()]
     plane = synth.plane_through(float(pose[2]))
     d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, plane), device="cuda")
     d_tau = torch.zeros(7, device="cuda")

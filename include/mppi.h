@@ -281,6 +281,12 @@ MPPI_API int mppi_set_obstacles_device(mppi_t h, int n, const float* d_obs);
 MPPI_API int mppi_force_estimate_device(mppi_t h, const float* d_q, const float* d_v, int n,
                                         float* d_F);
 
+/* The rollout kernel the handle runs (1, 2 or 3 as in mppi_config.variant;
+ * variant 0 resolves at creation: the warp-specialised kernel while its
+ * blocks for K samples fit on the device at once, else the register kernel;
+ * the rolled kernel when the wrench-estimate or collision cost is on). */
+MPPI_API int mppi_get_variant(mppi_t h, int* variant);
+
 /* End-effector pose (p xyz, quaternion wxyz) at joint angles q, computed on
  * the device by the rollouts' own kinematics (host arrays). */
 MPPI_API int mppi_ee_pose(mppi_t h, const float q[7], float pose_out[7]);

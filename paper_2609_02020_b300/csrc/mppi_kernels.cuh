@@ -621,15 +621,21 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
 
 constexpr int WS_B = 32;              // samples per block
 constexpr int WS_THREADS = 3 * WS_B;  // three warps
-constexpr int CHAIN_FIELDS = 24;      // R 9, p 3, Vw 3, Vv 3, Aw 3, Av 3
+// One record of 52 floats per (link, sample): 16-byte aligned, and a stride
+// of 52 words puts the eight lanes of each 128-bit access phase on distinct
+// banks.  float4 0-5, the link state: (z0 z1 z2 w0)(w1 w2 . .)(F0..F3)
+// (F4 F5 I0 I1)(I2..I5)(I6..I9), warp 0 writing the first two, the force
+// warps the last four; float4 6-11, the hand-off of the link's frame and
+// motion: (R0..R3)(R4..R7)(R8 p0 p1 p2)(Vw Vv0)(Vv1 Vv2 Aw0 Aw1)(Aw2 Av).
+constexpr int WS_REC = 52;
+constexpr int WS_HANDOFF = 6;  // float4 offset of the hand-off part
 constexpr int EE_FIELDS = 4;          // end-effector point 3, contact force
 constexpr int V_SLOTS = 3;            // ring of inputs v_s, slot s % 3
 // named barriers (0 is __syncthreads): one per link, link forces complete,
 // rows of M complete, inputs of the step complete
 constexpr int BAR_LINK0 = 1, BAR_FORCES = 8, BAR_MROWS = 9, BAR_STEP = 10;
-constexpr int WS_FLOATS_PER_SAMPLE = NJ * LINK_FIELDS + NJ * CHAIN_FIELDS + NJ * (NJ + 1) / 2 +
-                                     NJ /* h */ + 2 * NJ /* q, qd */ +
-                                     V_SLOTS * NJ /* v ring */ + EE_FIELDS;
+constexpr int WS_FLOATS_PER_SAMPLE = NJ * WS_REC + NJ * (NJ + 1) / 2 + NJ /* h */ +
+                                     2 * NJ /* q, qd */ + V_SLOTS * NJ /* v ring */ + EE_FIELDS;
 
 __device__ __forceinline__ void bar_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -645,10 +651,11 @@ __host__ __device__ constexpr int ws_link_count(int i, bool last_state) {
   return last_state ? 2 * WS_B : (i == NJ - 1 ? 3 * WS_B : 2 * WS_B);
 }
 
-// Dynamic shared memory of rollout_kernel_ws for horizon T.
-__host__ __device__ constexpr size_t ws_smem_bytes(int T) {
-  return sizeof(float) * (2 * static_cast<size_t>((T * NJ + 3) / 4 * 4) + 32 +
-                          static_cast<size_t>(WS_FLOATS_PER_SAMPLE) * WS_B);
+// Dynamic shared memory of rollout_kernel_ws (independent of T: the plans
+// are read from global memory, where they stay in L1).  56.2 KB: four
+// blocks fit on an SM.
+__host__ __device__ constexpr size_t ws_smem_bytes() {
+  return sizeof(float) * (32 + static_cast<size_t>(WS_FLOATS_PER_SAMPLE) * WS_B);
 }
 
 struct WsSmem {
@@ -658,9 +665,9 @@ struct WsSmem {
 __device__ __forceinline__ WsSmem ws_carve(float* base) {
   constexpr int B = WS_B;
   WsSmem m;
-  m.sl = base;                              // [7][22][B]: z, w (warp 0); F, In (warps 1, 2)
-  m.sc = m.sl + NJ * LINK_FIELDS * B;       // [7][24][B]: link frame and motion hand-off
-  m.sM = m.sc + NJ * CHAIN_FIELDS * B;      // [28][B]
+  m.sl = base;                              // [7][B] records (link state part)
+  m.sc = base + 4 * WS_HANDOFF;             // the same records' hand-off part
+  m.sM = m.sl + NJ * B * WS_REC;            // [28][B]
   m.sh = m.sM + (NJ * (NJ + 1) / 2) * B;    // [7][B]
   m.sq = m.sh + NJ * B;                     // [7][B]
   m.sqd = m.sq + NJ * B;                    // [7][B]
@@ -669,55 +676,140 @@ __device__ __forceinline__ WsSmem ws_carve(float* base) {
   return m;
 }
 
-// Rows [i] of M and, with H_OUT, h: the backward sweep of backward_link
-// down to the lowest listed row.  rows: bit i set for row i.
-template <bool H_OUT>
-__device__ __forceinline__ void ws_backward(const RobotK& rb, const WsSmem& m, unsigned rows,
-                                            int tid) {
+__device__ __forceinline__ float4* ws_rec(float* base, int i, int tid) {
+  return reinterpret_cast<float4*>(base + (i * WS_B + tid) * WS_REC);
+}
+__device__ __forceinline__ const float4* ws_rec(const float* base, int i, int tid) {
+  return reinterpret_cast<const float4*>(base + (i * WS_B + tid) * WS_REC);
+}
+
+__device__ __forceinline__ void ws_store_axis(float* sl, int i, int tid, const float z[3],
+                                              const float w[3]) {
+  float4* r = ws_rec(sl, i, tid);
+  r[0] = make_float4(z[0], z[1], z[2], w[0]);
+  r[1] = make_float4(w[1], w[2], 0.f, 0.f);
+}
+__device__ __forceinline__ void ws_load_axis(const float* sl, int i, int tid, float z[3],
+                                             float w[3]) {
+  const float4* r = ws_rec(sl, i, tid);
+  const float4 a = r[0], b = r[1];
+  z[0] = a.x; z[1] = a.y; z[2] = a.z;
+  w[0] = a.w; w[1] = b.x; w[2] = b.y;
+}
+__device__ __forceinline__ void ws_store_force(float* sl, int i, int tid, const float F[6],
+                                               const float In[10]) {
+  float4* r = ws_rec(sl, i, tid);
+  r[2] = make_float4(F[0], F[1], F[2], F[3]);
+  r[3] = make_float4(F[4], F[5], In[0], In[1]);
+  r[4] = make_float4(In[2], In[3], In[4], In[5]);
+  r[5] = make_float4(In[6], In[7], In[8], In[9]);
+}
+__device__ __forceinline__ void ws_load_force(const float* sl, int i, int tid, float F[6],
+                                              float In[10]) {
+  const float4* r = ws_rec(sl, i, tid);
+  const float4 a = r[2], b = r[3], c = r[4], d = r[5];
+  F[0] = a.x; F[1] = a.y; F[2] = a.z; F[3] = a.w; F[4] = b.x; F[5] = b.y;
+  In[0] = b.z; In[1] = b.w;
+  In[2] = c.x; In[3] = c.y; In[4] = c.z; In[5] = c.w;
+  In[6] = d.x; In[7] = d.y; In[8] = d.z; In[9] = d.w;
+}
+__device__ __forceinline__ void ws_load_inertia(const float* sl, int i, int tid, float In[10]) {
+  const float4* r = ws_rec(sl, i, tid);
+  const float4 b = r[3], c = r[4], d = r[5];
+  In[0] = b.z; In[1] = b.w;
+  In[2] = c.x; In[3] = c.y; In[4] = c.z; In[5] = c.w;
+  In[6] = d.x; In[7] = d.y; In[8] = d.z; In[9] = d.w;
+}
+__device__ __forceinline__ void ws_store_chain(float* sc, int i, int tid, const ChainState& c) {
+  float4* r = ws_rec(sc, i, tid);
+  r[0] = make_float4(c.R[0], c.R[1], c.R[2], c.R[3]);
+  r[1] = make_float4(c.R[4], c.R[5], c.R[6], c.R[7]);
+  r[2] = make_float4(c.R[8], c.p[0], c.p[1], c.p[2]);
+  r[3] = make_float4(c.Vw[0], c.Vw[1], c.Vw[2], c.Vv[0]);
+  r[4] = make_float4(c.Vv[1], c.Vv[2], c.Aw[0], c.Aw[1]);
+  r[5] = make_float4(c.Aw[2], c.Av[0], c.Av[1], c.Av[2]);
+}
+__device__ __forceinline__ void ws_load_chain(const float* sc, int i, int tid, ChainState& c) {
+  const float4* r = ws_rec(sc, i, tid);
+  const float4 a = r[0], b = r[1], d = r[2], e = r[3], f = r[4], g = r[5];
+  c.R[0] = a.x; c.R[1] = a.y; c.R[2] = a.z; c.R[3] = a.w;
+  c.R[4] = b.x; c.R[5] = b.y; c.R[6] = b.z; c.R[7] = b.w;
+  c.R[8] = d.x; c.p[0] = d.y; c.p[1] = d.z; c.p[2] = d.w;
+  c.Vw[0] = e.x; c.Vw[1] = e.y; c.Vw[2] = e.z; c.Vv[0] = e.w;
+  c.Vv[1] = f.x; c.Vv[2] = f.y; c.Aw[0] = f.z; c.Aw[1] = f.w;
+  c.Aw[2] = g.x; c.Av[0] = g.y; c.Av[1] = g.z; c.Av[2] = g.w;
+}
+
+// Row i of M from the composite momentum (H, Lm) of S_i:
+// M_ij = S_j . (H, Lm) for j < i, M_ii = S_i . (H, Lm) + armature.
+__device__ __forceinline__ void ws_row(const RobotK& rb, const WsSmem& m, int i, const float z[3],
+                                       const float w[3], const float H[3], const float Lm[3],
+                                       int tid) {
+  constexpr int B = WS_B;
+  const int row = i * (i + 1) / 2;
+#pragma unroll 1
+  for (int j = 0; j < i; ++j) {
+    float zj[3], wj[3];
+    ws_load_axis(m.sl, j, tid, zj, wj);
+    m.sM[(row + j) * B + tid] = dot3(zj, H) + dot3(wj, Lm);
+  }
+  m.sM[(row + i) * B + tid] = dot3(z, H) + dot3(w, Lm) + rb.L[i].arm;
+}
+
+// warp 0's share of the backward sweep: h over all links (backward_link's
+// suffix force sum and projection) and row NJ - 1 of M, whose composite
+// inertia is the last link's own.
+__device__ __forceinline__ void ws_backward_h(const RobotK& rb, const WsSmem& m, int tid) {
   constexpr int B = WS_B;
   float Fs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  float Ic[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int lowest = H_OUT ? 0 : __ffs(rows) - 1;
 #pragma unroll 1
-  for (int i = NJ - 1; i >= lowest; --i) {
-    LinkState S;
-    load_link<B>(m.sl, i, tid, S);
-    float H[3], Lm[3];
-    const float hi = backward_link(rb.L[i], m.sqd[i * B + tid], S, Fs, Ic, H, Lm);
-    if (H_OUT) m.sh[i * B + tid] = hi;
-    if (rows & (1u << i)) {
-      const int row = i * (i + 1) / 2;
-#pragma unroll 1
-      for (int j = 0; j < i; ++j) {
-        float zj[3], wj[3];
-        load_axis<B>(m.sl, j, tid, zj, wj);
-        m.sM[(row + j) * B + tid] = dot3(zj, H) + dot3(wj, Lm);
-      }
-      m.sM[(row + i) * B + tid] = dot3(S.z, H) + dot3(S.w, Lm) + rb.L[i].arm;
+  for (int i = NJ - 1; i >= 0; --i) {
+    float z[3], w[3];
+    ws_load_axis(m.sl, i, tid, z, w);
+    {
+      const float4* r = ws_rec(m.sl, i, tid);
+      const float4 a = r[2], b = r[3];
+      Fs[0] += a.x; Fs[1] += a.y; Fs[2] += a.z; Fs[3] += a.w; Fs[4] += b.x; Fs[5] += b.y;
+    }
+    m.sh[i * B + tid] = fmaf(rb.L[i].damp, m.sqd[i * B + tid],
+                             dot3(z, Fs) + fmaf(w[0], Fs[3], fmaf(w[1], Fs[4], w[2] * Fs[5])));
+    if (i == NJ - 1) {
+      float In[10], Ic[10], H[3], Lm[3];
+      ws_load_inertia(m.sl, i, tid, In);
+#pragma unroll
+      for (int a = 0; a < 10; ++a) Ic[a] = 0.f + In[a];
+      inertia_apply(Ic, z, w, H, Lm);
+      ws_row(rb, m, i, z, w, H, Lm, tid);
     }
   }
 }
 
-// Rows of M per warp (each costs about 30 + 6 i, plus the composite inertias
-// down to the lowest row); warp 0 also forms h.
-constexpr unsigned WS_ROWS0 = 1u << 6;
-constexpr unsigned WS_ROWS1 = (1u << 5) | (1u << 2) | (1u << 1);
-constexpr unsigned WS_ROWS2 = (1u << 4) | (1u << 3) | (1u << 0);
-
-__device__ __forceinline__ void ws_load_chain(const WsSmem& m, int i, int tid, ChainState& c) {
-  constexpr int B = WS_B;
-  const float* h = m.sc + i * CHAIN_FIELDS * B + tid;
+// the force warps' share: the composite inertias Ic_i = sum_{j >= i} In_j
+// (added in backward_link's order) down to the lowest listed row, and the
+// listed rows of M.
+__device__ __forceinline__ void ws_backward_rows(const RobotK& rb, const WsSmem& m, unsigned rows,
+                                                 int tid) {
+  float Ic[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int lowest = __ffs(rows) - 1;
+#pragma unroll 1
+  for (int i = NJ - 1; i >= lowest; --i) {
+    float In[10];
+    ws_load_inertia(m.sl, i, tid, In);
 #pragma unroll
-  for (int a = 0; a < 9; ++a) c.R[a] = h[a * B];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    c.p[a] = h[(9 + a) * B];
-    c.Vw[a] = h[(12 + a) * B];
-    c.Vv[a] = h[(15 + a) * B];
-    c.Aw[a] = h[(18 + a) * B];
-    c.Av[a] = h[(21 + a) * B];
+    for (int a = 0; a < 10; ++a) Ic[a] += In[a];
+    if (rows & (1u << i)) {
+      float z[3], w[3], H[3], Lm[3];
+      ws_load_axis(m.sl, i, tid, z, w);
+      inertia_apply(Ic, z, w, H, Lm);
+      ws_row(rb, m, i, z, w, H, Lm, tid);
+    }
   }
 }
+
+// Rows of M of the force warps (each costs about 30 + 6 i, plus the
+// composite inertias down to the lowest row); warp 0 forms h and row 6.
+constexpr unsigned WS_ROWS1 = (1u << 5) | (1u << 2) | (1u << 1);
+constexpr unsigned WS_ROWS2 = (1u << 4) | (1u << 3) | (1u << 0);
 
 // warp 0
 __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, const WsSmem& m,
@@ -744,25 +836,13 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
     for (int i = 0; i < NJ; ++i) {
       float z[3], w[3];
       forward_link_chain(P.rb.L[i], m.sq[i * B + tid], m.sqd[i * B + tid], c, z, w);
-      float* l = m.sl + i * LINK_FIELDS * B + tid;
-      float* h = m.sc + i * CHAIN_FIELDS * B + tid;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        l[a * B] = z[a];
-        l[(3 + a) * B] = w[a];
-        h[(9 + a) * B] = c.p[a];
-        h[(12 + a) * B] = c.Vw[a];
-        h[(15 + a) * B] = c.Vv[a];
-        h[(18 + a) * B] = c.Aw[a];
-        h[(21 + a) * B] = c.Av[a];
-      }
-#pragma unroll
-      for (int a = 0; a < 9; ++a) h[a * B] = c.R[a];
+      ws_store_axis(m.sl, i, tid, z, w);
+      ws_store_chain(m.sc, i, tid, c);
       if (!last || i == NJ - 1) bar_arrive(BAR_LINK0 + i, ws_link_count(i, last));
     }
     if (last) break;
     bar_sync(BAR_FORCES, 3 * B);
-    ws_backward<true>(P.rb, m, WS_ROWS0, tid);
+    ws_backward_h(P.rb, m, tid);
     bar_sync(BAR_MROWS, 3 * B);
     float M[NJ * (NJ + 1) / 2], invD[NJ];
 #pragma unroll
@@ -780,7 +860,7 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
         float zj[3], wj[3];
-        load_axis<B>(m.sl, j, tid, zj, wj);
+        ws_load_axis(m.sl, j, tid, zj, wj);
         rhs[j] = v[j * B] + dot3(zj, pxF) + dot3(wj, Fc) - m.sh[j * B + tid];
       }
     } else {
@@ -803,19 +883,14 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
 
 // warps 1 and 2, link phase: inertias and forces of links first, first + 2, ...
 __device__ __forceinline__ void ws_forces(const ProbK& P, const WsSmem& m, int first, int tid) {
-  constexpr int B = WS_B;
 #pragma unroll 1
   for (int i = first; i < NJ; i += 2) {
     bar_sync(BAR_LINK0 + i, ws_link_count(i, false));
     ChainState c;
-    ws_load_chain(m, i, tid, c);
+    ws_load_chain(m.sc, i, tid, c);
     float In[10], F[6];
     forward_link_force(P.rb.L[i], c.R, c.p, c.Vw, c.Vv, c.Aw, c.Av, In, F);
-    float* l = m.sl + i * LINK_FIELDS * B + tid;
-#pragma unroll
-    for (int a = 0; a < 6; ++a) l[(6 + a) * B] = F[a];
-#pragma unroll
-    for (int a = 0; a < 10; ++a) l[(12 + a) * B] = In[a];
+    ws_store_force(m.sl, i, tid, F, In);
   }
 }
 
@@ -838,13 +913,13 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
     ChainState c;
     if (s < T) {
       ws_forces(P, m, 0, tid);  // ends with the last link (even)
-      ws_load_chain(m, NJ - 1, tid, c);
+      ws_load_chain(m.sc, NJ - 1, tid, c);
       bar_sync(BAR_FORCES, 3 * B);
-      ws_backward<false>(P.rb, m, WS_ROWS1, tid);
+      ws_backward_rows(P.rb, m, WS_ROWS1, tid);
       bar_arrive(BAR_MROWS, 3 * B);
     } else {
       bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, true));
-      ws_load_chain(m, NJ - 1, tid, c);
+      ws_load_chain(m.sc, NJ - 1, tid, c);
     }
     // x_s and v_{s-1}, copied before warp 0 may overwrite them
     float q[NJ], qd[NJ], v[NJ];
@@ -896,7 +971,7 @@ __device__ __forceinline__ void ws_draw(const ProbK& P, const float* plan, uint6
   for (int j = 0; j < NJ; ++j) {
     const float du = P.sigma[j] * z[j];
     if (STORE_NOISE && live) noise[static_cast<size_t>(s * NJ + j) * K + k] = du;
-    v[j * B] = plan[s * NJ + j] + du;
+    v[j * B] = __ldg(plan + s * NJ + j) + du;
   }
 }
 
@@ -916,7 +991,7 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
     {
       bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, false));
       ChainState c;
-      ws_load_chain(m, NJ - 1, tid, c);
+      ws_load_chain(m.sc, NJ - 1, tid, c);
       EEState ee;
       chain_ee(P.rb, c, ee);
 #pragma unroll
@@ -924,7 +999,7 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
       m.se[3 * B + tid] = contact ? contact_force(C, plane, ee) : 0.f;
     }
     bar_sync(BAR_FORCES, 3 * B);
-    ws_backward<false>(P.rb, m, WS_ROWS2, tid);
+    ws_backward_rows(P.rb, m, WS_ROWS2, tid);
     bar_arrive(BAR_MROWS, 3 * B);
     if (s == 0) ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, 0, tid);
     bar_arrive(BAR_STEP, 3 * B);
@@ -939,16 +1014,11 @@ rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
                   float* __restrict__ S, float* __restrict__ noise,
                   const float* __restrict__ prop = nullptr,
                   const int* __restrict__ ksplit_p = nullptr) {
-  extern __shared__ float dsm[];
-  const int T = P.T, K = P.K;
+  extern __shared__ float4 dsm4[];
+  float* dsm = reinterpret_cast<float*>(dsm4);
+  const int K = P.K;
   const int k_split = ksplit_p ? *ksplit_p : K;
-  const int pstride = (T * NJ + 3) / 4 * 4;
-  float* s_plan = dsm;
-  float* s_prop = dsm + pstride;
-  float* s_in = s_prop + pstride;
-  for (int i = threadIdx.x; i < T * NJ; i += WS_THREADS) s_plan[i] = plan[i];
-  if (k_split < K)
-    for (int i = threadIdx.x; i < T * NJ; i += WS_THREADS) s_prop[i] = prop[i];
+  float* s_in = dsm;
   if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
   __syncthreads();
   const WsSmem m = ws_carve(s_in + 32);
@@ -964,8 +1034,7 @@ rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
     const float Sk = ws_costs(P, s_in, m, lane);
     if (live) S[k] = Sk;
   } else {
-    ws_noise<STORE_NOISE>(P, s_in, k < k_split ? s_plan : s_prop, *iter_p, k, live, noise, m,
-                          lane);
+    ws_noise<STORE_NOISE>(P, s_in, k < k_split ? plan : prop, *iter_p, k, live, noise, m, lane);
   }
 }
 

@@ -16,14 +16,30 @@ using namespace mppi_dev;
 
 #define MPPI_VERSION_STR "paper_2609_02020_b300 mppi 1.0 (sm_103a)"
 
-// Rollout kernel used when mppi_config.variant is 0: the rolled kernel
-// (short code, shared-memory link state) wins while there are too few
-// samples to give each SM scheduler more than a couple of warps; above that
-// the register-unrolled kernel's lower instruction count wins.  Measured on
-// B300 at T = 18: rolled 99 us vs 125 us at K = 16384, 260 us vs 210 us at
-// K = 65536.
-constexpr int kRolledMaxK = 32768;
-static int default_variant(int K) { return K <= kRolledMaxK ? 2 : 1; }
+// Rollout kernel used when mppi_config.variant is 0.  While there are too
+// few samples to give each SM scheduler more than a couple of warps, one
+// sample's dependency chain sets the time, and the warp-specialised kernel
+// (three warps per 32 samples) shortens it most - as long as all of its
+// blocks are resident at once (one wave; four 56 KB blocks per SM).  Beyond
+// that, throughput bounds and the register-unrolled kernel's lower
+// instruction count wins.  Measured on B300 at T = 18 (rollout only, us):
+//   K        512    4096   16384   24576   32768   65536
+//   ws        67      75      93     174     184     344
+//   rolled   114     104     103     139     139     268
+//   register 114     128     127     125     122     214
+// The rolled kernel carries the optional cost terms.
+static int default_variant(int K) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel_ws<true>, WS_THREADS,
+                                                    ws_smem_bytes()) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  const long long ws_blocks = (static_cast<long long>(K) + WS_B - 1) / WS_B;
+  return ws_blocks <= static_cast<long long>(sms) * per_sm ? 3 : 1;
+}
 
 static_assert(MPPI_OBS_MAX == OBS_MAX, "obstacle capacity of the ABI and the kernels");
 
@@ -342,7 +358,7 @@ cudaError_t prepare_rollout(mppi_s* h) {
   }
   if (h->variant == 2) return prepare_rolled<0>(h->P.T);
   if (h->variant == 3) {
-    const size_t smem = ws_smem_bytes(h->P.T);
+    const size_t smem = ws_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(rollout_kernel_ws<true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
@@ -366,7 +382,7 @@ cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float*
   if (h->variant == 2) return launch_rolled<0>(h, grid, in, plan, S, noise);
   if (h->variant == 3) {
     const int wgrid = (h->P.K + WS_B - 1) / WS_B;
-    const size_t smem = ws_smem_bytes(h->P.T);
+    const size_t smem = ws_smem_bytes();
     if (noise)
       rollout_kernel_ws<true><<<wgrid, WS_THREADS, smem, h->stream>>>(
           h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl);
@@ -518,7 +534,14 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
                 "the wrench-estimate and collision costs need the rolled rollout kernel "
                 "(variant 0 or 2)");
   }
-  h->variant = h->feat ? 2 : cfg->variant == 0 ? default_variant(cfg->K) : cfg->variant;
+  if (!h->feat && cfg->variant == 0) {
+    // the occupancy query needs the ws kernel's shared-memory opt-in first
+    h->variant = 3;
+    if (prepare_rollout(h) != cudaSuccess) cudaGetLastError();
+    h->variant = default_variant(cfg->K);
+  } else {
+    h->variant = h->feat ? 2 : cfg->variant;
+  }
   const int T = cfg->T, K = cfg->K;
   auto bail = [&](cudaError_t e, const char* what) {
     std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
@@ -876,6 +899,12 @@ int mppi_set_obstacles_device(mppi_t h, int n, const float* d_obs) {
                                 cudaMemcpyDeviceToDevice, h->stream));
   set_int_kernel<<<1, 32, 0, h->stream>>>(&h->d_obs->n, n);
   CUDA_TRY(h, cudaGetLastError());
+  return MPPI_OK;
+}
+
+int mppi_get_variant(mppi_t h, int* variant) {
+  if (!h || !variant) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  *variant = h->variant;
   return MPPI_OK;
 }
 

@@ -134,6 +134,7 @@ EXPORTS = [
     "mppi_simulate_device", "mppi_set_plan_device", "mppi_get_plan_device",
     "mppi_get_updated_plan_device", "mppi_set_proposal_device", "mppi_gravity_torque",
     "mppi_force_estimate_device", "mppi_set_obstacles", "mppi_set_obstacles_device",
+    "mppi_get_variant",
     # include/mppi_serve.h
     "mppi_pool_create", "mppi_pool_destroy", "mppi_pool_alloc", "mppi_pool_free",
     "mppi_pool_stats", "mppi_server_create", "mppi_server_destroy", "mppi_server_add_problem",
@@ -194,6 +195,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_gravity_torque": ([H, fp, fp], C.c_int),
         "mppi_force_estimate_device": ([H, vp, vp, C.c_int, vp], C.c_int),
         "mppi_set_obstacles": ([H, C.c_int, fp], C.c_int),
+        "mppi_get_variant": ([H, C.POINTER(C.c_int)], C.c_int),
         "mppi_set_obstacles_device": ([H, C.c_int, vp], C.c_int),
         "mppi_pool_create": ([C.c_size_t, C.POINTER(C.c_void_p)], C.c_int),
         "mppi_pool_destroy": ([H], C.c_int),
@@ -441,6 +443,12 @@ class MPPI:
         out = np.zeros(7, dtype=np.float32)
         self._check(self.lib.mppi_gravity_torque(self.h, _fp(_f32(q, NJ)), _fp(out)))
         return out
+
+    def variant(self) -> int:
+        """The rollout kernel this handle runs (1 register, 2 rolled, 3 warp-specialised)."""
+        v = C.c_int()
+        self._check(self.lib.mppi_get_variant(self.h, C.byref(v)))
+        return int(v.value)
 
     def set_obstacles(self, obs):
         """Obstacle capsules [n][7] (a xyz, b xyz, radius) for the following updates."""

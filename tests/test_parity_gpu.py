@@ -470,3 +470,16 @@ def test_receding_horizon_contact_loop():
             forces.append(oracle.contact(c["rb"], c["oc"], c["plane"], q, qd)[0])
         assert g.get_iter() == 200
     assert np.all(np.isfinite(q)) and np.all(np.abs(qd) < 50)
+
+
+def test_default_kernel_choice():
+    # variant 0: warp-specialised while its blocks fit on the device at once,
+    # register kernel beyond, rolled kernel for the optional cost terms
+    for K, want in [(256, 3), (16384, 3), (65536, 1)]:
+        with gpu_controller(make_case(0, K=K)) as g:
+            assert g.variant() == want, K
+    with gpu_controller(make_case(0, cost=synth.cost_force_estimate())) as g:
+        assert g.variant() == 2
+    for v in (1, 2, 3):
+        with gpu_controller(make_case(0), variant=v) as g:
+            assert g.variant() == v
