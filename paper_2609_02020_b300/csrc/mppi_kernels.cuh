@@ -1,6 +1,9 @@
 // Kernels of one MPPI update (sm_103a):
-//   rollout_kernel  - Eq. 1-3 with Eq. 5-7 and the running cost of Eq. 9-14,
-//                     one thread per sample;
+//   rollout_kernel, rollout_kernel_rolled, rollout_kernel_ws
+//                   - Eq. 1-3 with Eq. 5-7 and the running cost of Eq. 9-14
+//                     (register-unrolled, one thread per sample; link loops
+//                     rolled through shared memory; three warps per 32
+//                     samples);
 //   update_kernel   - Eq. 4a-4b and the warm-start shift, one block per plan
 //                     entry (t, j), each block reducing over all K samples.
 #pragma once
