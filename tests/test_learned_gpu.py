@@ -35,7 +35,10 @@ def test_learned_proposal_beats_plain_mppi_at_equal_samples():
                      ("learned512", lambda: learned.LearnedMPPI(prob, net, 512, seed=5, stream=s)),
                      ("plain16384", lambda: learned.PlainMPPI(prob, 16384, seed=5, stream=s))]:
         c = mk()
-        res[name] = learned.evaluate(prob, c, episodes=6, steps=120, seed=1, stream=s)
+        # 12 held-out episodes: closed-loop MPPI is sensitive to rounding, and
+        # over 6 episodes the ratio below ranged 0.65-0.88 between builds
+        # that differ only in summation order; over 12 it stays near 0.7
+        res[name] = learned.evaluate(prob, c, episodes=12, steps=120, seed=1, stream=s)
         c.close()
     assert res["learned512"]["tracking_cost"] < 0.85 * res["plain512"]["tracking_cost"], res
     assert res["learned512"]["tracking_cost"] < 1.05 * res["plain16384"]["tracking_cost"], res
