@@ -166,7 +166,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_create": ([C.POINTER(Robot), C.POINTER(Cost), C.POINTER(Config), vp,
                          C.POINTER(C.c_void_p)], C.c_int),
         "mppi_destroy": ([H], C.c_int),
-        "mppi_step": ([H, fp, fp, fp, fp, fp, fp], C.c_int),
+        "mppi_step": ([H, vp, vp, vp, vp, vp, vp], C.c_int),
         "mppi_step_device": ([H, vp, vp, vp], C.c_int),
         "mppi_sync": ([H], C.c_int),
         "mppi_get_costs": ([H, fp], C.c_int),
@@ -344,6 +344,15 @@ class MPPI:
         if rc != OK:
             raise MPPIError(rc, self.lib.mppi_last_error(None).decode())
         self.h = h
+        # host staging of mppi_step: inputs packed into one float32 record and
+        # the outputs, with their addresses cached so that a call marshals
+        # only integers
+        self._in = np.zeros(IN_FLOATS, dtype=np.float32)
+        self._tau = np.zeros(NJ, dtype=np.float32)
+        self._plan = np.zeros((self.T, NJ), dtype=np.float32)
+        a = self._in.ctypes.data
+        self._a_in = (a, a + 4 * NJ, a + 8 * NJ, a + 4 * (3 * NJ))
+        self._a_tau, self._a_plan = self._tau.ctypes.data, self._plan.ctypes.data
 
     # -- lifetime -----------------------------------------------------------
     def close(self):
@@ -369,23 +378,28 @@ class MPPI:
         return rc
 
     # -- updates ------------------------------------------------------------
+    def _stage(self, q, qd, goal, plane):
+        b = self._in
+        b[0:NJ] = q
+        b[NJ:2 * NJ] = qd
+        b[2 * NJ:3 * NJ] = goal
+        if plane is not None:
+            b[3 * NJ:] = plane
+        a = self._a_in
+        return a[0], a[1], a[2], (a[3] if plane is not None else None)
+
     def step(self, q, qd, goal, plane=None, want_plan: bool = True):
         """mppi_step from host arrays -> (tau0 [7], shifted plan [T, 7] or None)."""
-        tau0 = np.zeros(NJ, dtype=np.float32)
-        plan = np.zeros((self.T, NJ), dtype=np.float32) if want_plan else None
-        pl = _f32(plane, 4) if plane is not None else None
-        self._check(self.lib.mppi_step(self.h, _fp(_f32(q, NJ)), _fp(_f32(qd, NJ)),
-                                       _fp(_f32(goal, 7)), _fp(pl) if pl is not None else None,
-                                       _fp(tau0), _fp(plan) if plan is not None else None))
-        return tau0, plan
+        aq, aqd, ag, ap = self._stage(q, qd, goal, plane)
+        self._check(self.lib.mppi_step(self.h, aq, aqd, ag, ap, self._a_tau,
+                                       self._a_plan if want_plan else None))
+        return self._tau.copy(), (self._plan.copy() if want_plan else None)
 
     def step_status(self, q, qd, goal, plane=None):
         """Like step() but returns (rc, tau0) instead of raising on NONFINITE."""
-        tau0 = np.zeros(NJ, dtype=np.float32)
-        pl = _f32(plane, 4) if plane is not None else None
-        rc = self.lib.mppi_step(self.h, _fp(_f32(q, NJ)), _fp(_f32(qd, NJ)), _fp(_f32(goal, 7)),
-                                _fp(pl) if pl is not None else None, _fp(tau0), None)
-        return rc, tau0
+        aq, aqd, ag, ap = self._stage(q, qd, goal, plane)
+        rc = self.lib.mppi_step(self.h, aq, aqd, ag, ap, self._a_tau, None)
+        return rc, self._tau.copy()
 
     def step_device(self, d_in, d_tau0=None, d_plan=None):
         """mppi_step_device on torch CUDA tensors (queued; see sync())."""
