@@ -361,8 +361,11 @@ __device__ __forceinline__ void backward_sweep(const RobotK& rb, const float qd[
 // packed lower-triangle storage (M[i(i+1)/2 + j], j <= i): overwrites the
 // strict lower triangle with L (unit diagonal implied) and returns 1/D.
 // Every loop has a constant trip count (bounds are guards) so that the
-// factorisation unrolls completely and M stays in registers.
-template <int N>
+// factorisation unrolls completely and M stays in registers.  With
+// FAST_RCP the pivots' reciprocals take the hardware approximation
+// (__fdividef, about 2 ulp; the pivots are far from its 2^126 limit), which
+// shortens the dependent chain of the factorisation.
+template <int N, bool FAST_RCP = false>
 __device__ __forceinline__ void ldlt_factor(float M[N * (N + 1) / 2], float invD[N]) {
   float D[N];
 #pragma unroll
@@ -379,7 +382,7 @@ __device__ __forceinline__ void ldlt_factor(float M[N * (N + 1) / 2], float invD
       }
     }
     D[j] = d;
-    invD[j] = 1.0f / d;
+    invD[j] = FAST_RCP ? __fdividef(1.0f, d) : 1.0f / d;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       if (i > j) {

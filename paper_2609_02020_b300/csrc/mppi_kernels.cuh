@@ -636,9 +636,10 @@ constexpr int EE_FIELDS = 4;          // end-effector point 3, contact force
 constexpr int V_SLOTS = 3;            // ring of inputs v_s, slot s % 3
 // named barriers (0 is __syncthreads): one per link, link forces complete,
 // rows of M complete, inputs of the step complete
-constexpr int BAR_LINK0 = 1, BAR_FORCES = 8, BAR_MROWS = 9, BAR_STEP = 10;
+constexpr int BAR_LINK0 = 1, BAR_FORCES = 8, BAR_MROWS = 9, BAR_STEP = 10, BAR_DONE = 11;
 constexpr int WS_FLOATS_PER_SAMPLE = NJ * WS_REC + NJ * (NJ + 1) / 2 + NJ /* h */ +
-                                     2 * NJ /* q, qd */ + V_SLOTS * NJ /* v ring */ + EE_FIELDS;
+                                     2 * NJ /* q, qd */ + V_SLOTS * NJ /* v ring */ + EE_FIELDS +
+                                     2 /* warp 2's partial cost, a double */;
 
 __device__ __forceinline__ void bar_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -663,6 +664,7 @@ __host__ __device__ constexpr size_t ws_smem_bytes() {
 
 struct WsSmem {
   float *sl, *sc, *sM, *sh, *sq, *sqd, *sv, *se;
+  double* s2;
 };
 
 __device__ __forceinline__ WsSmem ws_carve(float* base) {
@@ -676,6 +678,7 @@ __device__ __forceinline__ WsSmem ws_carve(float* base) {
   m.sqd = m.sq + NJ * B;                    // [7][B]
   m.sv = m.sqd + NJ * B;                    // [3][7][B]: v_s in slot s % 3
   m.se = m.sv + V_SLOTS * NJ * B;           // [4][B]: end-effector point, contact force
+  m.s2 = reinterpret_cast<double*>(m.se + EE_FIELDS * B);  // [B] (8-byte aligned)
   return m;
 }
 
@@ -850,7 +853,7 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
     float M[NJ * (NJ + 1) / 2], invD[NJ];
 #pragma unroll
     for (int a = 0; a < NJ * (NJ + 1) / 2; ++a) M[a] = m.sM[a * B + tid];
-    ldlt_factor<NJ>(M, invD);
+    ldlt_factor<NJ, true>(M, invD);
     bar_sync(BAR_STEP, 3 * B);
     const float* v = m.sv + (s % V_SLOTS) * NJ * B + tid;
     const float f = m.se[3 * B + tid];
@@ -935,14 +938,18 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
     }
     if (s < T) bar_arrive(BAR_STEP, 3 * B);
     if (s == 0) continue;
-    // running cost l(x_s, v_{s-1}), Eq. 9-14
+    // running cost l(x_s, v_{s-1}), Eq. 9-14: the joint terms here, the
+    // motion and force terms on warp 2 for s < T and here for s = T
+    float cst = 0.f;
     EEState ee;
-    chain_ee(P.rb, c, ee);
-    float cst = motion_cost(C, pdes, Rd, ee);
-    if (contact) {
-      const float f = contact_force(C, plane, ee);
-      const float ef = C.fdes - f;
-      cst += C.wforce * ef * ef + C.wreg * f * f;
+    if (s == T) {
+      chain_ee(P.rb, c, ee);
+      cst = motion_cost(C, pdes, Rd, ee);
+      if (contact) {
+        const float f = contact_force(C, plane, ee);
+        const float ef = C.fdes - f;
+        cst += C.wforce * ef * ef + C.wreg * f * f;
+      }
     }
     float cj = 0.f;
 #pragma unroll
@@ -957,7 +964,8 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
     if (s == T && C.wterm != 0.f)
       Sacc += static_cast<double>(C.wterm * motion_cost(C, pdes, Rd, ee));
   }
-  return static_cast<float>(Sacc);
+  bar_sync(BAR_DONE, 2 * B);
+  return static_cast<float>(Sacc + m.s2[tid]);
 }
 
 // warp 2: the inputs v_s = u_s + dtau_s (Eq. 2) into slot s % 3
@@ -978,8 +986,9 @@ __device__ __forceinline__ void ws_draw(const ProbK& P, const float* plan, uint6
   }
 }
 
-// warp 2: forces of the odd links, the end-effector point and contact force
-// for the dynamics, and the inputs one step ahead
+// warp 2: forces of the odd links, the end-effector state and contact force
+// (for the dynamics and for the motion and force terms of l(x_s, v_{s-1}),
+// s = 1..T-1), and the inputs one step ahead
 template <bool STORE_NOISE>
 __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const float* plan,
                                          uint64_t iter, int k, bool live,
@@ -988,18 +997,27 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
   const int T = P.T;
   const CostK& C = P.cost;
   const bool contact = C.contact != 0;
+  const float pdes[3] = {in[14], in[15], in[16]};
+  float Rd[9];
+  {
+    const float qt[4] = {in[17], in[18], in[19], in[20]};
+    quat_to_R(qt, Rd);
+  }
   const float plane[4] = {in[21], in[22], in[23], in[24]};
+  double S2 = 0.0;
   for (int s = 0; s < T; ++s) {
     ws_forces(P, m, 1, tid);
+    EEState ee;
+    float f;
     {
       bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, false));
       ChainState c;
       ws_load_chain(m.sc, NJ - 1, tid, c);
-      EEState ee;
       chain_ee(P.rb, c, ee);
+      f = contact ? contact_force(C, plane, ee) : 0.f;
 #pragma unroll
       for (int a = 0; a < 3; ++a) m.se[a * B + tid] = ee.p[a];
-      m.se[3 * B + tid] = contact ? contact_force(C, plane, ee) : 0.f;
+      m.se[3 * B + tid] = f;
     }
     bar_sync(BAR_FORCES, 3 * B);
     ws_backward_rows(P.rb, m, WS_ROWS2, tid);
@@ -1007,7 +1025,17 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
     if (s == 0) ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, 0, tid);
     bar_arrive(BAR_STEP, 3 * B);
     if (s + 1 < T) ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, s + 1, tid);
+    if (s >= 1) {
+      float cst = motion_cost(C, pdes, Rd, ee);
+      if (contact) {
+        const float ef = C.fdes - f;
+        cst += C.wforce * ef * ef + C.wreg * f * f;
+      }
+      S2 += static_cast<double>(cst);
+    }
   }
+  m.s2[tid] = S2;
+  bar_arrive(BAR_DONE, 2 * B);
 }
 
 template <bool STORE_NOISE>

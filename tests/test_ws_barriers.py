@@ -10,7 +10,8 @@ then for the forces, arrives with its rows of M and with its copy of x_s;
 at s = T it waits for the last link only.  Warp 2 waits for the odd links
 and for the last link (it forms the end-effector state for the dynamics),
 then for the forces, and arrives with its rows of M and with the step's
-input.  The model runs the three programs under named-barrier semantics (a
+input; after the last state warp 2 hands its partial cost to warp 1 (one
+more barrier).  The model runs the three programs under named-barrier semantics (a
 phase completes when `count` threads have arrived or waited) in random
 interleavings and checks that every run ends with all barriers complete,
 that no phase mixes operations of two different states, and that no wait is
@@ -22,7 +23,7 @@ import random
 import pytest
 
 NJ = 7
-BAR_LINK0, BAR_FORCES, BAR_MROWS, BAR_STEP = 1, 8, 9, 10
+BAR_LINK0, BAR_FORCES, BAR_MROWS, BAR_STEP, BAR_DONE = 1, 8, 9, 10, 11
 B = 32
 
 
@@ -53,6 +54,7 @@ def warp1(T):
             yield ("arrive", BAR_STEP, 3 * B, s)
         else:
             yield ("sync", BAR_LINK0 + NJ - 1, link_count(NJ - 1, True), s)
+    yield ("sync", BAR_DONE, 2 * B, T)
 
 
 def warp2(T):
@@ -63,6 +65,7 @@ def warp2(T):
         yield ("sync", BAR_FORCES, 3 * B, s)
         yield ("arrive", BAR_MROWS, 3 * B, s)
         yield ("arrive", BAR_STEP, 3 * B, s)
+    yield ("arrive", BAR_DONE, 2 * B, T)
 
 
 def run(T, seed):
@@ -119,6 +122,7 @@ def test_model_detects_a_broken_protocol():
             yield ("sync", BAR_FORCES, 3 * B, s)
             yield ("arrive", BAR_MROWS, 3 * B, s)
             yield ("arrive", BAR_STEP, 3 * B, s)
+        yield ("arrive", BAR_DONE, 2 * B, T)
 
     warp2 = bad
     try:
