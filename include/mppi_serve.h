@@ -54,8 +54,11 @@ typedef struct mppi_server_config {
   int max_problems;   /* registered problems, 1..4096                         */
   int max_batch;      /* requests per tick, 1..1024                           */
   int lanes;          /* ticks in flight at once, 1..4                        */
-  int variant;        /* rollout kernel: 0 autotune, 1 unrolled, 2 rolled     */
-  int rollout_block;  /* samples per tile: 0 autotune, or 32, 64, 128         */
+  int variant;        /* rollout kernel: 0 autotune (unrolled until tuned),
+                         1 unrolled, 2 rolled, 3 warp-specialised (tiles of
+                         32 samples on 96 threads)                            */
+  int rollout_block;  /* samples per tile for variants 1, 2: 0 autotune, or
+                         32, 64, 128                                          */
 } mppi_server_config;
 
 /* Creates the server on the current device: allocates the pool, the problem

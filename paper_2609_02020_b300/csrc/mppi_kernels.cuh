@@ -632,14 +632,15 @@ constexpr int WS_THREADS = 3 * WS_B;  // three warps
 // motion: (R0..R3)(R4..R7)(R8 p0 p1 p2)(Vw Vv0)(Vv1 Vv2 Aw0 Aw1)(Aw2 Av).
 constexpr int WS_REC = 52;
 constexpr int WS_HANDOFF = 6;  // float4 offset of the hand-off part
-constexpr int EE_FIELDS = 4;          // end-effector point 3, contact force
 constexpr int V_SLOTS = 3;            // ring of inputs v_s, slot s % 3
 // named barriers (0 is __syncthreads): one per link, link forces complete,
 // rows of M complete, inputs of the step complete
 constexpr int BAR_LINK0 = 1, BAR_FORCES = 8, BAR_MROWS = 9, BAR_STEP = 10, BAR_DONE = 11;
 constexpr int WS_FLOATS_PER_SAMPLE = NJ * WS_REC + NJ * (NJ + 1) / 2 + NJ /* h */ +
-                                     2 * NJ /* q, qd */ + V_SLOTS * NJ /* v ring */ + EE_FIELDS +
-                                     2 /* warp 2's partial cost, a double */;
+                                     2 * NJ /* q, qd */ + V_SLOTS * NJ /* v ring */;
+// The last float4 of each record is free: link 0's holds the end-effector
+// point and contact force for the dynamics, link 1's warp 2's partial cost.
+constexpr int WS_PAD = 48;
 
 __device__ __forceinline__ void bar_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -663,8 +664,7 @@ __host__ __device__ constexpr size_t ws_smem_bytes() {
 }
 
 struct WsSmem {
-  float *sl, *sc, *sM, *sh, *sq, *sqd, *sv, *se;
-  double* s2;
+  float *sl, *sc, *sM, *sh, *sq, *sqd, *sv;
 };
 
 __device__ __forceinline__ WsSmem ws_carve(float* base) {
@@ -677,8 +677,6 @@ __device__ __forceinline__ WsSmem ws_carve(float* base) {
   m.sq = m.sh + NJ * B;                     // [7][B]
   m.sqd = m.sq + NJ * B;                    // [7][B]
   m.sv = m.sqd + NJ * B;                    // [3][7][B]: v_s in slot s % 3
-  m.se = m.sv + V_SLOTS * NJ * B;           // [4][B]: end-effector point, contact force
-  m.s2 = reinterpret_cast<double*>(m.se + EE_FIELDS * B);  // [B] (8-byte aligned)
   return m;
 }
 
@@ -687,6 +685,15 @@ __device__ __forceinline__ float4* ws_rec(float* base, int i, int tid) {
 }
 __device__ __forceinline__ const float4* ws_rec(const float* base, int i, int tid) {
   return reinterpret_cast<const float4*>(base + (i * WS_B + tid) * WS_REC);
+}
+
+// end-effector point (3) and contact force of sample tid, and warp 2's
+// partial cost of sample tid, in the free tails of records 0 and 1
+__device__ __forceinline__ float* ws_ee(const WsSmem& m, int tid) {
+  return m.sl + tid * WS_REC + WS_PAD;
+}
+__device__ __forceinline__ double* ws_s2(const WsSmem& m, int tid) {
+  return reinterpret_cast<double*>(m.sl + (WS_B + tid) * WS_REC + WS_PAD);
 }
 
 __device__ __forceinline__ void ws_store_axis(float* sl, int i, int tid, const float z[3],
@@ -856,10 +863,11 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
     ldlt_factor<NJ, true>(M, invD);
     bar_sync(BAR_STEP, 3 * B);
     const float* v = m.sv + (s % V_SLOTS) * NJ * B + tid;
-    const float f = m.se[3 * B + tid];
+    const float* ees = ws_ee(m, tid);
+    const float f = ees[3];
     float rhs[NJ];
     if (contact && f > 0.f) {
-      const float pe[3] = {m.se[tid], m.se[B + tid], m.se[2 * B + tid]};
+      const float pe[3] = {ees[0], ees[1], ees[2]};
       const float Fc[3] = {f * plane[0], f * plane[1], f * plane[2]};
       float pxF[3];
       cross3(pe, Fc, pxF);
@@ -965,7 +973,7 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
       Sacc += static_cast<double>(C.wterm * motion_cost(C, pdes, Rd, ee));
   }
   bar_sync(BAR_DONE, 2 * B);
-  return static_cast<float>(Sacc + m.s2[tid]);
+  return static_cast<float>(Sacc + *ws_s2(m, tid));
 }
 
 // warp 2: the inputs v_s = u_s + dtau_s (Eq. 2) into slot s % 3
@@ -1015,9 +1023,10 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
       ws_load_chain(m.sc, NJ - 1, tid, c);
       chain_ee(P.rb, c, ee);
       f = contact ? contact_force(C, plane, ee) : 0.f;
+      float* ees = ws_ee(m, tid);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) m.se[a * B + tid] = ee.p[a];
-      m.se[3 * B + tid] = f;
+      for (int a = 0; a < 3; ++a) ees[a] = ee.p[a];
+      ees[3] = f;
     }
     bar_sync(BAR_FORCES, 3 * B);
     ws_backward_rows(P.rb, m, WS_ROWS2, tid);
@@ -1034,7 +1043,7 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
       S2 += static_cast<double>(cst);
     }
   }
-  m.s2[tid] = S2;
+  *ws_s2(m, tid) = S2;
   bar_arrive(BAR_DONE, 2 * B);
 }
 

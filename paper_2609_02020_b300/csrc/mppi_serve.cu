@@ -74,9 +74,18 @@ __device__ __forceinline__ const TickItem* desc_items(const char* d) {
 
 constexpr int PROBK_FLOATS = static_cast<int>((sizeof(ProbK) + 15) / 16 * 4);
 
+// Variant 3 (warp-specialised): 32 samples per tile on 96 threads, the
+// problem's parameters plus the warp-specialised kernel's records; the plan
+// is read from global memory.
 __host__ __device__ constexpr size_t serve_smem_bytes(int variant, int B) {
-  return sizeof(float) * (static_cast<size_t>(PROBK_FLOATS) + T_MAX * NJ + 32 +
-                          (variant == 2 ? static_cast<size_t>(ROLLED_FLOATS_PER_THREAD) * B : 0));
+  return variant == 3
+             ? sizeof(float) * static_cast<size_t>(PROBK_FLOATS) + ws_smem_bytes()
+             : sizeof(float) * (static_cast<size_t>(PROBK_FLOATS) + T_MAX * NJ + 32 +
+                                (variant == 2 ? static_cast<size_t>(ROLLED_FLOATS_PER_THREAD) * B
+                                              : 0));
+}
+__host__ __device__ constexpr int serve_threads(int variant, int B) {
+  return variant == 3 ? WS_THREADS : B;
 }
 
 // Largest i with key(items[i]) <= x (items sorted by key, items[0] key 0).
@@ -140,6 +149,59 @@ serve_rollout_kernel(const char* __restrict__ desc, const ProbK* __restrict__ pr
   }
 }
 
+// Warp-specialised tiles: the three roles of rollout_kernel_ws on the
+// tile's 32 samples, the problem's parameters in shared memory; every warp
+// meets every barrier of a tile, and the block synchronises between tiles.
+__global__ void __launch_bounds__(WS_THREADS)
+serve_rollout_kernel_ws(const char* __restrict__ desc, const ProbK* __restrict__ probs,
+                        int* __restrict__ counters) {
+  extern __shared__ float4 dsm4[];
+  float* dsm = reinterpret_cast<float*>(dsm4);
+  ProbK* sP = reinterpret_cast<ProbK*>(dsm);
+  float* s_in = dsm + PROBK_FLOATS;
+  const WsSmem m = ws_carve(s_in + 32);
+  __shared__ int s_tile, s_item;
+  const TickHeader* H = reinterpret_cast<const TickHeader*>(desc);
+  const TickItem* items = desc_items(desc);
+  const int n_tiles = H->n_tiles, n_items = H->n_items;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int tile = atomicAdd(&counters[0], 1);
+      s_tile = tile;
+      if (tile < n_tiles)
+        s_item = find_item(items, n_items, tile, [](const TickItem& I) { return I.tile_begin; });
+    }
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= n_tiles) break;
+    const int it = s_item;
+    const TickItem& I = items[it];
+    if (it != cur) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(&probs[I.prob]);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(sP);
+      for (int w = threadIdx.x; w < static_cast<int>(sizeof(ProbK) / 4); w += WS_THREADS)
+        dst[w] = src[w];
+      if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = I.in[threadIdx.x];
+      cur = it;
+      __syncthreads();
+    }
+    const int k_raw = (tile - I.tile_begin) * WS_B + lane;
+    const bool live = k_raw < I.K;
+    const int k = live ? k_raw : I.K - 1;
+    if (warp == 0) {
+      ws_dynamics(*sP, s_in, m, lane);
+    } else if (warp == 1) {
+      const float Sk = ws_costs(*sP, s_in, m, lane);
+      if (live) I.S[k] = Sk;
+    } else {
+      ws_noise<true>(*sP, s_in, I.plan, I.iter, k, live, I.noise, m, lane);
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(UPDATE_THREADS)
 serve_update_kernel(const char* __restrict__ desc, const ProbK* __restrict__ probs,
                     int* __restrict__ counters, float* __restrict__ res) {
@@ -181,6 +243,7 @@ serve_update_kernel(const char* __restrict__ desc, const ProbK* __restrict__ pro
 using RolloutFn = void (*)(const char*, const ProbK*, int*);
 
 RolloutFn rollout_fn(int variant, int B) {
+  if (variant == 3) return serve_rollout_kernel_ws;
   if (variant == 2) {
     if (B == 32) return serve_rollout_kernel<2, 32>;
     if (B == 64) return serve_rollout_kernel<2, 64>;
@@ -302,7 +365,8 @@ struct Adm {
 struct Lane {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;     // tick with the tuned rollout kernel
+  cudaGraphExec_t graph_ws = nullptr;  // tick with the warp-specialised kernel
   char* h_desc = nullptr;
   char* d_desc = nullptr;
   float* h_res = nullptr;
@@ -325,6 +389,7 @@ struct mppi_server_s {
   int n_lanes = 1;
   int variant = 1, block = 32;
   int rollout_grid = 0, update_grid = 0;
+  int ws_grid = 0;  // resident warp-specialised blocks: the tiles of one wave
   std::mutex mu;
   std::condition_variable cv;
   std::deque<Req> pending;
@@ -363,12 +428,19 @@ int configure_kernels(mppi_server_s* s) {
       SCUDA(s, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(serve_smem_bytes(v, B))));
     }
+  SCUDA(s, cudaFuncSetAttribute(rollout_fn(3, WS_B), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(serve_smem_bytes(3, WS_B))));
   return MPPI_OK;
 }
 
+// Shapes the autotuner tries: (variant, samples per tile).
+constexpr int kShapes[][2] = {{1, 32}, {1, 64}, {1, 128}, {2, 32}, {2, 64}, {2, 128}, {3, WS_B}};
+
 int set_launch_shape(mppi_server_s* s, int variant, int B) {
+  if (variant == 3) B = WS_B;
   int nb = 0;
-  SCUDA(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_fn(variant, B), B,
+  SCUDA(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rollout_fn(variant, B),
+                                                          serve_threads(variant, B),
                                                           serve_smem_bytes(variant, B)));
   if (nb < 1) return sfail(s, MPPI_ERR_CUDA, "rollout kernel does not fit on an SM");
   int nu = 0;
@@ -385,11 +457,16 @@ int set_launch_shape(mppi_server_s* s, int variant, int B) {
   return MPPI_OK;
 }
 
-cudaError_t enqueue_kernels(mppi_server_s* s, Lane& L) {
+cudaError_t enqueue_kernels(mppi_server_s* s, Lane& L, bool ws) {
   cudaError_t e = cudaMemsetAsync(L.d_cnt, 0, 2 * sizeof(int), L.st);
   if (e != cudaSuccess) return e;
-  rollout_fn(s->variant, s->block)<<<s->rollout_grid, s->block, serve_smem_bytes(s->variant, s->block),
-                                      L.st>>>(L.d_desc, s->d_probs, L.d_cnt);
+  if (ws)
+    serve_rollout_kernel_ws<<<s->ws_grid, WS_THREADS, serve_smem_bytes(3, WS_B), L.st>>>(
+        L.d_desc, s->d_probs, L.d_cnt);
+  else
+    rollout_fn(s->variant, s->block)<<<s->rollout_grid, serve_threads(s->variant, s->block),
+                                        serve_smem_bytes(s->variant, s->block), L.st>>>(
+        L.d_desc, s->d_probs, L.d_cnt);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   serve_update_kernel<<<s->update_grid, UPDATE_THREADS, 0, L.st>>>(L.d_desc, s->d_probs, L.d_cnt,
@@ -397,18 +474,19 @@ cudaError_t enqueue_kernels(mppi_server_s* s, Lane& L) {
   return cudaGetLastError();
 }
 
-int ensure_graph(mppi_server_s* s, Lane& L) {
-  if (L.graph) return MPPI_OK;
+int ensure_graph(mppi_server_s* s, Lane& L, bool ws) {
+  cudaGraphExec_t& G = ws ? L.graph_ws : L.graph;
+  if (G) return MPPI_OK;
   cudaGraph_t g;
   SCUDA(s, cudaStreamBeginCapture(L.st, cudaStreamCaptureModeThreadLocal));
-  const cudaError_t e = enqueue_kernels(s, L);
+  const cudaError_t e = enqueue_kernels(s, L, ws);
   const cudaError_t e2 = cudaStreamEndCapture(L.st, &g);
   if (e != cudaSuccess) return sfail(s, MPPI_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
   if (e2 != cudaSuccess) return sfail(s, MPPI_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e2));
-  const cudaError_t e3 = cudaGraphInstantiate(&L.graph, g, 0);
+  const cudaError_t e3 = cudaGraphInstantiate(&G, g, 0);
   cudaGraphDestroy(g);
   if (e3 != cudaSuccess) {
-    L.graph = nullptr;
+    G = nullptr;
     return sfail(s, MPPI_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e3));
   }
   return MPPI_OK;
@@ -416,7 +494,8 @@ int ensure_graph(mppi_server_s* s, Lane& L) {
 
 // Fills the lane's host descriptor from admitted (problem, inputs) pairs and
 // the scratch offsets; returns the number of rollout tiles.
-void fill_desc(mppi_server_s* s, Lane& L, const std::vector<const float*>& inputs) {
+void fill_desc(mppi_server_s* s, Lane& L, const std::vector<const float*>& inputs,
+               int tile_samples) {
   TickHeader* H = reinterpret_cast<TickHeader*>(L.h_desc);
   TickItem* items = reinterpret_cast<TickItem*>(L.h_desc + kItemsOffset);
   int tiles = 0, upd = 0;
@@ -437,7 +516,7 @@ void fill_desc(mppi_server_s* s, Lane& L, const std::vector<const float*>& input
     I.S = reinterpret_cast<float*>(s->d_pool + a.off);
     I.noise = reinterpret_cast<float*>(s->d_pool + a.off + (sizeof(float) * p.K + 255) / 256 * 256);
     std::memcpy(I.in, inputs[i], sizeof(I.in));
-    tiles += (p.K + s->block - 1) / s->block;
+    tiles += (p.K + tile_samples - 1) / tile_samples;
     upd += p.T * NJ;
   }
   H->n_items = static_cast<int>(L.adm.size());
@@ -514,18 +593,25 @@ int round_locked(mppi_server_s* s, int* launched, bool* progress) {
     taken.push_back(i);
   }
   if (L->adm.empty()) return MPPI_OK;
-  int rc = ensure_graph(s, *L);
+  // a tick whose 32-sample tiles all fit in one wave of the warp-specialised
+  // kernel is latency-bound and runs on it; bigger ticks are throughput-bound
+  // and run on the tuned kernel (variant 0 only)
+  long long ws_tiles = 0;
+  for (const Adm& a : L->adm) ws_tiles += (s->probs[a.id].K + WS_B - 1) / WS_B;
+  const bool ws = s->cfg.variant == 0 ? ws_tiles <= s->ws_grid : s->variant == 3;
+  int rc = ensure_graph(s, *L, ws);
   if (rc != MPPI_OK) {
     for (const Adm& a : L->adm) pool_free(&s->pool, a.off);
     L->adm.clear();
     return rc;
   }
-  fill_desc(s, *L, inputs);
+  fill_desc(s, *L, inputs, ws ? WS_B : s->block);
+  const cudaGraphExec_t G = ws ? L->graph_ws : L->graph;
   for (const Adm& a : L->adm) s->probs[a.id].inflight = true;
   const size_t n = L->adm.size();
   cudaError_t e = cudaMemcpyAsync(L->d_desc, L->h_desc, desc_bytes(static_cast<int>(n)),
                                   cudaMemcpyHostToDevice, L->st);
-  if (e == cudaSuccess) e = cudaGraphLaunch(L->graph, L->st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(G, L->st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(L->h_res, L->d_res, sizeof(float) * RES_FLOATS * n, cudaMemcpyDeviceToHost, L->st);
   if (e == cudaSuccess) e = cudaEventRecord(L->ev, L->st);
@@ -631,8 +717,8 @@ int mppi_server_create(const mppi_server_config* cfg, mppi_server_t* out) {
     return sfail(nullptr, MPPI_ERR_INVALID_ARG, "max_batch must be in 1..1024");
   if (cfg->lanes < 1 || cfg->lanes > MAX_LANES)
     return sfail(nullptr, MPPI_ERR_INVALID_ARG, "lanes must be in 1..4");
-  if (cfg->variant < 0 || cfg->variant > 2)
-    return sfail(nullptr, MPPI_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+  if (cfg->variant < 0 || cfg->variant > 3)
+    return sfail(nullptr, MPPI_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   if (cfg->rollout_block != 0 && cfg->rollout_block != 32 && cfg->rollout_block != 64 &&
       cfg->rollout_block != 128)
     return sfail(nullptr, MPPI_ERR_INVALID_ARG, "rollout_block must be 0, 32, 64 or 128");
@@ -670,6 +756,13 @@ int mppi_server_create(const mppi_server_config* cfg, mppi_server_t* out) {
   s->probs.reserve(cfg->max_problems);
   int rc = configure_kernels(s);
   if (rc != MPPI_OK) return bail(rc);
+  {
+    int nws = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &nws, serve_rollout_kernel_ws, WS_THREADS, serve_smem_bytes(3, WS_B));
+    if (e != cudaSuccess || nws < 1) return bail(sfail(nullptr, MPPI_ERR_CUDA, "ws occupancy"));
+    s->ws_grid = nws * s->sm_count;
+  }
   rc = set_launch_shape(s, cfg->variant ? cfg->variant : 1, cfg->rollout_block ? cfg->rollout_block : 32);
   if (rc != MPPI_OK) return bail(rc);
   *out = s;
@@ -683,6 +776,7 @@ int mppi_server_destroy(mppi_server_t s) {
     Lane& L = s->lanes[l];
     if (L.st) cudaStreamSynchronize(L.st);
     if (L.graph) cudaGraphExecDestroy(L.graph);
+    if (L.graph_ws) cudaGraphExecDestroy(L.graph_ws);
     if (L.ev) cudaEventDestroy(L.ev);
     if (L.h_desc) cudaFreeHost(L.h_desc);
     if (L.h_res) cudaFreeHost(L.h_res);
@@ -877,6 +971,17 @@ int mppi_server_start(mppi_server_t s) {
   if (!s) return sfail(s, MPPI_ERR_INVALID_ARG, "null server");
   if (s->running.load()) return MPPI_OK;
   if (s->thr.joinable()) s->thr.join();
+  {
+    // capture every lane's tick graphs now rather than on a first request
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (int l = 0; l < s->n_lanes; ++l) {
+      Lane& L = s->lanes[l];
+      if (L.busy) continue;
+      int rc = ensure_graph(s, L, false);
+      if (rc == MPPI_OK && (s->cfg.variant == 0 || s->variant == 3)) rc = ensure_graph(s, L, true);
+      if (rc != MPPI_OK) return rc;
+    }
+  }
   s->stop_flag.store(false);
   s->running.store(true);
   s->thr = std::thread(scheduler_main, s);
@@ -947,13 +1052,15 @@ int mppi_server_autotune(mppi_server_t s, float* best_ms) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int rc = MPPI_OK;
-  for (int v = 1; v <= 2 && rc == MPPI_OK; ++v) {
+  for (const auto& shape : kShapes) {
+    if (rc != MPPI_OK) break;
+    const int v = shape[0], B = shape[1];
     if (s->cfg.variant && v != s->cfg.variant) continue;
-    for (int B : {32, 64, 128}) {
-      if (s->cfg.rollout_block && B != s->cfg.rollout_block) continue;
+    {
+      if (s->cfg.rollout_block && v != 3 && B != s->cfg.rollout_block) continue;
       rc = set_launch_shape(s, v, B);
       if (rc != MPPI_OK) break;
-      fill_desc(s, L, inputs);
+      fill_desc(s, L, inputs, v == 3 ? WS_B : B);
       const size_t n = L.adm.size();
       cudaError_t e = cudaMemcpyAsync(L.d_desc, L.h_desc, desc_bytes(static_cast<int>(n)),
                                       cudaMemcpyHostToDevice, L.st);
@@ -962,7 +1069,8 @@ int mppi_server_autotune(mppi_server_t s, float* best_ms) {
         e = cudaMemsetAsync(L.d_cnt, 0, 2 * sizeof(int), L.st);
         if (e == cudaSuccess) e = cudaEventRecord(e0, L.st);
         if (e == cudaSuccess) {
-          rollout_fn(v, B)<<<s->rollout_grid, B, serve_smem_bytes(v, B), L.st>>>(L.d_desc, s->d_probs, L.d_cnt);
+          rollout_fn(v, B)<<<s->rollout_grid, serve_threads(v, B), serve_smem_bytes(v, B), L.st>>>(
+              L.d_desc, s->d_probs, L.d_cnt);
           e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, L.st);
