@@ -18,6 +18,13 @@ constexpr int T_MAX = 256;
 constexpr int ROLLOUT_BLOCK = 32;
 constexpr int UPDATE_BLOCK = 256;
 
+// A rollout block's results are written: the update kernel, launched as a
+// programmatic dependent, may start to launch (it still waits for this
+// grid's completion before it reads them).
+__device__ __forceinline__ void allow_dependent_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Offsets in the per-handle output record (floats): tau0, status, stats.
 constexpr int OUT_TAU0 = 0;
 constexpr int OUT_STATUS = 7;   // written as an int: 0 ok, 1 no finite cost
@@ -135,6 +142,7 @@ rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
   S[k] = rollout_sample<STORE_NOISE>(P, s_in, k < k_split ? s_plan : s_prop, *iter_p, k, noise);
+  allow_dependent_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -599,6 +607,7 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
   S[k] = rollout_sample_rolled<STORE_NOISE, B, FEAT>(P, s_in, k < k_split ? s_plan : s_prop,
                                                      *iter_p, k, noise, s_work, threadIdx.x,
                                                      s_obs, n_obs);
+  allow_dependent_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -1076,6 +1085,7 @@ rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
   } else {
     ws_noise<STORE_NOISE>(P, s_in, k < k_split ? plan : prop, *iter_p, k, live, noise, m, lane);
   }
+  allow_dependent_launch();
 }
 
 // Wrench estimates F = Jbar^T (v - g(q)) (Eq. 13) for n pairs (q_i, v_i),
@@ -1301,6 +1311,9 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
               unsigned long long* __restrict__ iter_p, const float* __restrict__ prop = nullptr,
               const int* __restrict__ ksplit_p = nullptr, float* __restrict__ tau_dst = nullptr,
               float* __restrict__ plan_dst = nullptr) {
+  // launched as a programmatic dependent of the rollout kernel: wait here
+  // until the rollouts' results are visible (a no-op otherwise)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int e = blockIdx.x;
   const float* nrow = noise + static_cast<size_t>(e) * K;
   const int k_split = ksplit_p ? *ksplit_p : K;

@@ -405,16 +405,26 @@ cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const f
                           float* ustar, float* plan_next, float* out, unsigned long long* iter,
                           const float* prop = nullptr, const int* ksplit = nullptr,
                           float* tau_dst = nullptr, float* plan_dst = nullptr) {
-  const int grid = h->P.T * NJ;
+  // programmatic dependent launch: the update kernel's blocks may start as
+  // the rollout kernel's retire and wait (griddepcontrol.wait) for its
+  // results, which hides the launch gap between the two kernels
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(h->P.T * NJ);
+  lc.blockDim = dim3(UPDATE_THREADS);
+  lc.dynamicSmemBytes = 0;
+  lc.stream = h->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  const int K = h->P.K, T = h->P.T;
+  const float lambda = h->P.lambda;
   if (h->reduce_fp64)
-    update_kernel<double><<<grid, UPDATE_THREADS, 0, h->stream>>>(
-        h->P.K, h->P.T, h->P.lambda, S, noise, plan, ustar, plan_next, out, iter, prop, ksplit,
-        tau_dst, plan_dst);
-  else
-    update_kernel<float><<<grid, UPDATE_THREADS, 0, h->stream>>>(
-        h->P.K, h->P.T, h->P.lambda, S, noise, plan, ustar, plan_next, out, iter, prop, ksplit,
-        tau_dst, plan_dst);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&lc, update_kernel<double>, K, T, lambda, S, noise, plan, ustar,
+                              plan_next, out, iter, prop, ksplit, tau_dst, plan_dst);
+  return cudaLaunchKernelEx(&lc, update_kernel<float>, K, T, lambda, S, noise, plan, ustar,
+                            plan_next, out, iter, prop, ksplit, tau_dst, plan_dst);
 }
 
 // the whole update on device buffers: rollouts from the inputs at `in`, then
