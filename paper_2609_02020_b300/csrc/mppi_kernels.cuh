@@ -660,16 +660,22 @@ __device__ __forceinline__ void bar_arrive(int id, int count) {
 
 // Threads at link i's barrier: warp 0 and the force warp of link i, and for
 // the last link also the other force warp (it forms the end-effector state)
-// while s < T; at s = T only the last link's barrier runs, for warp 1.
-__host__ __device__ constexpr int ws_link_count(int i, bool last_state) {
-  return last_state ? 2 * WS_B : (i == NJ - 1 ? 3 * WS_B : 2 * WS_B);
+// while s < T; at s = T only the last link's barrier runs, for warp 1 and,
+// with the collision cost, warps 3 and 4 (they read the last state's link
+// points after it).
+__host__ __device__ constexpr int ws_link_count(int i, bool last_state, bool coll = false) {
+  return last_state ? (coll ? 4 : 2) * WS_B : (i == NJ - 1 ? 3 * WS_B : 2 * WS_B);
 }
+// Warps of the kernel, and threads at the barriers every warp meets.
+__host__ __device__ constexpr int ws_warps(bool coll) { return coll ? 5 : 3; }
+__host__ __device__ constexpr int ws_threads(bool coll) { return ws_warps(coll) * WS_B; }
 
 // Dynamic shared memory of rollout_kernel_ws (independent of T: the plans
 // are read from global memory, where they stay in L1).  56.2 KB: four
 // blocks fit on an SM.
-__host__ __device__ constexpr size_t ws_smem_bytes() {
-  return sizeof(float) * (32 + static_cast<size_t>(WS_FLOATS_PER_SAMPLE) * WS_B);
+__host__ __device__ constexpr size_t ws_smem_bytes(bool coll = false) {
+  return sizeof(float) * (32 + (coll ? OBS_SMEM_FLOATS : 0) +
+                          static_cast<size_t>(WS_FLOATS_PER_SAMPLE) * WS_B);
 }
 
 struct WsSmem {
@@ -701,8 +707,8 @@ __device__ __forceinline__ const float4* ws_rec(const float* base, int i, int ti
 __device__ __forceinline__ float* ws_ee(const WsSmem& m, int tid) {
   return m.sl + tid * WS_REC + WS_PAD;
 }
-__device__ __forceinline__ double* ws_s2(const WsSmem& m, int tid) {
-  return reinterpret_cast<double*>(m.sl + (WS_B + tid) * WS_REC + WS_PAD);
+__device__ __forceinline__ double* ws_s2(const WsSmem& m, int tid, int slot = 0) {
+  return reinterpret_cast<double*>(m.sl + ((1 + slot) * WS_B + tid) * WS_REC + WS_PAD);
 }
 
 __device__ __forceinline__ void ws_store_axis(float* sl, int i, int tid, const float z[3],
@@ -834,8 +840,10 @@ constexpr unsigned WS_ROWS1 = (1u << 5) | (1u << 2) | (1u << 1);
 constexpr unsigned WS_ROWS2 = (1u << 4) | (1u << 3) | (1u << 0);
 
 // warp 0
+template <bool COLL>
 __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, const WsSmem& m,
                                             int tid) {
+  constexpr int NA = ws_threads(COLL);
   constexpr int B = WS_B;
   const int T = P.T;
   const CostK& C = P.cost;
@@ -860,17 +868,17 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
       forward_link_chain(P.rb.L[i], m.sq[i * B + tid], m.sqd[i * B + tid], c, z, w);
       ws_store_axis(m.sl, i, tid, z, w);
       ws_store_chain(m.sc, i, tid, c);
-      if (!last || i == NJ - 1) bar_arrive(BAR_LINK0 + i, ws_link_count(i, last));
+      if (!last || i == NJ - 1) bar_arrive(BAR_LINK0 + i, ws_link_count(i, last, COLL));
     }
     if (last) break;
-    bar_sync(BAR_FORCES, 3 * B);
+    bar_sync(BAR_FORCES, NA);
     ws_backward_h(P.rb, m, tid);
     bar_sync(BAR_MROWS, 3 * B);
     float M[NJ * (NJ + 1) / 2], invD[NJ];
 #pragma unroll
     for (int a = 0; a < NJ * (NJ + 1) / 2; ++a) M[a] = m.sM[a * B + tid];
     ldlt_factor<NJ, true>(M, invD);
-    bar_sync(BAR_STEP, 3 * B);
+    bar_sync(BAR_STEP, NA);
     const float* v = m.sv + (s % V_SLOTS) * NJ * B + tid;
     const float* ees = ws_ee(m, tid);
     const float f = ees[3];
@@ -918,8 +926,10 @@ __device__ __forceinline__ void ws_forces(const ProbK& P, const WsSmem& m, int f
 }
 
 // warp 1: forces of the even links and the running cost; returns S_k
+template <bool COLL>
 __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const WsSmem& m,
                                           int tid) {
+  constexpr int NA = ws_threads(COLL);
   constexpr int B = WS_B;
   const int T = P.T;
   const CostK& C = P.cost;
@@ -937,11 +947,11 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
     if (s < T) {
       ws_forces(P, m, 0, tid);  // ends with the last link (even)
       ws_load_chain(m.sc, NJ - 1, tid, c);
-      bar_sync(BAR_FORCES, 3 * B);
+      bar_sync(BAR_FORCES, NA);
       ws_backward_rows(P.rb, m, WS_ROWS1, tid);
       bar_arrive(BAR_MROWS, 3 * B);
     } else {
-      bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, true));
+      bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, true, COLL));
       ws_load_chain(m.sc, NJ - 1, tid, c);
     }
     // x_s and v_{s-1}, copied before warp 0 may overwrite them
@@ -953,7 +963,7 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
       qd[j] = m.sqd[j * B + tid];
       v[j] = vp[j * B];
     }
-    if (s < T) bar_arrive(BAR_STEP, 3 * B);
+    if (s < T) bar_arrive(BAR_STEP, NA);
     if (s == 0) continue;
     // running cost l(x_s, v_{s-1}), Eq. 9-14: the joint terms here, the
     // motion and force terms on warp 2 for s < T and here for s = T
@@ -981,8 +991,10 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
     if (s == T && C.wterm != 0.f)
       Sacc += static_cast<double>(C.wterm * motion_cost(C, pdes, Rd, ee));
   }
-  bar_sync(BAR_DONE, 2 * B);
-  return static_cast<float>(Sacc + *ws_s2(m, tid));
+  bar_sync(BAR_DONE, (COLL ? 4 : 2) * B);
+  double S = Sacc + *ws_s2(m, tid);
+  if (COLL) S += *ws_s2(m, tid, 1) + *ws_s2(m, tid, 2);
+  return static_cast<float>(S);
 }
 
 // warp 2: the inputs v_s = u_s + dtau_s (Eq. 2) into slot s % 3
@@ -1006,10 +1018,11 @@ __device__ __forceinline__ void ws_draw(const ProbK& P, const float* plan, uint6
 // warp 2: forces of the odd links, the end-effector state and contact force
 // (for the dynamics and for the motion and force terms of l(x_s, v_{s-1}),
 // s = 1..T-1), and the inputs one step ahead
-template <bool STORE_NOISE>
+template <bool STORE_NOISE, bool COLL>
 __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const float* plan,
                                          uint64_t iter, int k, bool live,
                                          float* __restrict__ noise, const WsSmem& m, int tid) {
+  constexpr int NA = ws_threads(COLL);
   constexpr int B = WS_B;
   const int T = P.T;
   const CostK& C = P.cost;
@@ -1037,11 +1050,11 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
       for (int a = 0; a < 3; ++a) ees[a] = ee.p[a];
       ees[3] = f;
     }
-    bar_sync(BAR_FORCES, 3 * B);
+    bar_sync(BAR_FORCES, NA);
     ws_backward_rows(P.rb, m, WS_ROWS2, tid);
     bar_arrive(BAR_MROWS, 3 * B);
     if (s == 0) ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, 0, tid);
-    bar_arrive(BAR_STEP, 3 * B);
+    bar_arrive(BAR_STEP, NA);
     if (s + 1 < T) ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, s + 1, tid);
     if (s >= 1) {
       float cst = motion_cost(C, pdes, Rd, ee);
@@ -1053,24 +1066,126 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
     }
   }
   *ws_s2(m, tid) = S2;
-  bar_arrive(BAR_DONE, 2 * B);
+  bar_arrive(BAR_DONE, (COLL ? 4 : 2) * B);
 }
 
-template <bool STORE_NOISE>
-__global__ void __launch_bounds__(WS_THREADS)
+// Warps 3 and 4 (collision cost, Eq. 15): the link points of x_s are copied
+// from the hand-off records (and the end-effector point from warp 2's slot)
+// between the forces and the step barriers, then the pairs of this warp's
+// part are charged off the critical path: part 0 the link-link pairs and
+// links 0-1 against the obstacles, part 1 links 2-6 against the obstacles.
+// Link i spans pts[i] .. pts[i + 1]; same terms as collision_cost.
+template <int PART>
+__device__ __forceinline__ float ws_collision_pairs(const CostK& C, const float pts[NJ + 1][3],
+                                                    const float* s_obs, int n_obs) {
+  const float* lrad = s_obs + OBS_FIELDS * OBS_MAX;
+  float acc = 0.f;
+  float d[NJ][3];
+#pragma unroll
+  for (int i = 0; i < NJ; ++i)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[i][a] = pts[i + 1][a] - pts[i][a];
+  if (PART == 0) {
+#pragma unroll
+    for (int i = 0; i < NJ - 2; ++i)
+#pragma unroll
+      for (int j = i + 2; j < NJ; ++j) {
+        const float g2 = segment_dist2(pts[i], d[i], C.seg_a[i], C.seg_ia[i], pts[j], d[j],
+                                       C.seg_a[j], C.seg_ia[j]);
+        acc += collision_term(C.coll, g2, lrad[i] + lrad[j], C.dth_self);
+      }
+  }
+  constexpr int i0 = PART == 0 ? 0 : 2, i1 = PART == 0 ? 2 : NJ;
+#pragma unroll
+  for (int i = i0; i < i1; ++i) {
+#pragma unroll 1
+    for (int o = 0; o < n_obs; ++o) {
+      const float* ob = s_obs + OBS_FIELDS * o;
+      const float g2 = segment_dist2(pts[i], d[i], C.seg_a[i], C.seg_ia[i], ob, ob + 3, ob[6],
+                                     ob[7]);
+      acc += collision_term(C.coll, g2, lrad[i] + ob[8], C.dth_obs);
+    }
+  }
+  return acc;
+}
+
+template <int PART>
+__device__ __forceinline__ void ws_collision(const ProbK& P, const WsSmem& m, const float* s_obs,
+                                             int n_obs, int tid) {
+  constexpr int NA = ws_threads(true);
+  const int T = P.T;
+  const CostK& C = P.cost;
+  double Sc = 0.0;
+  for (int s = 0; s <= T; ++s) {
+    float pts[NJ + 1][3];
+    if (s < T) {
+      bar_sync(BAR_FORCES, NA);
+#pragma unroll
+      for (int i = 0; i < NJ; ++i) {
+        const float4 r = ws_rec(m.sc, i, tid)[2];  // (R8 p0 p1 p2)
+        pts[i][0] = r.y; pts[i][1] = r.z; pts[i][2] = r.w;
+      }
+      const float* ees = ws_ee(m, tid);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) pts[NJ][a] = ees[a];
+      bar_arrive(BAR_STEP, NA);
+    } else {
+      bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, true, true));
+#pragma unroll
+      for (int i = 0; i < NJ; ++i) {
+        const float4 r = ws_rec(m.sc, i, tid)[2];
+        pts[i][0] = r.y; pts[i][1] = r.z; pts[i][2] = r.w;
+      }
+      ChainState c;
+      ws_load_chain(m.sc, NJ - 1, tid, c);
+      EEState ee;
+      chain_ee(P.rb, c, ee);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) pts[NJ][a] = ee.p[a];
+    }
+    if (s == 0) continue;
+    Sc += static_cast<double>(C.wcoll * ws_collision_pairs<PART>(C, pts, s_obs, n_obs));
+  }
+  *ws_s2(m, tid, 1 + PART) = Sc;
+  bar_arrive(BAR_DONE, 4 * WS_B);
+}
+
+template <bool STORE_NOISE, bool COLL = false>
+__global__ void __launch_bounds__(ws_threads(COLL))
 rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
                   const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
                   float* __restrict__ S, float* __restrict__ noise,
                   const float* __restrict__ prop = nullptr,
-                  const int* __restrict__ ksplit_p = nullptr) {
+                  const int* __restrict__ ksplit_p = nullptr,
+                  const ObsK* __restrict__ obs = nullptr) {
   extern __shared__ float4 dsm4[];
   float* dsm = reinterpret_cast<float*>(dsm4);
   const int K = P.K;
   const int k_split = ksplit_p ? *ksplit_p : K;
   float* s_in = dsm;
+  float* s_obs = s_in + 32;  // COLL: obstacles (start, direction, |d|^2, 1/|d|^2, radius), radii
   if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
+  int n_obs = 0;
+  if (COLL) {
+    n_obs = min(max(obs->n, 0), OBS_MAX);
+    if (threadIdx.x < n_obs) {
+      const float* o = obs->o[threadIdx.x];
+      float* so = s_obs + OBS_FIELDS * threadIdx.x;
+      float e = 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        so[a] = o[a];
+        so[3 + a] = o[3 + a] - o[a];
+        e = fmaf(so[3 + a], so[3 + a], e);
+      }
+      so[6] = e;
+      so[7] = e > 1e-12f ? 1.f / e : 0.f;
+      so[8] = o[6];
+    }
+    if (threadIdx.x < NJ) s_obs[OBS_FIELDS * OBS_MAX + threadIdx.x] = P.cost.lrad[threadIdx.x];
+  }
   __syncthreads();
-  const WsSmem m = ws_carve(s_in + 32);
+  const WsSmem m = ws_carve(s_in + 32 + (COLL ? OBS_SMEM_FLOATS : 0));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // lanes past K run sample K - 1 so that every warp meets every barrier;
   // they write nothing
@@ -1078,12 +1193,16 @@ rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
   const bool live = k_raw < K;
   const int k = live ? k_raw : K - 1;
   if (warp == 0) {
-    ws_dynamics(P, s_in, m, lane);
+    ws_dynamics<COLL>(P, s_in, m, lane);
   } else if (warp == 1) {
-    const float Sk = ws_costs(P, s_in, m, lane);
+    const float Sk = ws_costs<COLL>(P, s_in, m, lane);
     if (live) S[k] = Sk;
-  } else {
-    ws_noise<STORE_NOISE>(P, s_in, k < k_split ? plan : prop, *iter_p, k, live, noise, m, lane);
+  } else if (warp == 2) {
+    ws_noise<STORE_NOISE, COLL>(P, s_in, k < k_split ? plan : prop, *iter_p, k, live, noise, m,
+                                lane);
+  } else if (COLL) {
+    if (warp == 3) ws_collision<0>(P, m, s_obs, n_obs, lane);
+    else ws_collision<1>(P, m, s_obs, n_obs, lane);
   }
   allow_dependent_launch();
 }

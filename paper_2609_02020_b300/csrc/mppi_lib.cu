@@ -28,17 +28,23 @@ using namespace mppi_dev;
 //   rolled   114     104     103     139     139     268
 //   register 114     128     127     125     122     214
 // The rolled kernel carries the optional cost terms.
-static int default_variant(int K) {
+// With the collision cost (coll) the alternative is the rolled kernel.
+static int default_variant(int K, bool coll = false) {
+  const int other = coll ? 2 : 1;
   int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel_ws<true>, WS_THREADS,
-                                                    ws_smem_bytes()) != cudaSuccess) {
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = coll ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel_ws<true, true>,
+                                                             ws_threads(true), ws_smem_bytes(true))
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel_ws<true>,
+                                                             ws_threads(false), ws_smem_bytes());
+  if (e != cudaSuccess) {
     cudaGetLastError();
-    return 1;
+    return other;
   }
   const long long ws_blocks = (static_cast<long long>(K) + WS_B - 1) / WS_B;
-  return ws_blocks <= static_cast<long long>(sms) * per_sm ? 3 : 1;
+  return ws_blocks <= static_cast<long long>(sms) * per_sm ? 3 : other;
 }
 
 static_assert(MPPI_OBS_MAX == OBS_MAX, "obstacle capacity of the ABI and the kernels");
@@ -350,6 +356,14 @@ cudaError_t prepare_rolled(int T) {
 }
 
 cudaError_t prepare_rollout(mppi_s* h) {
+  if (h->feat == FEAT_COLL && h->variant == 3) {
+    const int smem = static_cast<int>(ws_smem_bytes(true));
+    cudaError_t e = cudaFuncSetAttribute(rollout_kernel_ws<true, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(rollout_kernel_ws<false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
   switch (h->feat) {
     case FEAT_FEST: return prepare_rolled<FEAT_FEST>(h->P.T);
     case FEAT_COLL: return prepare_rolled<FEAT_COLL>(h->P.T);
@@ -371,6 +385,18 @@ cudaError_t prepare_rollout(mppi_s* h) {
 
 cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float* S, float* noise) {
   const int grid = (h->P.K + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
+  if (h->feat == FEAT_COLL && h->variant == 3) {
+    // the collision cost on two more warps of the warp-specialised kernel
+    const int wgrid = (h->P.K + WS_B - 1) / WS_B;
+    const size_t smem = ws_smem_bytes(true);
+    if (noise)
+      rollout_kernel_ws<true, true><<<wgrid, ws_threads(true), smem, h->stream>>>(
+          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, h->d_obs);
+    else
+      rollout_kernel_ws<false, true><<<wgrid, ws_threads(true), smem, h->stream>>>(
+          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, h->d_obs);
+    return cudaGetLastError();
+  }
   // the optional cost terms run in the rolled kernel only
   switch (h->feat) {
     case FEAT_FEST: return launch_rolled<FEAT_FEST>(h, grid, in, plan, S, noise);
@@ -538,19 +564,19 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
     return fail(nullptr, MPPI_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   }
   h->feat = (h->P.cost.fest ? FEAT_FEST : 0) | (h->P.cost.coll ? FEAT_COLL : 0);
-  if (h->feat && (cfg->variant == 1 || cfg->variant == 3)) {
+  if ((h->feat && cfg->variant == 1) || ((h->feat & FEAT_FEST) && cfg->variant == 3)) {
     delete h;
     return fail(nullptr, MPPI_ERR_INVALID_ARG,
-                "the wrench-estimate and collision costs need the rolled rollout kernel "
-                "(variant 0 or 2)");
+                "the wrench-estimate cost needs the rolled rollout kernel (variant 0 or 2), "
+                "the collision cost the rolled or warp-specialised one (variant 0, 2 or 3)");
   }
-  if (!h->feat && cfg->variant == 0) {
+  if ((h->feat == 0 || h->feat == FEAT_COLL) && cfg->variant == 0) {
     // the occupancy query needs the ws kernel's shared-memory opt-in first
     h->variant = 3;
     if (prepare_rollout(h) != cudaSuccess) cudaGetLastError();
-    h->variant = default_variant(cfg->K);
+    h->variant = default_variant(cfg->K, h->feat == FEAT_COLL);
   } else {
-    h->variant = h->feat ? 2 : cfg->variant;
+    h->variant = (h->feat & FEAT_FEST) ? 2 : cfg->variant;
   }
   const int T = cfg->T, K = cfg->K;
   auto bail = [&](cudaError_t e, const char* what) {

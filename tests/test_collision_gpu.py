@@ -68,18 +68,22 @@ def _near_threshold(c, plan, noise_k):
     return False
 
 
+# variant 0 runs the collision cost on the warp-specialised kernel's two
+# extra warps at these sizes, variant 2 on the rolled kernel
+@pytest.mark.parametrize("variant", [0, 2])
 @pytest.mark.parametrize("seed", range(4))
-def test_hinge_costs_match_oracle(seed):
+def test_hinge_costs_match_oracle(seed, variant):
     c = _case(seed, 2)
-    g, o = _run(c)
+    g, o = _run(c, variant=variant)
     _assert_costs(g["S"], o["S"])
 
 
+@pytest.mark.parametrize("variant", [0, 2])
 @pytest.mark.parametrize("seed", range(4))
-def test_indicator_costs_match_oracle(seed):
+def test_indicator_costs_match_oracle(seed, variant):
     w = 10.0
     c = _case(seed, 1, w=w)
-    g, o = _run(c)
+    g, o = _run(c, variant=variant)
     # the workload exercises the indicator: it changes the cost of every sample
     o0 = oracle_step(make_case(seed))
     assert np.all(o["S"] - o0["S"] >= w)
@@ -156,6 +160,7 @@ def test_collision_full_size_sampled():
     # K = 16384, T = 18 in the benchmark's launch shape: sampled samples one by one
     c = _case(5, 2, K=16384)
     with gpu_controller(c) as g:
+        assert g.variant() == 3
         g.step(c["q"], c["qd"], c["goal"], c["plane"])
         S = g.costs()
     plan = np.zeros((c["T"], 7))

@@ -480,6 +480,10 @@ def test_default_kernel_choice():
             assert g.variant() == want, K
     with gpu_controller(make_case(0, cost=synth.cost_force_estimate())) as g:
         assert g.variant() == 2
+    with gpu_controller(make_case(0, cost=synth.cost_collision(2))) as g:
+        assert g.variant() == 3
+    with gpu_controller(make_case(0, cost=synth.cost_collision(2), K=65536)) as g:
+        assert g.variant() == 2
     for v in (1, 2, 3):
         with gpu_controller(make_case(0), variant=v) as g:
             assert g.variant() == v

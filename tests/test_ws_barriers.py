@@ -11,7 +11,9 @@ at s = T it waits for the last link only.  Warp 2 waits for the odd links
 and for the last link (it forms the end-effector state for the dynamics),
 then for the forces, and arrives with its rows of M and with the step's
 input; after the last state warp 2 hands its partial cost to warp 1 (one
-more barrier).  The model runs the three programs under named-barrier semantics (a
+more barrier).  With the collision cost two more warps wait for the forces,
+arrive once they have copied the link points, wait for the last state's last
+link and hand over their partial costs.  The model runs the programs under named-barrier semantics (a
 phase completes when `count` threads have arrived or waited) in random
 interleavings and checks that every run ends with all barriers complete,
 that no phase mixes operations of two different states, and that no wait is
@@ -27,8 +29,15 @@ BAR_LINK0, BAR_FORCES, BAR_MROWS, BAR_STEP, BAR_DONE = 1, 8, 9, 10, 11
 B = 32
 
 
+COLL = False  # the collision-cost kernel: two more warps (see below)
+
+
 def link_count(i, last):
-    return 2 * B if last else (3 * B if i == NJ - 1 else 2 * B)
+    return (4 if COLL else 2) * B if last else (3 * B if i == NJ - 1 else 2 * B)
+
+
+def na():
+    return (5 if COLL else 3) * B
 
 
 def warp0(T):
@@ -39,9 +48,9 @@ def warp0(T):
                 yield ("arrive", BAR_LINK0 + i, link_count(i, last), s)
         if last:
             return
-        yield ("sync", BAR_FORCES, 3 * B, s)
+        yield ("sync", BAR_FORCES, na(), s)
         yield ("sync", BAR_MROWS, 3 * B, s)
-        yield ("sync", BAR_STEP, 3 * B, s)
+        yield ("sync", BAR_STEP, na(), s)
 
 
 def warp1(T):
@@ -49,12 +58,12 @@ def warp1(T):
         if s < T:
             for i in range(0, NJ, 2):
                 yield ("sync", BAR_LINK0 + i, link_count(i, False), s)
-            yield ("sync", BAR_FORCES, 3 * B, s)
+            yield ("sync", BAR_FORCES, na(), s)
             yield ("arrive", BAR_MROWS, 3 * B, s)
-            yield ("arrive", BAR_STEP, 3 * B, s)
+            yield ("arrive", BAR_STEP, na(), s)
         else:
             yield ("sync", BAR_LINK0 + NJ - 1, link_count(NJ - 1, True), s)
-    yield ("sync", BAR_DONE, 2 * B, T)
+    yield ("sync", BAR_DONE, (4 if COLL else 2) * B, T)
 
 
 def warp2(T):
@@ -62,20 +71,33 @@ def warp2(T):
         for i in range(1, NJ, 2):
             yield ("sync", BAR_LINK0 + i, link_count(i, False), s)
         yield ("sync", BAR_LINK0 + NJ - 1, link_count(NJ - 1, False), s)
-        yield ("sync", BAR_FORCES, 3 * B, s)
+        yield ("sync", BAR_FORCES, na(), s)
         yield ("arrive", BAR_MROWS, 3 * B, s)
-        yield ("arrive", BAR_STEP, 3 * B, s)
-    yield ("arrive", BAR_DONE, 2 * B, T)
+        yield ("arrive", BAR_STEP, na(), s)
+    yield ("arrive", BAR_DONE, (4 if COLL else 2) * B, T)
+
+
+def collision_warp(T):
+    for s in range(T + 1):
+        if s < T:
+            yield ("sync", BAR_FORCES, na(), s)
+            yield ("arrive", BAR_STEP, na(), s)
+        else:
+            yield ("sync", BAR_LINK0 + NJ - 1, link_count(NJ - 1, True), s)
+    yield ("arrive", BAR_DONE, 4 * B, T)
 
 
 def run(T, seed):
     rng = random.Random(seed)
     progs = [warp0(T), warp1(T), warp2(T)]
+    if COLL:
+        progs += [collision_warp(T), collision_warp(T)]
+    nw = len(progs)
     pend = [next(p, None) for p in progs]
-    waiting = [False] * 3
+    waiting = [False] * nw
     bars = {}
     while any(p is not None for p in pend):
-        runnable = [w for w in range(3) if pend[w] is not None and not waiting[w]]
+        runnable = [w for w in range(nw) if pend[w] is not None and not waiting[w]]
         if not runnable:
             return "deadlock"
         w = rng.choice(runnable)
@@ -103,10 +125,16 @@ def run(T, seed):
     return "ok" if not bars else f"incomplete barriers {sorted(bars)}"
 
 
+@pytest.mark.parametrize("coll", [False, True])
 @pytest.mark.parametrize("T", [1, 2, 3, 18, 64])
-def test_protocol_completes_in_every_interleaving_tried(T):
-    for seed in range(200):
-        assert run(T, seed) == "ok", (T, seed)
+def test_protocol_completes_in_every_interleaving_tried(T, coll):
+    global COLL
+    COLL = coll
+    try:
+        for seed in range(200):
+            assert run(T, seed) == "ok", (T, seed, coll)
+    finally:
+        COLL = False
 
 
 def test_model_detects_a_broken_protocol():
@@ -119,10 +147,10 @@ def test_model_detects_a_broken_protocol():
             for i in range(3, NJ, 2):
                 yield ("sync", BAR_LINK0 + i, link_count(i, False), s)
             yield ("sync", BAR_LINK0 + NJ - 1, link_count(NJ - 1, False), s)
-            yield ("sync", BAR_FORCES, 3 * B, s)
+            yield ("sync", BAR_FORCES, na(), s)
             yield ("arrive", BAR_MROWS, 3 * B, s)
-            yield ("arrive", BAR_STEP, 3 * B, s)
-        yield ("arrive", BAR_DONE, 2 * B, T)
+            yield ("arrive", BAR_STEP, na(), s)
+        yield ("arrive", BAR_DONE, (4 if COLL else 2) * B, T)
 
     warp2 = bad
     try:
