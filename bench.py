@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20  # twice the 126 MB L2
 # by K*T, on rollout_kernel_rolled at K=16384, T=18 (bench.py's own
 # workloads, two launches each).  The same count serves every kernel of a
 # workload: it is the method's arithmetic (the warp-specialised kernel
-# repeats 0.3 % of it, 4824.6).
+# executes 4766 for contact and 6607 for collision: within 1 %).
 FLOP_PER_ROLLOUT_STEP = {"contact": 4808.1, "force_estimate": 6004.6, "collision": 6692.8}
 # DRAM read + write bytes of one rollout launch at K=16384, T=18 per (cost,
 # kernel) (ncu dram__bytes_{read,write}.sum, mean of two launches).  The
@@ -55,7 +55,8 @@ FLOP_PER_ROLLOUT_STEP = {"contact": 4808.1, "force_estimate": 6004.6, "collision
 # back inside the launch.
 ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel"): 115456,
                                     ("contact", "rollout_kernel_rolled"): 55680,
-                                    ("contact", "rollout_kernel_ws"): 57216,
+                                    ("contact", "rollout_kernel_ws"): 61696,
+                                    ("collision", "rollout_kernel_ws"): 133632,
                                     ("force_estimate", "rollout_kernel_rolled"): 66432,
                                     ("collision", "rollout_kernel_rolled"): 70400}
 COSTS = ("contact", "force_estimate", "collision")
