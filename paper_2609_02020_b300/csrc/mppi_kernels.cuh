@@ -25,6 +25,36 @@ __device__ __forceinline__ void allow_dependent_launch() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Ordered keys of finite floats: the keys compare as unsigned integers the
+// way the floats compare, so that atomicMin over keys gives the minimum cost.
+__device__ __forceinline__ unsigned float_key(float f) {
+  const unsigned b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+constexpr unsigned KEY_NONE = 0xffffffffu;  // above every finite float's key: no finite cost
+
+// One warp's share of the two totals that Eq. 4a needs before the weights:
+// the minimum finite cost (as a key, red[0]) and the number of non-finite
+// costs (red[1]).  Every lane of the warp calls it; lanes without a sample
+// pass live = false.  The update kernel then skips its pass over S.
+__device__ __forceinline__ void reduce_min_bad(unsigned* red, float s, bool live) {
+  const bool fin = live && isfinite(s);
+  unsigned key = fin ? float_key(s) : KEY_NONE;
+  unsigned bad = (live && !fin) ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    key = min(key, __shfl_xor_sync(0xffffffffu, key, o));
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (key != KEY_NONE) atomicMin(red, key);
+    if (bad) atomicAdd(red + 1, bad);
+  }
+}
+
 // Offsets in the per-handle output record (floats): tau0, status, stats.
 constexpr int OUT_TAU0 = 0;
 constexpr int OUT_STATUS = 7;   // written as an int: 0 ok, 1 no finite cost
@@ -128,7 +158,8 @@ __global__ void __launch_bounds__(ROLLOUT_BLOCK)
 rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
                const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
                float* __restrict__ S, float* __restrict__ noise,
-               const float* __restrict__ prop = nullptr, const int* __restrict__ ksplit_p = nullptr) {
+               const float* __restrict__ prop = nullptr, const int* __restrict__ ksplit_p = nullptr,
+               unsigned* __restrict__ red = nullptr) {
   __shared__ float s_plan[T_MAX * NJ];
   __shared__ float s_prop[T_MAX * NJ];
   __shared__ float s_in[IN_FLOATS];
@@ -140,8 +171,12 @@ rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
   if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
   __syncthreads();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  S[k] = rollout_sample<STORE_NOISE>(P, s_in, k < k_split ? s_plan : s_prop, *iter_p, k, noise);
+  float sk = 0.f;
+  if (k < K) {
+    sk = rollout_sample<STORE_NOISE>(P, s_in, k < k_split ? s_plan : s_prop, *iter_p, k, noise);
+    S[k] = sk;
+  }
+  if (red) reduce_min_bad(red, sk, k < K);  // one warp per block
   allow_dependent_launch();
 }
 
@@ -567,7 +602,7 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
                       float* __restrict__ S, float* __restrict__ noise,
                       const float* __restrict__ prop = nullptr,
                       const int* __restrict__ ksplit_p = nullptr,
-                      const ObsK* __restrict__ obs = nullptr) {
+                      const ObsK* __restrict__ obs = nullptr, unsigned* __restrict__ red = nullptr) {
   constexpr bool COLL = (FEAT & FEAT_COLL) != 0;
   extern __shared__ float dsm[];
   const int T = P.T, K = P.K;
@@ -603,10 +638,14 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
   }
   __syncthreads();
   const int k = blockIdx.x * B + threadIdx.x;
-  if (k >= K) return;
-  S[k] = rollout_sample_rolled<STORE_NOISE, B, FEAT>(P, s_in, k < k_split ? s_plan : s_prop,
+  float sk = 0.f;
+  if (k < K) {
+    sk = rollout_sample_rolled<STORE_NOISE, B, FEAT>(P, s_in, k < k_split ? s_plan : s_prop,
                                                      *iter_p, k, noise, s_work, threadIdx.x,
                                                      s_obs, n_obs);
+    S[k] = sk;
+  }
+  if (red) reduce_min_bad(red, sk, k < K);  // B = 32: one warp per block
   allow_dependent_launch();
 }
 
@@ -1157,7 +1196,7 @@ rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
                   float* __restrict__ S, float* __restrict__ noise,
                   const float* __restrict__ prop = nullptr,
                   const int* __restrict__ ksplit_p = nullptr,
-                  const ObsK* __restrict__ obs = nullptr) {
+                  const ObsK* __restrict__ obs = nullptr, unsigned* __restrict__ red = nullptr) {
   extern __shared__ float4 dsm4[];
   float* dsm = reinterpret_cast<float*>(dsm4);
   const int K = P.K;
@@ -1197,6 +1236,7 @@ rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
   } else if (warp == 1) {
     const float Sk = ws_costs<COLL>(P, s_in, m, lane);
     if (live) S[k] = Sk;
+    if (red) reduce_min_bad(red, Sk, live);
   } else if (warp == 2) {
     ws_noise<STORE_NOISE, COLL>(P, s_in, k < k_split ? plan : prop, *iter_p, k, live, noise, m,
                                 lane);
@@ -1302,9 +1342,11 @@ __device__ __forceinline__ double acc_exp(double x) { return exp(x); }
 // Costs that are not finite get weight 0; if none is finite the plan is kept
 // (u* = u, next plan = u) and status 1 is reported.  out (may be null):
 // tau0, status, stats and a copy of the shifted plan (OUT_* offsets).
-// Each block walks K twice (min, then weights and the weighted noise row);
-// when S and the row are 16-byte aligned it reads float4 and keeps four
-// independent accumulators so that the L2 loads overlap.
+// Each block walks K for the weights and the weighted noise row; when S and
+// the row are 16-byte aligned it reads float4 and keeps four independent
+// accumulators so that the L2 loads overlap.  The minimum cost and the count
+// of non-finite costs come from the rollouts (red, see reduce_min_bad) in a
+// step, or from a first walk over K when the caller supplies S (red null).
 constexpr int UPDATE_THREADS = 512;
 
 template <typename Acc>
@@ -1338,7 +1380,8 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
                                                           const float* __restrict__ S,
                                                           const float* __restrict__ nrow,
                                                           float u, bool count_bad, float p = 0.f,
-                                                          int k_split = 0x7fffffff) {
+                                                          int k_split = 0x7fffffff,
+                                                          const unsigned* red = nullptr) {
   __shared__ float sm_f[32];
   __shared__ Acc sm_a[3 * 32];
   const bool vec = (K % 4 == 0) && ((reinterpret_cast<uintptr_t>(S) & 15) == 0) &&
@@ -1346,7 +1389,12 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
   const int K4 = vec ? K / 4 : 0;
   float m = INFINITY;
   int bad = 0;
-  {
+  if (red) {
+    // minimum and non-finite count from the rollouts (totals, not shares)
+    const unsigned key = __ldcg(red);
+    m = key == KEY_NONE ? INFINITY : key_float(key);
+    bad = static_cast<int>(__ldcg(red + 1));
+  } else {
     const float4* S4 = reinterpret_cast<const float4*>(S);
 #pragma unroll 4
     for (int i = threadIdx.x; i < K4; i += UPDATE_THREADS) {
@@ -1364,7 +1412,7 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
       else ++bad;
     }
   }
-  m = block_min<UPDATE_THREADS>(m, sm_f);
+  if (!red) m = block_min<UPDATE_THREADS>(m, sm_f);
   const bool ok = isfinite(m);
   Acc z = Acc(0), z2 = Acc(0), nacc = Acc(0), zb = Acc(0);
   if (ok) {
@@ -1397,7 +1445,9 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
     block_sum3<UPDATE_THREADS>(zbs, d1, d2, sm_a);
   }
   Acc nbad = Acc(0);
-  if (count_bad) {
+  if (count_bad && red) {
+    nbad = static_cast<Acc>(bad);
+  } else if (count_bad) {
     nbad = static_cast<Acc>(bad);
     d1 = d2 = Acc(0);
     __syncthreads();
@@ -1429,7 +1479,7 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
               float* __restrict__ ustar, float* __restrict__ plan_next, float* __restrict__ out,
               unsigned long long* __restrict__ iter_p, const float* __restrict__ prop = nullptr,
               const int* __restrict__ ksplit_p = nullptr, float* __restrict__ tau_dst = nullptr,
-              float* __restrict__ plan_dst = nullptr) {
+              float* __restrict__ plan_dst = nullptr, unsigned* __restrict__ red = nullptr) {
   // launched as a programmatic dependent of the rollout kernel: wait here
   // until the rollouts' results are visible (a no-op otherwise)
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -1437,8 +1487,17 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
   const float* nrow = noise + static_cast<size_t>(e) * K;
   const int k_split = ksplit_p ? *ksplit_p : K;
   const EntryResult<Acc> r =
-      update_entry<Acc>(K, lambda, S, nrow, plan[e], e == 0, k_split < K ? prop[e] : 0.f, k_split);
+      update_entry<Acc>(K, lambda, S, nrow, plan[e], e == 0, k_split < K ? prop[e] : 0.f, k_split,
+                        red);
   if (threadIdx.x != 0) return;
+  // red (from the rollouts): the last block to finish resets it for the next
+  // update; all threads of this block read it before update_entry's barriers
+  if (red) __threadfence();
+  if (red && atomicAdd(red + 2, 1u) == gridDim.x - 1) {
+    red[0] = KEY_NONE;
+    red[1] = 0u;
+    red[2] = 0u;
+  }
   const int t = e / NJ;
   const float us = r.us;
   if (r.ok) {

@@ -69,6 +69,7 @@ struct mppi_s {
   float* d_prop = nullptr;                // second proposal plan [T][7]
   int* d_ctl = nullptr;                   // {k_split of the next update, K}
   ObsK* d_obs = nullptr;                  // obstacle capsules of Eq. 15
+  unsigned* d_red = nullptr;              // {min-cost key, non-finite count, done blocks}
   int feat = 0;                           // FEAT_* cost terms of the rollouts
   unsigned long long* d_iter = nullptr;
   // pinned host staging
@@ -329,14 +330,14 @@ int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, Pr
 
 template <int FEAT>
 cudaError_t launch_rolled(mppi_s* h, int grid, const float* in, const float* plan, float* S,
-                          float* noise) {
+                          float* noise, unsigned* red) {
   const size_t smem = rolled_smem_bytes(h->P.T, ROLLOUT_BLOCK, FEAT);
   if (noise)
     rollout_kernel_rolled<true, ROLLOUT_BLOCK, FEAT><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
-        h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, h->d_obs);
+        h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, h->d_obs, red);
   else
     rollout_kernel_rolled<false, ROLLOUT_BLOCK, FEAT><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
-        h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, h->d_obs);
+        h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, h->d_obs, red);
   return cudaGetLastError();
 }
 
@@ -383,7 +384,10 @@ cudaError_t prepare_rollout(mppi_s* h) {
   return cudaSuccess;
 }
 
-cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float* S, float* noise) {
+// red non-null: the rollouts also leave the minimum cost and the number of
+// non-finite costs there for an update kernel launched with the same red
+cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float* S, float* noise,
+                           unsigned* red = nullptr) {
   const int grid = (h->P.K + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
   if (h->feat == FEAT_COLL && h->variant == 3) {
     // the collision cost on two more warps of the warp-specialised kernel
@@ -391,46 +395,49 @@ cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float*
     const size_t smem = ws_smem_bytes(true);
     if (noise)
       rollout_kernel_ws<true, true><<<wgrid, ws_threads(true), smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, h->d_obs);
+          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, h->d_obs, red);
     else
       rollout_kernel_ws<false, true><<<wgrid, ws_threads(true), smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, h->d_obs);
+          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, h->d_obs, red);
     return cudaGetLastError();
   }
   // the optional cost terms run in the rolled kernel only
   switch (h->feat) {
-    case FEAT_FEST: return launch_rolled<FEAT_FEST>(h, grid, in, plan, S, noise);
-    case FEAT_COLL: return launch_rolled<FEAT_COLL>(h, grid, in, plan, S, noise);
+    case FEAT_FEST: return launch_rolled<FEAT_FEST>(h, grid, in, plan, S, noise, red);
+    case FEAT_COLL: return launch_rolled<FEAT_COLL>(h, grid, in, plan, S, noise, red);
     case FEAT_FEST | FEAT_COLL:
-      return launch_rolled<FEAT_FEST | FEAT_COLL>(h, grid, in, plan, S, noise);
+      return launch_rolled<FEAT_FEST | FEAT_COLL>(h, grid, in, plan, S, noise, red);
     default: break;
   }
-  if (h->variant == 2) return launch_rolled<0>(h, grid, in, plan, S, noise);
+  if (h->variant == 2) return launch_rolled<0>(h, grid, in, plan, S, noise, red);
   if (h->variant == 3) {
     const int wgrid = (h->P.K + WS_B - 1) / WS_B;
     const size_t smem = ws_smem_bytes();
     if (noise)
       rollout_kernel_ws<true><<<wgrid, WS_THREADS, smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl);
+          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, nullptr, red);
     else
       rollout_kernel_ws<false><<<wgrid, WS_THREADS, smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl);
+          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, nullptr, red);
     return cudaGetLastError();
   }
   if (noise)
     rollout_kernel<true><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S, noise,
-                                                               h->d_prop, h->d_ctl);
+                                                               h->d_prop, h->d_ctl, red);
   else
     rollout_kernel<false><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S,
-                                                                nullptr, h->d_prop, h->d_ctl);
+                                                                nullptr, h->d_prop, h->d_ctl, red);
   return cudaGetLastError();
 }
 
-// prop / ksplit null: plain Eq. 4 (every sample around plan)
+// prop / ksplit null: plain Eq. 4 (every sample around plan).  red non-null:
+// the minimum and the non-finite count come from the rollouts that wrote S
+// (launch_rollout with the same red), and the update resets red afterwards.
 cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const float* plan,
                           float* ustar, float* plan_next, float* out, unsigned long long* iter,
                           const float* prop = nullptr, const int* ksplit = nullptr,
-                          float* tau_dst = nullptr, float* plan_dst = nullptr) {
+                          float* tau_dst = nullptr, float* plan_dst = nullptr,
+                          unsigned* red = nullptr) {
   // programmatic dependent launch: the update kernel's blocks may start as
   // the rollout kernel's retire and wait (griddepcontrol.wait) for its
   // results, which hides the launch gap between the two kernels
@@ -448,9 +455,16 @@ cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const f
   const float lambda = h->P.lambda;
   if (h->reduce_fp64)
     return cudaLaunchKernelEx(&lc, update_kernel<double>, K, T, lambda, S, noise, plan, ustar,
-                              plan_next, out, iter, prop, ksplit, tau_dst, plan_dst);
+                              plan_next, out, iter, prop, ksplit, tau_dst, plan_dst, red);
   return cudaLaunchKernelEx(&lc, update_kernel<float>, K, T, lambda, S, noise, plan, ustar,
-                            plan_next, out, iter, prop, ksplit, tau_dst, plan_dst);
+                            plan_next, out, iter, prop, ksplit, tau_dst, plan_dst, red);
+}
+
+// red back to {no finite cost yet, no non-finite cost, no block done}
+cudaError_t reset_red(mppi_s* h) {
+  cudaError_t e = cudaMemsetAsync(h->d_red, 0xff, sizeof(unsigned), h->stream);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(h->d_red + 1, 0, 2 * sizeof(unsigned), h->stream);
 }
 
 // the whole update on device buffers: rollouts from the inputs at `in`, then
@@ -458,11 +472,14 @@ cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const f
 // second proposal set for this update is consumed (k_split := K)
 cudaError_t enqueue_update(mppi_s* h, int cur, const float* in = nullptr, float* tau_dst = nullptr,
                            float* plan_dst = nullptr) {
-  cudaError_t e = launch_rollout(h, in ? in : h->d_in, h->d_plan[cur], h->d_S, h->d_noise);
+  cudaError_t e = launch_rollout(h, in ? in : h->d_in, h->d_plan[cur], h->d_S, h->d_noise, h->d_red);
   if (e != cudaSuccess) return e;
   e = launch_update(h, h->d_S, h->d_noise, h->d_plan[cur], h->d_ustar, h->d_plan[cur ^ 1],
-                    h->d_out, h->d_iter, h->d_prop, h->d_ctl, tau_dst, plan_dst);
-  if (e != cudaSuccess) return e;
+                    h->d_out, h->d_iter, h->d_prop, h->d_ctl, tau_dst, plan_dst, h->d_red);
+  if (e != cudaSuccess) {
+    reset_red(h);  // the rollouts' totals are not consumed
+    return e;
+  }
   return cudaMemcpyAsync(h->d_ctl, h->d_ctl + 1, sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
 }
 
@@ -607,6 +624,8 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
   if ((e = cudaMalloc(&h->d_prop, plan_b)) != cudaSuccess) return bail(e, "cudaMalloc prop");
   if ((e = cudaMalloc(&h->d_ctl, 2 * sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc ctl");
   if ((e = cudaMalloc(&h->d_obs, sizeof(ObsK))) != cudaSuccess) return bail(e, "cudaMalloc obs");
+  if ((e = cudaMalloc(&h->d_red, 4 * sizeof(unsigned))) != cudaSuccess) return bail(e, "cudaMalloc red");
+  if ((e = reset_red(h)) != cudaSuccess) return bail(e, "reset red");
   {
     ObsK ob;
     fill_obs(cost->n_obstacles, &cost->obstacles[0][0], &ob);
@@ -659,6 +678,7 @@ int mppi_destroy(mppi_t h) {
   cudaFree(h->d_prop);
   cudaFree(h->d_ctl);
   cudaFree(h->d_obs);
+  cudaFree(h->d_red);
   cudaFree(h->d_out);
   cudaFree(h->d_iter);
   if (h->h_in) cudaFreeHost(h->h_in);
@@ -965,11 +985,13 @@ int mppi_time_kernels(mppi_t h, const float* d_in, int iters, float* ms_rollout,
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < iters && e == cudaSuccess; ++i) {
     e = cudaEventRecord(ev[0], h->stream);
-    if (e == cudaSuccess) e = launch_rollout(h, d_in, h->d_plan[h->cur], h->d_S, h->d_noise);
+    if (e == cudaSuccess)
+      e = launch_rollout(h, d_in, h->d_plan[h->cur], h->d_S, h->d_noise, h->d_red);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
     if (e == cudaSuccess)
       e = launch_update(h, h->d_S, h->d_noise, h->d_plan[h->cur], h->d_scratch_plan,
-                        h->d_scratch_plan + plan_f, nullptr, nullptr, h->d_prop, h->d_ctl);
+                        h->d_scratch_plan + plan_f, nullptr, nullptr, h->d_prop, h->d_ctl,
+                        nullptr, nullptr, h->d_red);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
     float a = 0.f, b = 0.f;
@@ -979,7 +1001,10 @@ int mppi_time_kernels(mppi_t h, const float* d_in, int iters, float* ms_rollout,
     tu += b;
   }
   for (auto& x : ev) cudaEventDestroy(x);
-  if (e != cudaSuccess) return fail(h, MPPI_ERR_CUDA, std::string("time_kernels: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    reset_red(h);  // a rollout's totals may be left unconsumed
+    return fail(h, MPPI_ERR_CUDA, std::string("time_kernels: ") + cudaGetErrorString(e));
+  }
   *ms_rollout = tr / iters;
   *ms_update = tu / iters;
   return MPPI_OK;

@@ -168,6 +168,27 @@ def test_update_nonfinite_costs():
         assert np.array_equal(dx.cpu().numpy(), plan)
 
 
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_rollout_min_matches_two_pass_update(variant):
+    # in a step the rollouts hand the update the minimum cost and the
+    # non-finite count; the update on caller buffers finds both in a pass of
+    # its own.  Both must give the same m and bit-identical plans, on every
+    # one of consecutive steps (the step's totals are reset after each use).
+    torch = torch_mod()
+    c = make_case(3, cost=parity_cost(), K=1000, T=6)
+    with gpu_controller(c, variant=variant) as g:
+        for _ in range(3):
+            plan = g.get_plan()
+            g.step(c["q"], c["qd"], c["goal"], c["plane"])
+            S, n, st = g.costs(), g.noise(), g.stats()
+            assert st[0] == S.min() and st[3] == 0
+            dS, dn, dp = (torch.tensor(x, device="cuda") for x in (S, n, plan))
+            du, dx = torch.zeros_like(dp), torch.zeros_like(dp)
+            g.update_device(dS, dn, dp, du, dx)
+            torch.cuda.synchronize()
+            assert np.array_equal(du.cpu().numpy(), g.updated_plan())
+
+
 def test_step_with_no_finite_cost_keeps_plan():
     c = make_case(0, K=64, T=4)
     with gpu_controller(c) as g:
