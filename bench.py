@@ -53,12 +53,12 @@ FLOP_PER_ROLLOUT_STEP = {"contact": 4808.1, "force_estimate": 6004.6, "collision
 # kernel) (ncu dram__bytes_{read,write}.sum, mean of two launches).  The
 # 8.3 MB of stored noise stays in L2 for update_kernel and is not written
 # back inside the launch.
-ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel"): 115456,
-                                    ("contact", "rollout_kernel_rolled"): 55680,
-                                    ("contact", "rollout_kernel_ws"): 61696,
-                                    ("collision", "rollout_kernel_ws"): 133632,
+ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel"): 113408,
+                                    ("contact", "rollout_kernel_rolled"): 55552,
+                                    ("contact", "rollout_kernel_ws"): 64384,
+                                    ("collision", "rollout_kernel_ws"): 134144,
                                     ("force_estimate", "rollout_kernel_rolled"): 66432,
-                                    ("collision", "rollout_kernel_rolled"): 70400}
+                                    ("collision", "rollout_kernel_rolled"): 70656}
 COSTS = ("contact", "force_estimate", "collision")
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
@@ -303,8 +303,9 @@ def run_ours(args, rank, world):
     pose = ctl.ee_pose(q)
     if args.cost == "collision":
         ctl.set_obstacles(obstacles(rank, arm, pose[:3]))
-    # the optional cost terms run in the rolled kernel; otherwise variant 0
-    # picks it for K <= 32768
+    # variant 0 picks the warp-specialised kernel (with the collision cost on
+    # its two extra warps) while its blocks fit in one wave, the rolled kernel
+    # for the wrench-estimate cost, the register kernel for larger K
     kname = {1: "rollout_kernel", 2: "rollout_kernel_rolled",
              3: "rollout_kernel_ws"}[ctl.variant()]
     plane = synth.plane_through(float(pose[2]))
