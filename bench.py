@@ -237,10 +237,24 @@ def cpu_baseline(K: int, T: int, budget_s: float = 10.0, cost_name: str = "conta
                          plane, plan, nthreads=nth)
         reps += 1
     dt = time.perf_counter() - t0
+    # the oracle's other modes: one thread at this K (one update), and one
+    # thread and all threads at K = 256 (about two seconds each)
+    modes = []
+    for Km, thr, budget in ((K, 1, 0.0), (256, 1, 2.0), (256, nth, 2.0)):
+        rbm, ocm, qm, qdm, gm, pm = oracle_problem(Km, T, cost_name)
+        n = 0
+        t1 = time.perf_counter()
+        while n == 0 or time.perf_counter() - t1 < budget:
+            oracle.mppi_step(rbm, ocm, DT, T, Km, LAMBDA, np.full(7, SIGMA), SEED, n, qm, qdm, gm,
+                             pm, plan, nthreads=thr)
+            n += 1
+        d = time.perf_counter() - t1
+        modes.append({"K": Km, "threads": thr, "value": Km * T * n / d, "updates": n,
+                      "seconds": d})
     return {"value": K * T * reps / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
             "sample": f"{reps} full FP64 updates at K={K}, T={T} (same arm and cost), "
                       f"OpenMP over samples on {nth} threads, {dt:.1f} s",
-            "seconds": dt}
+            "seconds": dt, "modes": modes}
 
 
 def run_reference(args, rank, world):
@@ -385,11 +399,15 @@ def run_ours(args, rank, world):
         achieved = flop * K * T / (ms_roll * 1e-3) / 1e12
         traffic = (ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH.get((args.cost, kname))
                    if (K, T) == (K_DEFAULT, T_DEFAULT) else None)
+        fma = mppi.measure_fp32_peak()  # outside the timed regions
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
                 "frac": achieved / peak_max, "traffic": traffic,
                 "kernel": kname, "kernel_ms": ms_roll,
                 "peak_note": "FP32 peak of 148 SMs x 128 lanes x 2 FLOP at the 2032 MHz "
-                             "maximum SM clock (derived; no measured FP32 peak)"}
+                             "maximum SM clock (derived; no measured FP32 peak is on file); "
+                             "peak_fma_measured: independent FMA chains on every SM of this "
+                             "GPU, median of five launches",
+                "peak_fma_measured": fma, "frac_of_fma_measured": achieved / fma}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -286,15 +286,24 @@ MPPI_API int mppi_force_estimate_device(mppi_t h, const float* d_q, const float*
                                         float* d_F);
 
 /* The rollout kernel the handle runs (1, 2 or 3 as in mppi_config.variant;
- * variant 0 resolves at creation: the warp-specialised kernel while its
- * blocks for K samples fit on the device at once, else the register kernel
- * - or the rolled kernel when the wrench-estimate or collision cost is on,
- * see mppi_cost). */
+ * variant 0 resolves at creation: with the wrench-estimate cost the rolled
+ * kernel; otherwise the warp-specialised kernel while its blocks for K
+ * samples fit on the device at once, else the register kernel, or the rolled
+ * kernel when the collision cost is on; see mppi_cost). */
 MPPI_API int mppi_get_variant(mppi_t h, int* variant);
 
 /* End-effector pose (p xyz, quaternion wxyz) at joint angles q, computed on
  * the device by the rollouts' own kinematics (host arrays). */
 MPPI_API int mppi_ee_pose(mppi_t h, const float q[7], float pose_out[7]);
+
+/* FP32 FMA throughput of the current device in TFLOP/s (2 FLOP per FFMA),
+ * measured by a kernel of independent FMA chains over every SM, timed with
+ * CUDA events on a stream of its own (median of five launches after one
+ * warm-up, about a millisecond each).  Measurement support for the roofline
+ * of the rollout kernels, whose bound is FP32 arithmetic; the paper has no
+ * counterpart.  Allocates and frees a small device buffer; returns
+ * MPPI_ERR_CUDA on a CUDA failure (message in mppi_last_error(NULL)). */
+MPPI_API int mppi_measure_fp32_peak(double* tflops);
 
 /* Device time of the two kernels of one update, averaged over `iters`
  * updates from the inputs at d_in (CUDA events on the handle's stream).  The

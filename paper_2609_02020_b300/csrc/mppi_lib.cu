@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 
 #include "mppi.h"
 #include "mppi_kernels.cuh"
@@ -555,9 +556,80 @@ int mppi_convert_params(const mppi_robot* rb, const mppi_cost* c, const mppi_con
 }
 
 // ---------------------------------------------------------------------------
+// FP32 FMA throughput probe (the roofline's peak for the rollout kernels)
+
+constexpr int PEAK_THREADS = 256;
+constexpr int PEAK_BLOCKS_PER_SM = 8;  // 2048 threads: a full SM
+constexpr int PEAK_CHAINS = 8;         // independent FMA chains per thread
+constexpr int PEAK_ITERS = 8192;       // a multiple of the unroll below
+
+// Every thread advances PEAK_CHAINS independent chains a <- a m + c; the
+// store is taken only if the sum equals `never` (it cannot: the chains stay
+// positive), which keeps the arithmetic live without memory traffic.
+__global__ void __launch_bounds__(PEAK_THREADS)
+fp32_peak_kernel(float* __restrict__ out, int iters, float never) {
+  float a[PEAK_CHAINS];
+#pragma unroll
+  for (int j = 0; j < PEAK_CHAINS; ++j) a[j] = 1.0f + 1e-3f * static_cast<float>(threadIdx.x + j);
+  const float m = 0.9999999f, c = 1e-7f;
+#pragma unroll 16
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < PEAK_CHAINS; ++j) a[j] = fmaf(a[j], m, c);
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int j = 0; j < PEAK_CHAINS; ++j) sum += a[j];
+  if (sum == never) out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 
 extern "C" {
+
+int mppi_measure_fp32_peak(double* tflops) {
+  if (!tflops) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null argument");
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess)
+    return fail(nullptr, MPPI_ERR_CUDA, std::string("fp32 peak: ") + cudaGetErrorString(e));
+  const int grid = sms * PEAK_BLOCKS_PER_SM;
+  float* out = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  float ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  e = cudaMalloc(&out, sizeof(float) * size_t(grid) * PEAK_THREADS);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  if (e == cudaSuccess) {
+    fp32_peak_kernel<<<grid, PEAK_THREADS, 0, st>>>(out, PEAK_ITERS, -1.0f);  // warm-up
+    e = cudaGetLastError();
+  }
+  for (int r = 0; r < 5 && e == cudaSuccess; ++r) {
+    e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) {
+      fp32_peak_kernel<<<grid, PEAK_THREADS, 0, st>>>(out, PEAK_ITERS, -1.0f);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[r], ev[0], ev[1]);
+  }
+  if (ev[0]) cudaEventDestroy(ev[0]);
+  if (ev[1]) cudaEventDestroy(ev[1]);
+  if (st) cudaStreamDestroy(st);
+  if (out) cudaFree(out);
+  if (e != cudaSuccess)
+    return fail(nullptr, MPPI_ERR_CUDA, std::string("fp32 peak: ") + cudaGetErrorString(e));
+  for (int i = 1; i < 5; ++i)  // insertion sort for the median
+    for (int j = i; j > 0 && ms[j] < ms[j - 1]; --j) std::swap(ms[j], ms[j - 1]);
+  const double flop = 2.0 * PEAK_CHAINS * double(PEAK_ITERS) * double(grid) * PEAK_THREADS;
+  *tflops = flop / (double(ms[2]) * 1e-3) / 1e12;
+  return MPPI_OK;
+}
 
 const char* mppi_version(void) { return MPPI_VERSION_STR; }
 

@@ -134,7 +134,7 @@ EXPORTS = [
     "mppi_simulate_device", "mppi_set_plan_device", "mppi_get_plan_device",
     "mppi_get_updated_plan_device", "mppi_set_proposal_device", "mppi_gravity_torque",
     "mppi_force_estimate_device", "mppi_set_obstacles", "mppi_set_obstacles_device",
-    "mppi_get_variant",
+    "mppi_get_variant", "mppi_measure_fp32_peak",
     # include/mppi_serve.h
     "mppi_pool_create", "mppi_pool_destroy", "mppi_pool_alloc", "mppi_pool_free",
     "mppi_pool_stats", "mppi_server_create", "mppi_server_destroy", "mppi_server_add_problem",
@@ -196,6 +196,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_force_estimate_device": ([H, vp, vp, C.c_int, vp], C.c_int),
         "mppi_set_obstacles": ([H, C.c_int, fp], C.c_int),
         "mppi_get_variant": ([H, C.POINTER(C.c_int)], C.c_int),
+        "mppi_measure_fp32_peak": ([C.POINTER(C.c_double)], C.c_int),
         "mppi_set_obstacles_device": ([H, C.c_int, vp], C.c_int),
         "mppi_pool_create": ([C.c_size_t, C.POINTER(C.c_void_p)], C.c_int),
         "mppi_pool_destroy": ([H], C.c_int),
@@ -544,6 +545,16 @@ def pack_inputs(q, qd, goal, plane=None) -> np.ndarray:
     """The 25-float input record (q, qd, goal, plane) of mppi_step_device."""
     pl = np.array([0.0, 0.0, 1.0, -1.0e9]) if plane is None else plane
     return np.concatenate([_f32(q, NJ), _f32(qd, NJ), _f32(goal, 7), _f32(pl, 4)]).astype(np.float32)
+
+
+def measure_fp32_peak() -> float:
+    """FP32 FMA throughput of the current CUDA device, TFLOP/s."""
+    L = load()
+    v = C.c_double()
+    rc = L.mppi_measure_fp32_peak(C.byref(v))
+    if rc != 0:
+        raise MPPIError(rc, L.mppi_last_error(None).decode())
+    return v.value
 
 
 def version() -> str:

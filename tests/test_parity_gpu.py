@@ -508,3 +508,13 @@ def test_default_kernel_choice():
     for v in (1, 2, 3):
         with gpu_controller(make_case(0), variant=v) as g:
             assert g.variant() == v
+
+
+def test_fp32_peak_probe():
+    # the FMA probe behind the roofline's measured FP32 peak: positive and at
+    # most the derived 128 lanes x 2 FLOP x SMs at the 2032 MHz maximum clock
+    torch = torch_mod()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    derived = sms * 128 * 2 * 2.032e9 / 1e12
+    v = mppi.measure_fp32_peak()
+    assert 0.3 * derived < v <= 1.02 * derived, (v, derived)
