@@ -5,7 +5,8 @@ and costs, then the Eq. 4 update and the shift) of a seeded 7-joint arm with
 plane contact, dt = 0.01 s.  Prints one JSON line on rank 0.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--cost contact|force_estimate|collision] [--mode update|serve|learned]
+                    [--cost contact|force_estimate|collision]
+                    [--mode update|serve|learned|sweep]
 
 `value` times the update on device-resident inputs with CUDA events on the
 library's stream, L2 flushed between steps; `e2e` times the public host call
@@ -82,10 +83,11 @@ def parse():
                     help="update mode: the plane-contact workload (default), or the same with "
                          "C_force on the wrench estimate of Eq. 13, or with the collision "
                          "indicator of Eq. 15 against 3 obstacles")
-    ap.add_argument("--mode", default="update", choices=["update", "serve", "learned"],
+    ap.add_argument("--mode", default="update", choices=["update", "serve", "learned", "sweep"],
                     help="update: the headline single-update benchmark; serve: batched "
                          "serving of 256 problems under Poisson load; learned: train the "
-                         "learned proposal and compare it with plain MPPI")
+                         "learned proposal and compare it with plain MPPI; sweep: the update "
+                         "over K x T with FP32 and FP64 reductions")
     ap.add_argument("--pairs", type=int, default=200_000, help="learned mode: training pairs")
     ap.add_argument("--train-steps", type=int, default=12_000, help="learned mode: Adam steps")
     ap.add_argument("--episodes", type=int, default=12, help="learned mode: eval episodes")
@@ -477,6 +479,71 @@ def run_serve(args, rank, world):
             "points": points}), flush=True)
 
 
+SWEEP_K = (1024, 4096, 16384, 65536)
+SWEEP_T = (18, 36, 50)
+
+
+def run_sweep(args, rank, world):
+    """The update of the contact workload over K x T, with the FP32 and the
+    FP64 reduction of Eq. 4: device time per update (CUDA events, L2 flushed
+    between updates), the kernel variant 0 chose and its kernel times."""
+    import torch
+    from paper_2609_02020_b300 import mppi, synth
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    arm, cost, q, qd, goal = workload(rank, "contact")
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    steps = max(args.steps, 1)
+    rows, spans = [], []
+    with ClockSampler(dev) as clk:
+        for T in SWEEP_T:
+            for K in SWEEP_K:
+                for fp64 in (False, True):
+                    ctl = mppi.MPPI(arm, cost, dt=DT, T=T, K=K, lam=LAMBDA, sigma=SIGMA,
+                                    seed=SEED + rank, reduce_fp64=fp64, stream=stream)
+                    pose = ctl.ee_pose(q)
+                    plane = synth.plane_through(float(pose[2]))
+                    d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, plane), device="cuda")
+                    d_tau = torch.zeros(7, device="cuda")
+                    d_plan = torch.zeros(T, 7, device="cuda")
+                    for _ in range(max(args.warmup, 3)):
+                        ctl.step_device(d_in, d_tau, d_plan)
+                    st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+                    en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+                    torch.cuda.synchronize()
+                    a = clk.mark()
+                    for i in range(steps):
+                        flush.zero_()
+                        st[i].record(stream)
+                        ctl.step_device(d_in, d_tau, d_plan)
+                        en[i].record(stream)
+                    torch.cuda.synchronize()
+                    spans.append((a, clk.mark()))
+                    if ctl.sync() != 0:
+                        raise RuntimeError(f"update failed at K={K} T={T}")
+                    ms = np.array([x.elapsed_time(y) for x, y in zip(st, en)])
+                    ms_roll, ms_upd = ctl.time_kernels(d_in, 20)
+                    rows.append({"K": K, "T": T, "reduce": "f64" if fp64 else "f32",
+                                 "variant": ctl.variant(), "ms_per_update": float(ms.mean()),
+                                 "p50_ms": float(np.percentile(ms, 50)),
+                                 "p99_ms": float(np.percentile(ms, 99)),
+                                 "rollout_steps_per_s": K * T / (float(ms.mean()) * 1e-3),
+                                 "rollout_ms": ms_roll, "update_ms": ms_upd})
+                    ctl.close()
+    clocks = clk.summary(spans)
+    if rank == 0:
+        print(json.dumps({
+            "mode": "sweep", "metric": "MPPI update time over K x T (contact workload)",
+            "unit": "ms", "n_gpus": world, "steps": steps, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"7-DoF seeded arm with plane contact, dt={DT} s, "
+                                   f"sigma={SIGMA} N m, lambda={LAMBDA}",
+                       "K": list(SWEEP_K), "T": list(SWEEP_T),
+                       "l2": "flushed between timed steps"},
+            "clocks": clocks, "points": rows}), flush=True)
+
+
 def run_learned(args, rank, world):
     """Learned proposal: pairs from plain MPPI at K=16384, training on the GPU
     with the library's BF16 tensor-core kernels, then closed-loop tracking
@@ -538,6 +605,8 @@ def main():
             run_serve(args, rank, world)
         elif args.mode == "learned":
             run_learned(args, rank, world)
+        elif args.mode == "sweep":
+            run_sweep(args, rank, world)
         else:
             run_ours(args, rank, world)
     finally:

@@ -157,7 +157,8 @@ typedef struct mppi_config {
   double lambda;    /* temperature, > 0                                      */
   double sigma[7];  /* noise standard deviation per joint [N m], >= 0        */
   uint64_t seed;    /* Philox key                                            */
-  int reduce_fp64;  /* 0: FP32 weight reduction; 1: FP64 accumulators       */
+  int reduce_fp64;  /* 0: FP32 weight reduction; 1: FP64 sums over K (the
+                     * weights themselves are FP32 in both modes)              */
   int use_graph;    /* 1: mppi_step replays a captured CUDA graph            */
   int variant;      /* rollout kernel: 0 default, 1 links unrolled in registers,
                        2 link loops rolled through shared memory, 3 three

@@ -1335,8 +1335,6 @@ __device__ __forceinline__ void block_sum3(V& a, V& b, V& c, V* sm) {
   }
 }
 
-__device__ __forceinline__ float acc_exp(float x) { return expf(x); }
-__device__ __forceinline__ double acc_exp(double x) { return exp(x); }
 
 // Eq. 4a-4b for plan entry e = blockIdx.x = t*7 + j, and the shift.
 // Costs that are not finite get weight 0; if none is finite the plan is kept
@@ -1349,11 +1347,15 @@ __device__ __forceinline__ double acc_exp(double x) { return exp(x); }
 // step, or from a first walk over K when the caller supplies S (red null).
 constexpr int UPDATE_THREADS = 512;
 
+// The weight exp(-(S_k - S_min) / lambda) is formed in FP32 for both
+// accumulator types: its rounding (a few 1e-7 relative) moves u* by about
+// 1e-7 |dtau|, far below what the FP32 sums over K lose, and an FP64
+// exponential per (entry, sample) would cost more than the whole update on
+// this GPU's FP64 rate.  Acc = double then makes only the sums FP64.
 template <typename Acc>
-__device__ __forceinline__ void weight_acc(float s, float n, float m, Acc inv_l, Acc& z, Acc& z2,
+__device__ __forceinline__ void weight_acc(float s, float n, float m, float inv_l, Acc& z, Acc& z2,
                                            Acc& nacc, Acc& zb, bool second) {
-  const Acc w = isfinite(s) ? acc_exp((static_cast<Acc>(m) - static_cast<Acc>(s)) * inv_l)
-                            : Acc(0);
+  const Acc w = static_cast<Acc>(isfinite(s) ? expf((m - s) * inv_l) : 0.f);
   z += w;
   z2 += w * w;
   nacc += w * static_cast<Acc>(n);
@@ -1416,7 +1418,7 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
   const bool ok = isfinite(m);
   Acc z = Acc(0), z2 = Acc(0), nacc = Acc(0), zb = Acc(0);
   if (ok) {
-    const Acc inv_l = Acc(1) / static_cast<Acc>(lambda);
+    const float inv_l = 1.0f / lambda;
     const float4* S4 = reinterpret_cast<const float4*>(S);
     const float4* N4 = reinterpret_cast<const float4*>(nrow);
     Acc za[4] = {Acc(0), Acc(0), Acc(0), Acc(0)}, z2a[4] = {Acc(0), Acc(0), Acc(0), Acc(0)},
@@ -1426,10 +1428,25 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
       const float4 sv = S4[i];
       const float4 nv = N4[i];
       const int k = 4 * i;
-      weight_acc(sv.x, nv.x, m, inv_l, za[0], z2a[0], na[0], zba[0], k >= k_split);
-      weight_acc(sv.y, nv.y, m, inv_l, za[1], z2a[1], na[1], zba[1], k + 1 >= k_split);
-      weight_acc(sv.z, nv.z, m, inv_l, za[2], z2a[2], na[2], zba[2], k + 2 >= k_split);
-      weight_acc(sv.w, nv.w, m, inv_l, za[3], z2a[3], na[3], zba[3], k + 3 >= k_split);
+      if constexpr (sizeof(Acc) == sizeof(double)) {
+        // FP64 sums of four-sample FP32 partials: one FP64 add per quantity
+        // and float4 instead of one FP64 multiply-add per sample (the FP32
+        // partial of four terms loses no more than the FP32 weights do)
+        float pz = 0.f, pz2 = 0.f, pn = 0.f, pb = 0.f;
+        weight_acc(sv.x, nv.x, m, inv_l, pz, pz2, pn, pb, k >= k_split);
+        weight_acc(sv.y, nv.y, m, inv_l, pz, pz2, pn, pb, k + 1 >= k_split);
+        weight_acc(sv.z, nv.z, m, inv_l, pz, pz2, pn, pb, k + 2 >= k_split);
+        weight_acc(sv.w, nv.w, m, inv_l, pz, pz2, pn, pb, k + 3 >= k_split);
+        za[0] += pz;
+        z2a[0] += pz2;
+        na[0] += pn;
+        zba[0] += pb;
+      } else {
+        weight_acc(sv.x, nv.x, m, inv_l, za[0], z2a[0], na[0], zba[0], k >= k_split);
+        weight_acc(sv.y, nv.y, m, inv_l, za[1], z2a[1], na[1], zba[1], k + 1 >= k_split);
+        weight_acc(sv.z, nv.z, m, inv_l, za[2], z2a[2], na[2], zba[2], k + 2 >= k_split);
+        weight_acc(sv.w, nv.w, m, inv_l, za[3], z2a[3], na[3], zba[3], k + 3 >= k_split);
+      }
     }
     for (int k = 4 * K4 + threadIdx.x; k < K; k += UPDATE_THREADS)
       weight_acc(S[k], nrow[k], m, inv_l, za[0], z2a[0], na[0], zba[0], k >= k_split);
