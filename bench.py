@@ -422,7 +422,9 @@ def run_ours(args, rank, world):
                     "d2h_bytes_per_step": (16 + T * 7) * 4,
                     "p50_ms": float(np.percentile(e2e_ms, 50)),
                     "p99_ms": float(np.percentile(e2e_ms, 99)),
-                    "api": "mppi_step (host buffers, CUDA graph replay)"},
+                    "api": "mppi_step (host buffers, CUDA graph replay: H2D copy of the "
+                           "inputs, two kernels, the update kernel writing tau0, status and "
+                           "plan into pinned host memory)"},
             "roofline": roof,
             "clocks": clocks,
             "gpu_launches": launches,

@@ -186,7 +186,9 @@ MPPI_API int mppi_destroy(mppi_t h);
 /* One MPPI update from host memory: copies (q, qd, goal, plane) to the
  * device, runs the rollouts and the update, and returns tau0 = u*_0 (7
  * floats) and, when plan_out is not NULL, the shifted plan [T][7] that the
- * next update samples around.  Blocks until the result is in host memory.
+ * next update samples around.  The update kernel writes its output record
+ * straight into the handle's pinned host buffer (no separate device-to-host
+ * copy).  Blocks until the result is in host memory.
  * Returns MPPI_ERR_NONFINITE (plan unchanged, iter unchanged) when no sample
  * has a finite cost. */
 MPPI_API int mppi_step(mppi_t h, const float q[7], const float qd[7], const float goal[7],

@@ -1495,8 +1495,9 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
               const float* __restrict__ noise, const float* __restrict__ plan,
               float* __restrict__ ustar, float* __restrict__ plan_next, float* __restrict__ out,
               unsigned long long* __restrict__ iter_p, const float* __restrict__ prop = nullptr,
-              const int* __restrict__ ksplit_p = nullptr, float* __restrict__ tau_dst = nullptr,
-              float* __restrict__ plan_dst = nullptr, unsigned* __restrict__ red = nullptr) {
+              const int* ksplit_p = nullptr, float* __restrict__ tau_dst = nullptr,
+              float* __restrict__ plan_dst = nullptr, unsigned* __restrict__ red = nullptr,
+              int* ctl_reset = nullptr) {
   // launched as a programmatic dependent of the rollout kernel: wait here
   // until the rollouts' results are visible (a no-op otherwise)
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -1508,12 +1509,15 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
                         red);
   if (threadIdx.x != 0) return;
   // red (from the rollouts): the last block to finish resets it for the next
-  // update; all threads of this block read it before update_entry's barriers
+  // update, and with ctl_reset (= ksplit_p's {k_split, K}) consumes a second
+  // proposal (k_split := K); all threads of this block read both before
+  // update_entry's barriers
   if (red) __threadfence();
   if (red && atomicAdd(red + 2, 1u) == gridDim.x - 1) {
     red[0] = KEY_NONE;
     red[1] = 0u;
     red[2] = 0u;
+    if (ctl_reset) ctl_reset[0] = ctl_reset[1];
   }
   const int t = e / NJ;
   const float us = r.us;

@@ -75,7 +75,9 @@ struct mppi_s {
   unsigned long long* d_iter = nullptr;
   // pinned host staging
   float* h_in = nullptr;
-  float* h_out = nullptr;
+  float* h_out = nullptr;                 // pinned, mapped: host steps write it directly
+  float* h_out_dev = nullptr;             // h_out as the device sees it
+  bool out_on_host = false;               // the last update's record is in h_out, not d_out
   int cur = 0;  // index of the current nominal plan
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   std::string err;
@@ -438,7 +440,7 @@ cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const f
                           float* ustar, float* plan_next, float* out, unsigned long long* iter,
                           const float* prop = nullptr, const int* ksplit = nullptr,
                           float* tau_dst = nullptr, float* plan_dst = nullptr,
-                          unsigned* red = nullptr) {
+                          unsigned* red = nullptr, int* ctl_reset = nullptr) {
   // programmatic dependent launch: the update kernel's blocks may start as
   // the rollout kernel's retire and wait (griddepcontrol.wait) for its
   // results, which hides the launch gap between the two kernels
@@ -456,9 +458,10 @@ cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const f
   const float lambda = h->P.lambda;
   if (h->reduce_fp64)
     return cudaLaunchKernelEx(&lc, update_kernel<double>, K, T, lambda, S, noise, plan, ustar,
-                              plan_next, out, iter, prop, ksplit, tau_dst, plan_dst, red);
+                              plan_next, out, iter, prop, ksplit, tau_dst, plan_dst, red,
+                              ctl_reset);
   return cudaLaunchKernelEx(&lc, update_kernel<float>, K, T, lambda, S, noise, plan, ustar,
-                            plan_next, out, iter, prop, ksplit, tau_dst, plan_dst, red);
+                            plan_next, out, iter, prop, ksplit, tau_dst, plan_dst, red, ctl_reset);
 }
 
 // red back to {no finite cost yet, no non-finite cost, no block done}
@@ -469,35 +472,37 @@ cudaError_t reset_red(mppi_s* h) {
 }
 
 // the whole update on device buffers: rollouts from the inputs at `in`, then
-// Eq. 4 into the other plan (and into tau_dst / plan_dst when given); a
-// second proposal set for this update is consumed (k_split := K)
+// Eq. 4 into the other plan (and into tau_dst / plan_dst when given) with
+// the output record at `out` (default d_out); the update's last block
+// consumes a second proposal set for this update (k_split := K)
 cudaError_t enqueue_update(mppi_s* h, int cur, const float* in = nullptr, float* tau_dst = nullptr,
-                           float* plan_dst = nullptr) {
+                           float* plan_dst = nullptr, float* out = nullptr) {
   cudaError_t e = launch_rollout(h, in ? in : h->d_in, h->d_plan[cur], h->d_S, h->d_noise, h->d_red);
   if (e != cudaSuccess) return e;
   e = launch_update(h, h->d_S, h->d_noise, h->d_plan[cur], h->d_ustar, h->d_plan[cur ^ 1],
-                    h->d_out, h->d_iter, h->d_prop, h->d_ctl, tau_dst, plan_dst, h->d_red);
+                    out ? out : h->d_out, h->d_iter, h->d_prop, h->d_ctl, tau_dst, plan_dst,
+                    h->d_red, h->d_ctl);
   if (e != cudaSuccess) {
     reset_red(h);  // the rollouts' totals are not consumed
     return e;
   }
-  return cudaMemcpyAsync(h->d_ctl, h->d_ctl + 1, sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
+  return cudaSuccess;
 }
 
 __global__ void set_int_kernel(int* dst, int v) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
 }
 
-size_t out_bytes(const mppi_s* h) { return sizeof(float) * (OUT_PLAN + h->P.T * NJ); }
 
 // host-buffer step: H2D inputs, update, D2H outputs (captured once per parity)
 cudaError_t enqueue_host_step(mppi_s* h, int cur) {
   cudaError_t e = cudaMemcpyAsync(h->d_in, h->h_in, sizeof(float) * IN_FLOATS,
                                   cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return e;
-  e = enqueue_update(h, cur);
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyAsync(h->h_out, h->d_out, out_bytes(h), cudaMemcpyDeviceToHost, h->stream);
+  // the update kernel writes the output record straight into pinned host
+  // memory (tau0, status, stats, shifted plan: 568 B at T = 18), so no
+  // device-to-host copy follows it
+  return enqueue_update(h, cur, nullptr, nullptr, nullptr, h->h_out_dev);
 }
 
 void destroy_graphs(mppi_s* h) {
@@ -717,8 +722,12 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
   if ((e = cudaMalloc(&h->d_iter, sizeof(unsigned long long))) != cudaSuccess)
     return bail(e, "cudaMalloc iter");
   if ((e = cudaMallocHost(&h->h_in, sizeof(float) * 32)) != cudaSuccess) return bail(e, "cudaMallocHost");
-  if ((e = cudaMallocHost(&h->h_out, sizeof(float) * h->out_floats)) != cudaSuccess)
-    return bail(e, "cudaMallocHost");
+  if ((e = cudaHostAlloc(&h->h_out, sizeof(float) * h->out_floats, cudaHostAllocMapped)) !=
+      cudaSuccess)
+    return bail(e, "cudaHostAlloc");
+  if ((e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->h_out_dev), h->h_out, 0)) !=
+      cudaSuccess)
+    return bail(e, "cudaHostGetDevicePointer");
   std::memset(h->h_in, 0, sizeof(float) * 32);
   std::memset(h->h_out, 0, sizeof(float) * h->out_floats);
   if ((e = cudaMemsetAsync(h->d_plan[0], 0, plan_b, h->stream)) != cudaSuccess) return bail(e, "memset");
@@ -795,6 +804,7 @@ int mppi_step(mppi_t h, const float q[7], const float qd[7], const float goal[7]
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   h->cur = cur ^ 1;  // the update wrote the next plan into the other buffer
+  h->out_on_host = true;
   rc = read_status(h);
   std::memcpy(tau0_out, h->h_out + OUT_TAU0, 7 * sizeof(float));
   if (plan_out) std::memcpy(plan_out, h->h_out + OUT_PLAN, sizeof(float) * h->P.T * NJ);
@@ -809,13 +819,15 @@ int mppi_step_device(mppi_t h, const float* d_in, float* d_tau0, float* d_plan) 
   const int cur = h->cur;
   CUDA_TRY(h, enqueue_update(h, cur, d_in, d_tau0, d_plan));
   h->cur = cur ^ 1;
+  h->out_on_host = false;
   return MPPI_OK;
 }
 
 int mppi_sync(mppi_t h) {
   if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
-  CUDA_TRY(h, cudaMemcpyAsync(h->h_out + OUT_STATUS, h->d_out + OUT_STATUS, 5 * sizeof(float),
-                              cudaMemcpyDeviceToHost, h->stream));
+  if (!h->out_on_host)
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_out + OUT_STATUS, h->d_out + OUT_STATUS, 5 * sizeof(float),
+                                cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return read_status(h);
 }
@@ -846,8 +858,14 @@ int mppi_get_updated_plan(mppi_t h, float* u_out) {
 int mppi_get_stats(mppi_t h, double stats[4]) {
   if (!h || !stats) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
   float tmp[4];
-  CUDA_TRY(h, cudaMemcpyAsync(tmp, h->d_out + OUT_STATS, sizeof tmp, cudaMemcpyDeviceToHost, h->stream));
-  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (h->out_on_host) {
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    std::memcpy(tmp, h->h_out + OUT_STATS, sizeof tmp);
+  } else {
+    CUDA_TRY(h, cudaMemcpyAsync(tmp, h->d_out + OUT_STATS, sizeof tmp, cudaMemcpyDeviceToHost,
+                                h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
   for (int i = 0; i < 4; ++i) stats[i] = tmp[i];
   return MPPI_OK;
 }
