@@ -518,3 +518,31 @@ def test_fp32_peak_probe():
     derived = sms * 128 * 2 * 2.032e9 / 1e12
     v = mppi.measure_fp32_peak()
     assert 0.3 * derived < v <= 1.02 * derived, (v, derived)
+
+
+def test_status_and_stats_follow_the_last_update_path():
+    # host steps leave their output record in pinned host memory, device
+    # steps in device memory: sync() and stats() must read the record of
+    # whichever update ran last
+    torch = torch_mod()
+    c = make_case(1, cost=parity_cost(), K=512, T=5)
+    d_in = torch.tensor(mppi.pack_inputs(c["q"], c["qd"], c["goal"], c["plane"]), device="cuda")
+    with gpu_controller(c) as g:
+        for path in ("host", "device", "device", "host", "device", "host"):
+            if path == "host":
+                g.step(c["q"], c["qd"], c["goal"], c["plane"])
+            else:
+                g.step_device(d_in)
+                assert g.sync() == 0
+            st, S = g.stats(), g.costs()
+            assert st[0] == S.min() and st[3] == 0, path
+    # a device step that finds no finite cost reports it through sync()
+    qd_bad = np.full(7, 1e18, dtype=np.float32)
+    d_bad = torch.tensor(mppi.pack_inputs(c["q"], qd_bad, c["goal"], c["plane"]), device="cuda")
+    with gpu_controller(c) as g:
+        g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        g.step_device(d_bad)
+        assert g.sync() == mppi.ERR_NONFINITE
+        assert g.stats()[3] == c["K"]
+        g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        assert g.sync() == 0 and g.stats()[3] == 0
