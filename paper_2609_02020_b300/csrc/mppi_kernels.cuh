@@ -36,6 +36,16 @@ __device__ __forceinline__ float key_float(unsigned k) {
 }
 constexpr unsigned KEY_NONE = 0xffffffffu;  // above every finite float's key: no finite cost
 
+// atomicAdd with acquire-release semantics at GPU scope
+__device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+               : "=r"(old)
+               : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
 // One warp's share of the two totals that Eq. 4a needs before the weights:
 // the minimum finite cost (as a key, red[0]) and the number of non-finite
 // costs (red[1]).  Every lane of the warp calls it; lanes without a sample
@@ -1503,17 +1513,18 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int e = blockIdx.x;
   const float* nrow = noise + static_cast<size_t>(e) * K;
+  const float pe = prop ? prop[e] : 0.f;  // loaded beside k_split, not after it
   const int k_split = ksplit_p ? *ksplit_p : K;
   const EntryResult<Acc> r =
-      update_entry<Acc>(K, lambda, S, nrow, plan[e], e == 0, k_split < K ? prop[e] : 0.f, k_split,
+      update_entry<Acc>(K, lambda, S, nrow, plan[e], e == 0, k_split < K ? pe : 0.f, k_split,
                         red);
   if (threadIdx.x != 0) return;
   // red (from the rollouts): the last block to finish resets it for the next
   // update, and with ctl_reset (= ksplit_p's {k_split, K}) consumes a second
-  // proposal (k_split := K); all threads of this block read both before
-  // update_entry's barriers
-  if (red) __threadfence();
-  if (red && atomicAdd(red + 2, 1u) == gridDim.x - 1) {
+  // proposal (k_split := K).  All threads of this block read both before
+  // update_entry's barriers; the acquire-release count orders those reads
+  // before the last block's resets.
+  if (red && atomic_add_acq_rel(red + 2, 1u) == gridDim.x - 1) {
     red[0] = KEY_NONE;
     red[1] = 0u;
     red[2] = 0u;
