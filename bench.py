@@ -500,6 +500,7 @@ def run_sweep(args, rank, world):
     torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     steps = max(args.steps, 1)
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2032e6 / 1e12  # derived, as in the update line
     rows, spans = [], []
     with ClockSampler(dev) as clk:
         for T in SWEEP_T:
@@ -529,12 +530,14 @@ def run_sweep(args, rank, world):
                         raise RuntimeError(f"update failed at K={K} T={T}")
                     ms = np.array([x.elapsed_time(y) for x, y in zip(st, en)])
                     ms_roll, ms_upd = ctl.time_kernels(d_in, 20)
+                    tflops = FLOP_PER_ROLLOUT_STEP["contact"] * K * T / (ms_roll * 1e-3) / 1e12
                     rows.append({"K": K, "T": T, "reduce": "f64" if fp64 else "f32",
                                  "variant": ctl.variant(), "ms_per_update": float(ms.mean()),
                                  "p50_ms": float(np.percentile(ms, 50)),
                                  "p99_ms": float(np.percentile(ms, 99)),
                                  "rollout_steps_per_s": K * T / (float(ms.mean()) * 1e-3),
-                                 "rollout_ms": ms_roll, "update_ms": ms_upd})
+                                 "rollout_ms": ms_roll, "update_ms": ms_upd,
+                                 "rollout_tflops": tflops, "frac_fp32_peak": tflops / peak})
                     ctl.close()
     clocks = clk.summary(spans)
     if rank == 0:
