@@ -1356,6 +1356,7 @@ __device__ __forceinline__ void block_sum3(V& a, V& b, V& c, V* sm) {
 // of non-finite costs come from the rollouts (red, see reduce_min_bad) in a
 // step, or from a first walk over K when the caller supplies S (red null).
 constexpr int UPDATE_THREADS = 512;
+constexpr int UPDATE_BATCH = 8;  // float4 pairs (S, noise) in flight per thread
 
 // The weight exp(-(S_k - S_min) / lambda) is formed in FP32 for both
 // accumulator types: its rounding (a few 1e-7 relative) moves u* by about
@@ -1433,29 +1434,45 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
     const float4* N4 = reinterpret_cast<const float4*>(nrow);
     Acc za[4] = {Acc(0), Acc(0), Acc(0), Acc(0)}, z2a[4] = {Acc(0), Acc(0), Acc(0), Acc(0)},
         na[4] = {Acc(0), Acc(0), Acc(0), Acc(0)}, zba[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
-#pragma unroll 2
-    for (int i = threadIdx.x; i < K4; i += UPDATE_THREADS) {
-      const float4 sv = S4[i];
-      const float4 nv = N4[i];
-      const int k = 4 * i;
-      if constexpr (sizeof(Acc) == sizeof(double)) {
-        // FP64 sums of four-sample FP32 partials: one FP64 add per quantity
-        // and float4 instead of one FP64 multiply-add per sample (the FP32
-        // partial of four terms loses no more than the FP32 weights do)
-        float pz = 0.f, pz2 = 0.f, pn = 0.f, pb = 0.f;
-        weight_acc(sv.x, nv.x, m, inv_l, pz, pz2, pn, pb, k >= k_split);
-        weight_acc(sv.y, nv.y, m, inv_l, pz, pz2, pn, pb, k + 1 >= k_split);
-        weight_acc(sv.z, nv.z, m, inv_l, pz, pz2, pn, pb, k + 2 >= k_split);
-        weight_acc(sv.w, nv.w, m, inv_l, pz, pz2, pn, pb, k + 3 >= k_split);
-        za[0] += pz;
-        z2a[0] += pz2;
-        na[0] += pn;
-        zba[0] += pb;
-      } else {
-        weight_acc(sv.x, nv.x, m, inv_l, za[0], z2a[0], na[0], zba[0], k >= k_split);
-        weight_acc(sv.y, nv.y, m, inv_l, za[1], z2a[1], na[1], zba[1], k + 1 >= k_split);
-        weight_acc(sv.z, nv.z, m, inv_l, za[2], z2a[2], na[2], zba[2], k + 2 >= k_split);
-        weight_acc(sv.w, nv.w, m, inv_l, za[3], z2a[3], na[3], zba[3], k + 3 >= k_split);
+    // batches of UPDATE_BATCH float4 pairs per thread: all loads of a batch
+    // are issued before the first weight, so one L2 round trip covers them
+    // (K = 16384: the whole walk in one batch)
+    for (int base = threadIdx.x; base < K4; base += UPDATE_BATCH * UPDATE_THREADS) {
+      float4 sb[UPDATE_BATCH], nb[UPDATE_BATCH];
+#pragma unroll
+      for (int j = 0; j < UPDATE_BATCH; ++j) {
+        const int i = base + j * UPDATE_THREADS;
+        if (i < K4) {
+          sb[j] = S4[i];
+          nb[j] = N4[i];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < UPDATE_BATCH; ++j) {
+        const int i = base + j * UPDATE_THREADS;
+        if (i >= K4) break;
+        const float4 sv = sb[j];
+        const float4 nv = nb[j];
+        const int k = 4 * i;
+        if constexpr (sizeof(Acc) == sizeof(double)) {
+          // FP64 sums of four-sample FP32 partials: one FP64 add per quantity
+          // and float4 instead of one FP64 multiply-add per sample (the FP32
+          // partial of four terms loses no more than the FP32 weights do)
+          float pz = 0.f, pz2 = 0.f, pn = 0.f, pb = 0.f;
+          weight_acc(sv.x, nv.x, m, inv_l, pz, pz2, pn, pb, k >= k_split);
+          weight_acc(sv.y, nv.y, m, inv_l, pz, pz2, pn, pb, k + 1 >= k_split);
+          weight_acc(sv.z, nv.z, m, inv_l, pz, pz2, pn, pb, k + 2 >= k_split);
+          weight_acc(sv.w, nv.w, m, inv_l, pz, pz2, pn, pb, k + 3 >= k_split);
+          za[0] += pz;
+          z2a[0] += pz2;
+          na[0] += pn;
+          zba[0] += pb;
+        } else {
+          weight_acc(sv.x, nv.x, m, inv_l, za[0], z2a[0], na[0], zba[0], k >= k_split);
+          weight_acc(sv.y, nv.y, m, inv_l, za[1], z2a[1], na[1], zba[1], k + 1 >= k_split);
+          weight_acc(sv.z, nv.z, m, inv_l, za[2], z2a[2], na[2], zba[2], k + 2 >= k_split);
+          weight_acc(sv.w, nv.w, m, inv_l, za[3], z2a[3], na[3], zba[3], k + 3 >= k_split);
+        }
       }
     }
     for (int k = 4 * K4 + threadIdx.x; k < K; k += UPDATE_THREADS)
