@@ -1356,7 +1356,11 @@ __device__ __forceinline__ void block_sum3(V& a, V& b, V& c, V* sm) {
 // of non-finite costs come from the rollouts (red, see reduce_min_bad) in a
 // step, or from a first walk over K when the caller supplies S (red null).
 constexpr int UPDATE_THREADS = 512;
-constexpr int UPDATE_BATCH = 8;  // float4 pairs (S, noise) in flight per thread
+// float4 pairs (S, noise) in flight per thread in the weight walk: 8 for the
+// single-problem update (126 blocks, one per SM: latency rules), 2 where
+// blocks share SMs (serving: more resident blocks beat deeper batches)
+constexpr int UPDATE_BATCH = 8;
+constexpr int UPDATE_BATCH_SHARED = 2;
 
 // The weight exp(-(S_k - S_min) / lambda) is formed in FP32 for both
 // accumulator types: its rounding (a few 1e-7 relative) moves u* by about
@@ -1387,8 +1391,9 @@ struct EntryResult {
 // nrow[K].  Samples k >= k_split were drawn around the second proposal p:
 // u* = sum_k wbar_k (u^(k) + dtau_k) = u + (Zb (p - u) + N) / Z, which is
 // exactly u + N / Z when no sample used p (Zb = 0).  Every thread of the
-// block must call it.
-template <typename Acc>
+// block must call it.  BATCH: float4 pairs in flight per thread (see
+// UPDATE_BATCH).
+template <typename Acc, int BATCH = UPDATE_BATCH>
 __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
                                                           const float* __restrict__ S,
                                                           const float* __restrict__ nrow,
@@ -1434,13 +1439,13 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
     const float4* N4 = reinterpret_cast<const float4*>(nrow);
     Acc za[4] = {Acc(0), Acc(0), Acc(0), Acc(0)}, z2a[4] = {Acc(0), Acc(0), Acc(0), Acc(0)},
         na[4] = {Acc(0), Acc(0), Acc(0), Acc(0)}, zba[4] = {Acc(0), Acc(0), Acc(0), Acc(0)};
-    // batches of UPDATE_BATCH float4 pairs per thread: all loads of a batch
-    // are issued before the first weight, so one L2 round trip covers them
-    // (K = 16384: the whole walk in one batch)
-    for (int base = threadIdx.x; base < K4; base += UPDATE_BATCH * UPDATE_THREADS) {
-      float4 sb[UPDATE_BATCH], nb[UPDATE_BATCH];
+    // batches of BATCH float4 pairs per thread: all loads of a batch are
+    // issued before the first weight, so one L2 round trip covers them
+    // (K = 16384 with BATCH = 8: the whole walk in one batch)
+    for (int base = threadIdx.x; base < K4; base += BATCH * UPDATE_THREADS) {
+      float4 sb[BATCH], nb[BATCH];
 #pragma unroll
-      for (int j = 0; j < UPDATE_BATCH; ++j) {
+      for (int j = 0; j < BATCH; ++j) {
         const int i = base + j * UPDATE_THREADS;
         if (i < K4) {
           sb[j] = S4[i];
@@ -1448,7 +1453,7 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
         }
       }
 #pragma unroll
-      for (int j = 0; j < UPDATE_BATCH; ++j) {
+      for (int j = 0; j < BATCH; ++j) {
         const int i = base + j * UPDATE_THREADS;
         if (i >= K4) break;
         const float4 sv = sb[j];

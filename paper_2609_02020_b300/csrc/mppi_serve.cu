@@ -223,8 +223,9 @@ serve_update_kernel(const char* __restrict__ desc, const ProbK* __restrict__ pro
     const TickItem& I = items[it];
     const int e = u - I.upd_begin;
     const EntryResult<float> r =
-        update_entry<float>(I.K, probs[I.prob].lambda, I.S, I.noise + static_cast<size_t>(e) * I.K,
-                            I.plan[e], false);
+        update_entry<float, UPDATE_BATCH_SHARED>(I.K, probs[I.prob].lambda, I.S,
+                                                 I.noise + static_cast<size_t>(e) * I.K,
+                                                 I.plan[e], false);
     if (threadIdx.x == 0) {
       const int t = e / NJ;
       if (r.ok) {
