@@ -93,18 +93,35 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
   }
 }
 
-// u = ((x >> 8) + 0.5) 2^-24 is exact in FP32, so both sides of any
-// comparison see the same uniforms.
-__device__ __forceinline__ float u24(uint32_t x) {
-  return (static_cast<float>(x >> 8) + 0.5f) * 5.9604644775390625e-8f;
+// The uniform u = ((x >> 8) + 1/2) 2^-24 as uh + delta: uh the FP32 value,
+// rounded where u >= 1/2 (there the sum needs 25 significant bits), and
+// delta the exact rest (0 or +-2^-25), so that both sides of any comparison
+// start from the same uniforms.  Every operation here and in box_muller is
+// an explicitly rounded intrinsic, so that no kernel's FMA contraction can
+// change a normal: all kernels draw bit-identical noise.
+__device__ __forceinline__ float uniform24(uint32_t x, float& delta) {
+  constexpr float SCALE = 5.9604644775390625e-8f;  // 2^-24
+  const float t = static_cast<float>(x >> 8);       // exact
+  const float sum = __fadd_rn(t, 0.5f);             // rounded to even when t >= 2^23
+  delta = __fmul_rn(__fadd_rn(__fsub_rn(t, sum), 0.5f), SCALE);  // exact
+  return __fmul_rn(sum, SCALE);
 }
 
+// Box-Muller: z0 = r cos 2 pi u2, z1 = r sin 2 pi u2, r = sqrt(-2 ln u1).
+// The rests of the uniforms enter to first order (their squares are below
+// 1e-14): ln u1 = ln uh1 + delta1 / uh1 (keeps small radii near u1 = 1
+// right: an uh1 rounded to 1 would give r = 0), and the angle's rest
+// 2 pi delta2 rotates (cos, sin).
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
-  const float r = sqrtf(-2.0f * logf(u24(a)));
+  float da, db;
+  const float ua = uniform24(a, da), ub = uniform24(b, db);
+  const float ln_u = __fadd_rn(logf(ua), __fmul_rn(da, __frcp_rn(ua)));
+  const float r = sqrtf(__fmul_rn(-2.0f, ln_u));
   float s, c;
-  sincospif(2.0f * u24(b), &s, &c);
-  z0 = r * c;
-  z1 = r * s;
+  sincospif(__fmul_rn(2.0f, ub), &s, &c);
+  const float e = __fmul_rn(6.28318530717958648f, db);
+  z0 = __fmul_rn(r, fmaf(-e, s, c));
+  z1 = __fmul_rn(r, fmaf(e, c, s));
 }
 
 // The 8 normals of (sample k, step t, update iter); joints use z[0..6].

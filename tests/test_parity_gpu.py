@@ -87,15 +87,33 @@ def test_costs_match_oracle(seed, contact, variant):
     assert_costs(g["S"], o["S"])
 
 
+def assert_plan(g, o, c):
+    """u*, tau0 and the shifted plan against the oracle.  The 1e-5 N m bar
+    holds where FP32 resolves the weights: where the first-order effect of
+    the measured FP32 cost errors on u* (Eq. 4a: sigma dS / lambda through
+    the weights) stays under half the bar.  Where it does not (the seed-4 arm:
+    n_eff ~ 12 and cost errors of 1e-6 relative, far inside the cost bar),
+    the plan error must be that effect, to 1e-6."""
+    dS = g["S"].astype(np.float64) - o["S"]
+    expl = explained_plan_error(o["S"], dS, o["noise"], c["lam"])
+    expl_next = np.vstack([expl[1:], expl[-1:]])
+    pairs = [(g["ustar"], o["ustar"], expl), (g["tau0"], o["ustar"][0], expl[0]),
+             (g["plan"], o["plan_next"], expl_next)]
+    resolved = np.abs(expl).max() <= 0.5 * PLAN_TOL
+    for got, want, e in pairs:
+        if resolved:
+            assert np.abs(got - want).max() <= PLAN_TOL
+        else:
+            assert np.abs(got - want - e).max() <= 0.1 * PLAN_TOL
+
+
 @pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("seed", range(6))
 def test_plan_matches_oracle(seed, variant):
     c = make_case(seed, cost=parity_cost())
     g, o = run_pair(c, variant=variant)
     assert_costs(g["S"], o["S"])
-    assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL
-    assert np.abs(g["tau0"] - o["ustar"][0]).max() <= PLAN_TOL
-    assert np.abs(g["plan"] - o["plan_next"]).max() <= PLAN_TOL
+    assert_plan(g, o, c)
     assert g["iter"] == 1
     # statistics of Eq. 4a
     assert abs(g["stats"][0] - o["stats"][0]) <= S_RTOL * abs(o["stats"][0])
@@ -219,8 +237,7 @@ def test_sizes(K, T, variant):
     c = make_case(4, cost=parity_cost(), K=K, T=T, dt=dt)
     g, o = run_pair(c, variant=variant)
     assert_costs(g["S"], o["S"])
-    assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL
-    assert np.abs(g["plan"] - o["plan_next"]).max() <= PLAN_TOL
+    assert_plan(g, o, c)
     if K == 1:
         nz = noise_ktj(g["noise"], T, K)[0]
         assert np.array_equal(g["ustar"], nz.astype(np.float32))
@@ -366,6 +383,29 @@ def test_full_size_workload_sampled(variant):
         assert np.abs(nzk[k] - nk).max() <= 1e-5
     _, ref, _, _ = oracle.mppi_update(S.astype(np.float64), nzk, np.zeros((c["T"], 7)), c["lam"])
     assert np.abs(us - ref).max() <= PLAN_TOL
+
+
+@pytest.mark.parametrize("K,T,fp64", [(65536, 18, False), (1024, 50, False), (4096, 36, True),
+                                      (65536, 50, True)])
+def test_sweep_points_sampled(K, T, fp64):
+    """Corners of the K x T throughput sweep (contact cost, dt = 0.01 s, the
+    library's kernel choice, FP32 or FP64 reduction): sampled costs and
+    noise against single oracle rollouts, the update against the FP64 update
+    of the GPU's own costs and noise."""
+    c = make_case(1, contact=True, K=K, T=T)
+    with gpu_controller(c, reduce_fp64=fp64) as g:
+        g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        S, nz, us = g.costs(), g.noise(), g.updated_plan()
+    ks = sorted(set(np.linspace(0, K - 1, 24).astype(int).tolist() + [K - 1, 31, 32]))
+    nzk = noise_ktj(nz, T, K)
+    for k in ks:
+        Sk, nk = oracle.rollout(c["rb"], c["oc"], c["dt"], T, c["sigma"], c["seed"], 0, k,
+                                c["q"], c["qd"], c["goal"], c["plane"], np.zeros((T, 7)),
+                                want_noise=True)
+        assert abs(S[k] - Sk) <= S_RTOL * abs(Sk) + S_ATOL, k
+        assert np.abs(nzk[k] - nk).max() <= 1e-5
+    _, ref, _, _ = oracle.mppi_update(S.astype(np.float64), nzk, np.zeros((T, 7)), c["lam"])
+    assert np.abs(us - ref).max() <= (2e-6 if fp64 else PLAN_TOL)
 
 
 def test_rollout_device_matches_step_costs():

@@ -49,20 +49,33 @@ def alone(c, variant, steps=1):
 @pytest.mark.parametrize("variant", [1, 2, 3])
 def test_each_result_same_alone_and_in_the_mix(variant):
     cases = mix(12)
-    with mppi.Server(pool_bytes=1 << 30, max_problems=32, max_batch=32, lanes=2,
-                     variant=variant, rollout_block=64) as srv:
+    kw = dict(pool_bytes=1 << 30, max_problems=32, max_batch=32, lanes=2, variant=variant,
+              rollout_block=64)
+    with mppi.Server(**kw) as srv:
         ids = register(srv, cases)
         tickets = [srv.submit(i, inputs(c)) for i, c in zip(ids, cases)]
         res = [srv.wait(t) for t in tickets]
         plans = [srv.get_plan(i) for i in ids]
         st = srv.stats()
         assert st["ticks"] == 1 and st["completed"] == len(cases)
+    # the same problems served alone, one request per tick: bit-identical
+    with mppi.Server(**kw) as srv:
+        ids = register(srv, cases)
+        for i, c, (rc, tau0), plan in zip(ids, cases, res, plans):
+            rc1, tau1 = srv.wait(srv.submit(i, inputs(c)))
+            assert rc1 == rc == mppi.OK
+            assert np.array_equal(tau1, tau0) and np.array_equal(srv.get_plan(i), plan)
+    # and alone on a single-problem handle (mppi_step).  The rolled and the
+    # warp-specialised serving kernels reproduce it bit for bit.  The register
+    # kernel is compiled twice under register pressure, and the two builds
+    # contract FP32 multiply-adds differently; each result is within the plan
+    # tolerance of the exact (FP64) update, so the two are within twice it.
+    tol = 2 * PLAN_TOL if variant == 1 else 0.0
     for c, (rc, tau0), plan in zip(cases, res, plans):
-        assert rc == mppi.OK
         t_ref, p_ref, it = alone(c, variant)
         assert it == 1
-        assert np.abs(tau0 - t_ref).max() <= PLAN_TOL
-        assert np.abs(plan - p_ref).max() <= PLAN_TOL
+        assert np.abs(tau0 - t_ref).max() <= tol
+        assert np.abs(plan - p_ref).max() <= tol
 
 
 def test_served_problem_matches_oracle():
