@@ -54,12 +54,10 @@ FLOP_PER_ROLLOUT_STEP = {"contact": 4808.1, "force_estimate": 6004.6, "collision
 # kernel) (ncu dram__bytes_{read,write}.sum, mean of two launches).  The
 # 8.3 MB of stored noise stays in L2 for update_kernel and is not written
 # back inside the launch.
-ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel"): 113408,
-                                    ("contact", "rollout_kernel_rolled"): 55552,
-                                    ("contact", "rollout_kernel_ws"): 64384,
-                                    ("collision", "rollout_kernel_ws"): 134144,
-                                    ("force_estimate", "rollout_kernel_rolled"): 66432,
-                                    ("collision", "rollout_kernel_rolled"): 70656}
+# Only kernels captured since their last change are listed; the others
+# report null.
+ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel_ws"): 67328,
+                                    ("collision", "rollout_kernel_ws"): 175360}
 COSTS = ("contact", "force_estimate", "collision")
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
