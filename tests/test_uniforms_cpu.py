@@ -42,8 +42,10 @@ def test_first_order_log_and_angle():
         ln1 = np.log(float(uh)) + float(d) / float(uh)
         assert abs(ln1 - np.log(u)) <= 1e-14 * max(1.0, abs(np.log(u))) + 1e-20, t
         # r = sqrt(-2 ln u) near u = 1: the correction keeps it (an uh of 1
-        # gives 0).  The neglected second-order term delta^2 / (2 uh^2) <=
-        # 2^-51 of ln u moves r by at most 2^-51 / r <= 2e-12 (r >= 2.4e-4)
+        # gives 0).  The neglected second-order term delta^2 / (2 uh^2) of
+        # ln u is at most 2^-51 where uh is near 1, the only place r is small,
+        # and moves r by at most 2^-51 / r <= 2e-12 there (r >= 2.4e-4);
+        # elsewhere it is below 2^-49 against an r of order one
         r_true = np.sqrt(-2.0 * np.log(u))
         assert abs(np.sqrt(-2.0 * ln1) - r_true) <= 2e-12, t
         # angle: (cos, sin)(2 pi uh) rotated by 2 pi delta, to first order
