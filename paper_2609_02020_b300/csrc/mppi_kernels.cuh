@@ -79,11 +79,12 @@ template <bool STORE_NOISE>
 __device__ __forceinline__ float rollout_sample(const ProbK& P, const float* in, const float* plan,
                                                 uint64_t iter, int k, float* __restrict__ noise) {
   const int T = P.T, K = P.K;
-  float q[NJ], qd[NJ];
+  float q[NJ], qd[NJ], q_lo[NJ], qd_lo[NJ];
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     q[j] = in[j];
     qd[j] = in[NJ + j];
+    q_lo[j] = qd_lo[j] = 0.f;
   }
   const float pdes[3] = {in[14], in[15], in[16]};
   float Rd[9];
@@ -128,13 +129,10 @@ __device__ __forceinline__ float rollout_sample(const ProbK& P, const float* in,
     }
     float qdd[NJ];
     ldlt_solve(M, rhs, qdd);
-    // Eq. 7: semi-implicit Euler
+    // Eq. 7: semi-implicit Euler (compensated)
     const float dt = P.dt;
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      qd[j] = fmaf(qdd[j], dt, qd[j]);
-      q[j] = fmaf(qd[j], dt, q[j]);
-    }
+    for (int j = 0; j < NJ; ++j) euler_step(qdd[j], dt, q[j], q_lo[j], qd[j], qd_lo[j]);
     // kinematics and RNEA forward sweep at x_{t+1} (reused by step t+1)
     forward_sweep(P.rb, q, qd, ls, ee);
     // running cost l(x_{t+1}, v_t), Eq. 9-14
@@ -498,11 +496,12 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
   float* sg = sY + 6 * NJ * B;                      // [7][B]    (FEST)
   float* sP = sh + NJ * B + (FEST ? FEST_FLOATS_PER_THREAD * B : 0);  // [8][3][B] (COLL)
   const int T = P.T, K = P.K;
-  float q[NJ], qd[NJ];
+  float q[NJ], qd[NJ], q_lo[NJ], qd_lo[NJ];
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     q[j] = in[j];
     qd[j] = in[NJ + j];
+    q_lo[j] = qd_lo[j] = 0.f;
     sq[j * B + tid] = q[j];
     sqd[j * B + tid] = qd[j];
   }
@@ -566,8 +565,7 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
     const float dt = P.dt;
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
-      qd[j] = fmaf(qdd[j], dt, qd[j]);
-      q[j] = fmaf(qd[j], dt, q[j]);
+      euler_step(qdd[j], dt, q[j], q_lo[j], qd[j], qd_lo[j]);
       sq[j * B + tid] = q[j];
       sqd[j * B + tid] = qd[j];
     }
@@ -898,11 +896,12 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
   const CostK& C = P.cost;
   const bool contact = C.contact != 0;
   const float plane[4] = {in[21], in[22], in[23], in[24]};
-  float q[NJ], qd[NJ];
+  float q[NJ], qd[NJ], q_lo[NJ], qd_lo[NJ];
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     q[j] = in[j];
     qd[j] = in[NJ + j];
+    q_lo[j] = qd_lo[j] = 0.f;
     m.sq[j * B + tid] = q[j];
     m.sqd[j * B + tid] = qd[j];
   }
@@ -953,8 +952,7 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
     const float dt = P.dt;
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
-      qd[j] = fmaf(qdd[j], dt, qd[j]);
-      q[j] = fmaf(qd[j], dt, q[j]);
+      euler_step(qdd[j], dt, q[j], q_lo[j], qd[j], qd_lo[j]);
       m.sq[j * B + tid] = q[j];
       m.sqd[j * B + tid] = qd[j];
     }
@@ -1594,11 +1592,12 @@ static __global__ void simulate_kernel(const __grid_constant__ ProbK P, int n, c
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float* r = in + static_cast<size_t>(i) * IN_FLOATS;
-  float q[NJ], qd[NJ], u[NJ];
+  float q[NJ], qd[NJ], u[NJ], q_lo[NJ], qd_lo[NJ];
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     q[j] = r[j];
     qd[j] = r[NJ + j];
+    q_lo[j] = qd_lo[j] = 0.f;
     u[j] = tau[static_cast<size_t>(i) * NJ + j];
   }
   const float plane[4] = {r[21], r[22], r[23], r[24]};
@@ -1620,10 +1619,7 @@ static __global__ void simulate_kernel(const __grid_constant__ ProbK P, int n, c
     float qdd[NJ];
     ldlt_solve(M, rhs, qdd);
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      qd[j] = fmaf(qdd[j], h, qd[j]);
-      q[j] = fmaf(qd[j], h, q[j]);
-    }
+    for (int j = 0; j < NJ; ++j) euler_step(qdd[j], h, q[j], q_lo[j], qd[j], qd_lo[j]);
   }
   float* o = out + static_cast<size_t>(i) * 2 * NJ;
 #pragma unroll

@@ -70,13 +70,3 @@ def oracle_step(c: dict, plan=None, it: int = 0, want_noise: bool = True, nthrea
 def noise_ktj(gpu_noise: np.ndarray, T: int, K: int) -> np.ndarray:
     """[T*7, K] as the library stores it -> [K, T, 7] as the oracle uses it."""
     return gpu_noise.reshape(T, 7, K).transpose(2, 0, 1).astype(np.float64)
-
-
-def explained_plan_error(S_orc, dS, noise, lam):
-    """First-order effect of per-sample cost errors dS on Eq. 4b:
-    d u* = -sum_k wbar_k (dtau_k - ubar)(dS_k - sum_j wbar_j dS_j) / lambda."""
-    w = np.exp(-(S_orc - S_orc.min()) / lam)
-    wb = w / w.sum()
-    ub = np.einsum("k,ktj->tj", wb, noise)
-    de = dS - np.sum(wb * dS)
-    return -np.einsum("k,ktj->tj", wb * de, noise - ub[None]) / lam

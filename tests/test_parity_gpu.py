@@ -3,11 +3,15 @@
 Tolerances (FP32 path against the FP64 oracle):
   * Philox words: bit-exact (integer work);
   * per-sample cost S_k: |S_gpu - S_orc| <= 1e-4 |S_orc| + 1e-6;
-  * updated plan u* and tau0: <= 1e-5 N m on workloads whose costs FP32
-    resolves (parity_cost); on the heavier free-space weights the plan error
-    minus the first-order effect of the measured cost errors must be
-    <= 1e-5 N m (the error is fully explained by the costs);
+  * updated plan u*, tau0 and the shifted plan: <= 1e-5 N m wherever FP32
+    costs resolve the weights of Eq. 4a: the parity weights (S of 15-50
+    lambda), the contact workload where one sample dominates (n_eff ~ 1),
+    the full-size benchmark workload and the sweep corners;
   * the update alone (same costs and noise on both sides): <= 1e-5 N m.
+At the heavier free-space weights (S of 300-1000 lambda with n_eff of 1-7)
+the 1e-5 N m bar is missed: one FP32 ulp of S_k is there about 1e-5 lambda,
+so no FP32 rollout resolves the weights that finely.  That miss is recorded
+with its measured size in test_plan_recorded_miss_at_heavy_weights.
 """
 import json
 import math
@@ -18,7 +22,7 @@ import pytest
 
 import oracle
 from paper_2609_02020_b300 import mppi, synth
-from _common import (SEED, explained_plan_error, f32, gpu_controller, make_case, noise_ktj,
+from _common import (SEED, f32, gpu_controller, make_case, noise_ktj,
                      oracle_step, parity_cost)
 
 pytestmark = pytest.mark.gpu
@@ -87,24 +91,17 @@ def test_costs_match_oracle(seed, contact, variant):
     assert_costs(g["S"], o["S"])
 
 
-def assert_plan(g, o, c):
-    """u*, tau0 and the shifted plan against the oracle.  The 1e-5 N m bar
-    holds where FP32 resolves the weights: where the first-order effect of
-    the measured FP32 cost errors on u* (Eq. 4a: sigma dS / lambda through
-    the weights) stays under half the bar.  Where it does not (the seed-4 arm:
-    n_eff ~ 12 and cost errors of 1e-6 relative, far inside the cost bar),
-    the plan error must be that effect, to 1e-6."""
-    dS = g["S"].astype(np.float64) - o["S"]
-    expl = explained_plan_error(o["S"], dS, o["noise"], c["lam"])
-    expl_next = np.vstack([expl[1:], expl[-1:]])
-    pairs = [(g["ustar"], o["ustar"], expl), (g["tau0"], o["ustar"][0], expl[0]),
-             (g["plan"], o["plan_next"], expl_next)]
-    resolved = np.abs(expl).max() <= 0.5 * PLAN_TOL
-    for got, want, e in pairs:
-        if resolved:
-            assert np.abs(got - want).max() <= PLAN_TOL
-        else:
-            assert np.abs(got - want - e).max() <= 0.1 * PLAN_TOL
+def plan_errors(g, o):
+    """max |u*_gpu - u*_orc|, max |tau0_gpu - tau0_orc| and max |plan_gpu - plan_orc|."""
+    return (float(np.abs(g["ustar"] - o["ustar"]).max()),
+            float(np.abs(g["tau0"] - o["ustar"][0]).max()),
+            float(np.abs(g["plan"] - o["plan_next"]).max()))
+
+
+def assert_plan(g, o):
+    """u*, tau0 and the shifted plan within 1e-5 N m of the oracle's."""
+    eu, et, ep = plan_errors(g, o)
+    assert eu <= PLAN_TOL and et <= PLAN_TOL and ep <= PLAN_TOL, (eu, et, ep)
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3])
@@ -113,25 +110,47 @@ def test_plan_matches_oracle(seed, variant):
     c = make_case(seed, cost=parity_cost())
     g, o = run_pair(c, variant=variant)
     assert_costs(g["S"], o["S"])
-    assert_plan(g, o, c)
+    assert_plan(g, o)
     assert g["iter"] == 1
     # statistics of Eq. 4a
     assert abs(g["stats"][0] - o["stats"][0]) <= S_RTOL * abs(o["stats"][0])
     assert abs(g["stats"][2] - o["stats"][2]) <= 1e-3 * o["stats"][2]
 
 
-@pytest.mark.parametrize("seed,scale", [(0, 1.0), (1, 1.0), (2, 1.0), (3, 1.0), (4, 0.1),
-                                        (6, 0.1)])
-def test_plan_error_explained_by_cost_error(seed, scale):
-    """Heavier weights (S ~ 30-1000 lambda): FP32 cost errors move the
-    weights; after removing their first-order effect the plan agrees."""
-    c = make_case(seed, cost=parity_cost(scale))
-    g, o = run_pair(c)
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("seed", range(4))
+def test_contact_plan_matches_oracle(seed, variant):
+    """Contact workload (plane 2 cm into contact, 10 N target), K = 256: one
+    sample carries the update (n_eff ~ 1), and the plan meets the bar."""
+    c = make_case(seed, contact=True)
+    g, o = run_pair(c, variant=variant)
     assert_costs(g["S"], o["S"])
-    dS = g["S"].astype(np.float64) - o["S"]
-    expl = explained_plan_error(o["S"], dS, o["noise"], c["lam"])
-    resid = g["ustar"] - o["ustar"] - expl
-    assert np.abs(resid).max() <= PLAN_TOL
+    assert_plan(g, o)
+
+
+# Recorded miss of the 1e-5 N m plan bar.  At these weights S_k is 300-1000
+# lambda (free space, SURVEY c22 weights) or 1e3-1e5 lambda (contact), and the
+# weights of Eq. 4a are spread over a few samples (n_eff of 1.5-7).  A cost
+# error dS moves u* by about sigma dS / lambda through the weights, and FP32
+# cannot make dS smaller than one ulp of S_k (6e-8 S_k, 2e-5 to 6e-5 lambda
+# here) even with exact arithmetic; the measured cost errors are 1e-7 to 8e-6
+# relative, well inside the 1e-4 cost bar.  Measured max |du*| (N m):
+# c22 weights, seeds 0-5: 5e-7 to 5.6e-5; contact seed 4 (n_eff 1.5, the two
+# best samples 1.4 lambda apart): 2.7e-3.  The bounds below guard those sizes.
+HEAVY_MISS_BOUND = {"c22": 1e-4, "contact": 5e-3}
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("case", ["c22-0", "c22-1", "c22-2", "c22-3", "c22-4", "c22-5",
+                                  "contact-4"])
+def test_plan_recorded_miss_at_heavy_weights(case, variant):
+    kind, seed = case.split("-")
+    c = (make_case(int(seed), cost=parity_cost(1.0)) if kind == "c22"
+         else make_case(int(seed), contact=True))
+    g, o = run_pair(c, variant=variant)
+    assert_costs(g["S"], o["S"])
+    assert np.argmin(g["S"]) == np.argmin(o["S"])
+    assert max(plan_errors(g, o)) <= HEAVY_MISS_BOUND[kind]
 
 
 @pytest.mark.parametrize("fp64", [False, True])
@@ -237,7 +256,7 @@ def test_sizes(K, T, variant):
     c = make_case(4, cost=parity_cost(), K=K, T=T, dt=dt)
     g, o = run_pair(c, variant=variant)
     assert_costs(g["S"], o["S"])
-    assert_plan(g, o, c)
+    assert_plan(g, o)
     if K == 1:
         nz = noise_ktj(g["noise"], T, K)[0]
         assert np.array_equal(g["ustar"], nz.astype(np.float32))
@@ -356,56 +375,58 @@ def test_paper_table1_workload():
     c = make_case(7, cost=cost, K=cfg["K"], T=cfg["T"], dt=cfg["dt"], penetration=0.004)
     g, o = run_pair(c)
     assert_costs(g["S"], o["S"])
+    # Table I's weights make S_k of order 1e6 lambda: the weights of Eq. 4a
+    # are one-hot, u* = u + dtau of the best sample.  The plan therefore meets
+    # the bar when both sides pick the same sample, which the gap between the
+    # two best costs guarantees when it exceeds the GPU's cost errors.
     order = np.argsort(o["S"])
     gap = o["S"][order[1]] - o["S"][order[0]]
     dS = np.abs(g["S"].astype(np.float64) - o["S"]).max()
     assert np.argmin(g["S"]) == order[0]
-    if gap > 40.0 * max(dS, 1e-30) * c["lam"] or gap > 40 * c["lam"]:
-        assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL
+    assert gap > 40.0 * dS and gap > 40.0 * c["lam"], (gap, dS)
+    assert_plan(g, o)
+
+
+_ORACLE_FULL = {}
+
+
+def oracle_full(seed, K, T):
+    """The oracle's whole update of the contact workload (cached per case):
+    every sample's cost and noise, u* and the shifted plan."""
+    key = (seed, K, T)
+    if key not in _ORACLE_FULL:
+        c = make_case(seed, contact=True, K=K, T=T)
+        _ORACLE_FULL.clear()
+        _ORACLE_FULL[key] = (c, oracle_step(c, nthreads=os.cpu_count() or 8))
+    return _ORACLE_FULL[key]
+
+
+def assert_full_update(c, o, variant=0, fp64=False):
+    """One GPU update against the oracle's, element by element: all K costs,
+    all K*T*7 noise values, and u*, tau0 and the shifted plan."""
+    with gpu_controller(c, variant=variant, reduce_fp64=fp64) as g:
+        tau0, plan = g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        out = dict(tau0=tau0, plan=plan, S=g.costs(), ustar=g.updated_plan(),
+                   noise=noise_ktj(g.noise(), c["T"], c["K"]))
+    assert_costs(out["S"], o["S"])
+    assert np.abs(out["noise"] - o["noise"]).max() <= 1e-5
+    assert_plan(out, o)
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3])
-def test_full_size_workload_sampled(variant):
-    """K=16384, T=18 with contact (the benchmark's workload): sampled costs
-    and noise against single oracle rollouts; the update against the FP64
-    update of the GPU's own costs and noise."""
-    c = make_case(0, contact=True, K=16384, T=18)
-    with gpu_controller(c, variant=variant) as g:
-        g.step(c["q"], c["qd"], c["goal"], c["plane"])
-        S, nz, us = g.costs(), g.noise(), g.updated_plan()
-    ks = sorted(set(np.linspace(0, c["K"] - 1, 40).astype(int).tolist() + [c["K"] - 1, 127, 128]))
-    nzk = noise_ktj(nz, c["T"], c["K"])
-    for k in ks:
-        Sk, nk = oracle.rollout(c["rb"], c["oc"], c["dt"], c["T"], c["sigma"], c["seed"], 0, k,
-                                c["q"], c["qd"], c["goal"], c["plane"], np.zeros((c["T"], 7)),
-                                want_noise=True)
-        assert abs(S[k] - Sk) <= S_RTOL * abs(Sk) + S_ATOL, k
-        assert np.abs(nzk[k] - nk).max() <= 1e-5
-    _, ref, _, _ = oracle.mppi_update(S.astype(np.float64), nzk, np.zeros((c["T"], 7)), c["lam"])
-    assert np.abs(us - ref).max() <= PLAN_TOL
+def test_full_size_workload_matches_oracle(variant):
+    """K=16384, T=18 with contact (the benchmark's workload and launch shape)."""
+    c, o = oracle_full(0, 16384, 18)
+    assert_full_update(c, o, variant)
 
 
 @pytest.mark.parametrize("K,T,fp64", [(65536, 18, False), (1024, 50, False), (4096, 36, True),
                                       (65536, 50, True)])
-def test_sweep_points_sampled(K, T, fp64):
+def test_sweep_points_match_oracle(K, T, fp64):
     """Corners of the K x T throughput sweep (contact cost, dt = 0.01 s, the
-    library's kernel choice, FP32 or FP64 reduction): sampled costs and
-    noise against single oracle rollouts, the update against the FP64 update
-    of the GPU's own costs and noise."""
-    c = make_case(1, contact=True, K=K, T=T)
-    with gpu_controller(c, reduce_fp64=fp64) as g:
-        g.step(c["q"], c["qd"], c["goal"], c["plane"])
-        S, nz, us = g.costs(), g.noise(), g.updated_plan()
-    ks = sorted(set(np.linspace(0, K - 1, 24).astype(int).tolist() + [K - 1, 31, 32]))
-    nzk = noise_ktj(nz, T, K)
-    for k in ks:
-        Sk, nk = oracle.rollout(c["rb"], c["oc"], c["dt"], T, c["sigma"], c["seed"], 0, k,
-                                c["q"], c["qd"], c["goal"], c["plane"], np.zeros((T, 7)),
-                                want_noise=True)
-        assert abs(S[k] - Sk) <= S_RTOL * abs(Sk) + S_ATOL, k
-        assert np.abs(nzk[k] - nk).max() <= 1e-5
-    _, ref, _, _ = oracle.mppi_update(S.astype(np.float64), nzk, np.zeros((T, 7)), c["lam"])
-    assert np.abs(us - ref).max() <= (2e-6 if fp64 else PLAN_TOL)
+    library's kernel choice, FP32 or FP64 reduction)."""
+    c, o = oracle_full(1, K, T)
+    assert_full_update(c, o, 0, fp64)
 
 
 def test_rollout_device_matches_step_costs():
@@ -508,8 +529,10 @@ def plant_step(c, q, qd, tau, dt, sub=10):
 
 def test_receding_horizon_contact_loop():
     """200 warm-started updates (K=4096, T=18) closing the loop on the FP64
-    model with a zero-order hold; one update mid-way is checked against the
-    oracle from the same state, plan and iter."""
+    model with a zero-order hold, pressing on the plane toward the 10 N
+    target; update 100 is checked against the oracle from the same state,
+    plan and iter (costs, the best sample, u*, tau0 and the shifted plan),
+    and the force over the last 100 updates against the target."""
     c = make_case(0, contact=True, K=4096, T=18, penetration=0.02)
     q, qd = c["q"].copy(), c["qd"].copy()
     gcomp = oracle.rnea(c["rb"], q, np.zeros(7), np.zeros(7))
@@ -520,10 +543,12 @@ def test_receding_horizon_contact_loop():
             if it == 100:
                 plan = g.get_plan()
                 q32, qd32 = f32(q), f32(qd)
-                tau0, _ = g.step(q32, qd32, c["goal"], c["plane"])
-                S = g.costs()
+                tau0, pl = g.step(q32, qd32, c["goal"], c["plane"])
+                out = dict(tau0=tau0, plan=pl, S=g.costs(), ustar=g.updated_plan())
                 o = oracle_step(c, plan=plan, it=100, q=q32, qd=qd32, want_noise=False)
-                assert_costs(S, o["S"])
+                assert_costs(out["S"], o["S"])
+                assert np.argmin(out["S"]) == np.argmin(o["S"])
+                mid = (max(plan_errors(out, o)), o["stats"][2], o["stats"][0])
             else:
                 tau0, _ = g.step(f32(q), f32(qd), c["goal"], c["plane"])
             assert np.all(np.isfinite(tau0))
@@ -531,6 +556,18 @@ def test_receding_horizon_contact_loop():
             forces.append(oracle.contact(c["rb"], c["oc"], c["plane"], q, qd)[0])
         assert g.get_iter() == 200
     assert np.all(np.isfinite(q)) and np.all(np.abs(qd) < 50)
+    f = np.array(forces[100:])
+    print(f"update 100: max |du*| {mid[0]:.2e} N m, n_eff {mid[1]:.2f}, S_min {mid[2]:.4g}; "
+          f"contact force over updates 100-199: mean {f.mean():.3f} N, std {f.std():.3f} N, "
+          f"min {f.min():.3f}, max {f.max():.3f}, in contact {np.mean(f > 0):.2f}")
+    # Update 100 sits in the heavy-weight regime (S_min ~ 250 lambda, n_eff
+    # ~ 5.5) where the 1e-5 N m plan bar is a recorded miss: measured 8.9e-4.
+    assert mid[0] <= 2e-3
+    # force tracking (BASELINE config 2's 10 N target): measured mean 9.73 N,
+    # std 0.71 N, in contact at every update
+    assert abs(f.mean() - 10.0) <= 1.0
+    assert np.mean(np.abs(f - 10.0)) <= 1.0
+    assert f.min() > 0.0
 
 
 def test_default_kernel_choice():
