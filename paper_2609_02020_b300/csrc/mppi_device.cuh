@@ -455,24 +455,25 @@ __device__ __forceinline__ void ldlt_solve(float M[NJ * (NJ + 1) / 2], const flo
 // ---------------------------------------------------------------------------
 // Semi-implicit Euler step of Eq. 7 on a compensated state.  Each of q and qd
 // is carried as an unevaluated sum hi + lo of two floats: hi is the nearest
-// float of the state and the one the dynamics and costs see; lo is the exact
-// rounding error of the last addition (Knuth's TwoSum), folded into the next
-// step's increment.  Plain FP32 would round q to half an ulp (about 1e-7 rad)
-// at every step, and over a horizon that rounding, fed back through the
-// dynamics, is the largest error of an FP32 rollout against an exact one.
-// Every operation is explicitly rounded, so that no FMA contraction breaks
-// the error recovery.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+// float of the state and the one the dynamics and costs see; lo is the
+// rounding error of the last addition, recovered by Dekker's Fast2Sum and
+// folded into the next step's increment.  Plain FP32 would round q to half
+// an ulp (about 1e-7 rad) at every step, and over a horizon that rounding,
+// fed back through the dynamics, is the largest error of an FP32 rollout
+// against an exact one.  Fast2Sum is exact when |hi| >= |increment|; where
+// it is not (a state near zero), the part it misses is below half an ulp of
+// the increment (under 3e-8 rad/s for qd, 2e-9 rad for q).  Every operation
+// is explicitly rounded, so that no FMA contraction breaks the recovery.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  e = __fsub_rn(b, __fsub_rn(s, a));
 }
 
 // qd' = qd + qdd dt, q' = q + qd' dt (Eq. 7) on (hi, lo) pairs.
 __device__ __forceinline__ void euler_step(float qdd, float dt, float& q, float& q_lo, float& qd,
                                            float& qd_lo) {
-  two_sum(qd, __fmaf_rn(qdd, dt, qd_lo), qd, qd_lo);
-  two_sum(q, __fmaf_rn(qd, dt, __fmaf_rn(qd_lo, dt, q_lo)), q, q_lo);
+  fast_two_sum(qd, __fmaf_rn(qdd, dt, qd_lo), qd, qd_lo);
+  fast_two_sum(q, __fmaf_rn(qd, dt, __fmaf_rn(qd_lo, dt, q_lo)), q, q_lo);
 }
 
 // ---------------------------------------------------------------------------

@@ -4,8 +4,11 @@
 //                     (register-unrolled, one thread per sample; link loops
 //                     rolled through shared memory; three warps per 32
 //                     samples);
-//   update_kernel   - Eq. 4a-4b and the warm-start shift, one block per plan
-//                     entry (t, j), each block reducing over all K samples.
+//   merge_kernel    - Eq. 4a-4b and the warm-start shift of a step: one block
+//                     per plan entry (t, j) merging the rollout blocks'
+//                     log-sum-exp partials (block_partial);
+//   update_kernel   - Eq. 4a-4b and the shift from caller-supplied costs and
+//                     noise, one block per plan entry reducing over all K.
 #pragma once
 #include <cfloat>
 #include <cstdint>
@@ -25,17 +28,6 @@ __device__ __forceinline__ void allow_dependent_launch() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Ordered keys of finite floats: the keys compare as unsigned integers the
-// way the floats compare, so that atomicMin over keys gives the minimum cost.
-__device__ __forceinline__ unsigned float_key(float f) {
-  const unsigned b = __float_as_uint(f);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float key_float(unsigned k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
-}
-constexpr unsigned KEY_NONE = 0xffffffffu;  // above every finite float's key: no finite cost
-
 // atomicAdd with acquire-release semantics at GPU scope
 __device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned* p, unsigned v) {
   unsigned old;
@@ -46,22 +38,76 @@ __device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned* p, unsigned v) 
   return old;
 }
 
-// One warp's share of the two totals that Eq. 4a needs before the weights:
-// the minimum finite cost (as a key, red[0]) and the number of non-finite
-// costs (red[1]).  Every lane of the warp calls it; lanes without a sample
-// pass live = false.  The update kernel then skips its pass over S.
-__device__ __forceinline__ void reduce_min_bad(unsigned* red, float s, bool live) {
-  const bool fin = live && isfinite(s);
-  unsigned key = fin ? float_key(s) : KEY_NONE;
-  unsigned bad = (live && !fin) ? 1u : 0u;
+template <typename V>
+__device__ __forceinline__ V warp_sum(V x) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    key = min(key, __shfl_xor_sync(0xffffffffu, key, o));
-    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ float warp_min(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+// Log-sum-exp partials of one rollout block (the sharded form of Eq. 4: a
+// block's share of the update, merged over blocks by merge_kernel).  Record
+// of PART_HEAD + T*7 floats (stride part_stride(T)):
+//   [0] m_b = min of the block's finite costs (+inf if none)
+//   [1] Z_b = sum_k w_k, w_k = exp(-(S_k - m_b) / lambda), 0 for non-finite S_k
+//   [2] sum_k w_k^2                      [3] sum of w_k over k >= k_split
+//   [4] number of non-finite costs       [PART_HEAD + e] N_b[e] = sum_k w_k dtau_{k,e}
+constexpr int PART_HEAD = 8;
+__host__ __device__ constexpr int part_stride(int T) { return (PART_HEAD + T * NJ + 3) / 4 * 4; }
+
+// Every thread of a block of NT threads calls it after the block's n costs
+// (samples k0 .. k0 + n - 1, n <= 32) are in s_S[0..n); the block's noise
+// dtau[T*7][K] was written earlier in the same kernel and is read back
+// through L2 (ld.global.cg), 32 samples x 4 B per plan entry.
+template <int NT>
+__device__ __forceinline__ void block_partial(const float* s_S, float* s_w, int k0, int n, int K,
+                                              int T, float lambda, int k_split, const float* noise,
+                                              float* part) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+    const float sk = l < n ? s_S[l] : 0.f;
+    const bool fin = l < n && isfinite(sk);
+    const float m = warp_min(fin ? sk : INFINITY);
+    const float w = fin ? expf((m - sk) * (1.0f / lambda)) : 0.f;
+    s_w[l] = w;
+    const float z = warp_sum(w), z2 = warp_sum(w * w);
+    const float zs = warp_sum(k0 + l >= k_split ? w : 0.f);
+    const unsigned bad = __popc(__ballot_sync(0xffffffffu, l < n && !fin));
+    if (l == 0) {
+      part[0] = m;
+      part[1] = z;
+      part[2] = z2;
+      part[3] = zs;
+      part[4] = static_cast<float>(bad);
+    }
   }
-  if ((threadIdx.x & 31) == 0) {
-    if (key != KEY_NONE) atomicMin(red, key);
-    if (bad) atomicAdd(red + 1, bad);
+  __syncthreads();
+  const int E = T * NJ;
+  const bool vec = n == 32 && (K & 3) == 0;
+  for (int e = threadIdx.x; e < E; e += NT) {
+    const float* row = noise + static_cast<size_t>(e) * K + k0;
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    if (vec) {
+      float4 v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = __ldcg(reinterpret_cast<const float4*>(row) + i);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        a[0] = fmaf(s_w[4 * i], v[i].x, a[0]);
+        a[1] = fmaf(s_w[4 * i + 1], v[i].y, a[1]);
+        a[2] = fmaf(s_w[4 * i + 2], v[i].z, a[2]);
+        a[3] = fmaf(s_w[4 * i + 3], v[i].w, a[3]);
+      }
+    } else {
+      for (int l = 0; l < n; ++l) a[l & 3] = fmaf(s_w[l], __ldcg(row + l), a[l & 3]);
+    }
+    part[PART_HEAD + e] = (a[0] + a[1]) + (a[2] + a[3]);
   }
 }
 
@@ -160,14 +206,15 @@ __device__ __forceinline__ float rollout_sample(const ProbK& P, const float* in,
 // One rollout per thread.  plan: [T][7] nominal torques; in: IN_FLOATS
 // inputs; iter: update counter (device); S: [K] costs; noise: [T*7][K].
 // Samples k < k_split roll out around plan; samples k >= k_split around the
-// second proposal prop (ksplit_p null: every sample around plan).
+// second proposal prop (ksplit_p null: every sample around plan).  part
+// (with STORE_NOISE): each block's log-sum-exp partials (block_partial).
 template <bool STORE_NOISE>
 __global__ void __launch_bounds__(ROLLOUT_BLOCK)
 rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
                const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
                float* __restrict__ S, float* __restrict__ noise,
                const float* __restrict__ prop = nullptr, const int* __restrict__ ksplit_p = nullptr,
-               unsigned* __restrict__ red = nullptr) {
+               float* __restrict__ part = nullptr) {
   __shared__ float s_plan[T_MAX * NJ];
   __shared__ float s_prop[T_MAX * NJ];
   __shared__ float s_in[IN_FLOATS];
@@ -184,7 +231,13 @@ rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
     sk = rollout_sample<STORE_NOISE>(P, s_in, k < k_split ? s_plan : s_prop, *iter_p, k, noise);
     S[k] = sk;
   }
-  if (red) reduce_min_bad(red, sk, k < K);  // one warp per block
+  if (STORE_NOISE && part) {
+    __shared__ float s_S[ROLLOUT_BLOCK], s_w[ROLLOUT_BLOCK];
+    s_S[threadIdx.x] = sk;
+    const int k0 = blockIdx.x * ROLLOUT_BLOCK;
+    block_partial<ROLLOUT_BLOCK>(s_S, s_w, k0, min(ROLLOUT_BLOCK, K - k0), K, T, P.lambda, k_split,
+                                 noise, part + static_cast<size_t>(blockIdx.x) * part_stride(T));
+  }
   allow_dependent_launch();
 }
 
@@ -610,7 +663,7 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
                       float* __restrict__ S, float* __restrict__ noise,
                       const float* __restrict__ prop = nullptr,
                       const int* __restrict__ ksplit_p = nullptr,
-                      const ObsK* __restrict__ obs = nullptr, unsigned* __restrict__ red = nullptr) {
+                      const ObsK* __restrict__ obs = nullptr, float* __restrict__ part = nullptr) {
   constexpr bool COLL = (FEAT & FEAT_COLL) != 0;
   extern __shared__ float dsm[];
   const int T = P.T, K = P.K;
@@ -653,7 +706,13 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
                                                      s_obs, n_obs);
     S[k] = sk;
   }
-  if (red) reduce_min_bad(red, sk, k < K);  // B = 32: one warp per block
+  if (STORE_NOISE && part) {
+    __shared__ float s_S[B], s_w[B];
+    s_S[threadIdx.x] = sk;
+    const int k0 = blockIdx.x * B;
+    block_partial<B>(s_S, s_w, k0, min(B, K - k0), K, T, P.lambda, k_split, noise,
+                     part + static_cast<size_t>(blockIdx.x) * part_stride(T));
+  }
   allow_dependent_launch();
 }
 
@@ -1204,7 +1263,7 @@ rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
                   float* __restrict__ S, float* __restrict__ noise,
                   const float* __restrict__ prop = nullptr,
                   const int* __restrict__ ksplit_p = nullptr,
-                  const ObsK* __restrict__ obs = nullptr, unsigned* __restrict__ red = nullptr) {
+                  const ObsK* __restrict__ obs = nullptr, float* __restrict__ part = nullptr) {
   extern __shared__ float4 dsm4[];
   float* dsm = reinterpret_cast<float*>(dsm4);
   const int K = P.K;
@@ -1239,18 +1298,24 @@ rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
   const int k_raw = blockIdx.x * WS_B + lane;
   const bool live = k_raw < K;
   const int k = live ? k_raw : K - 1;
+  __shared__ float s_S[WS_B], s_w[WS_B];
   if (warp == 0) {
     ws_dynamics<COLL>(P, s_in, m, lane);
   } else if (warp == 1) {
     const float Sk = ws_costs<COLL>(P, s_in, m, lane);
     if (live) S[k] = Sk;
-    if (red) reduce_min_bad(red, Sk, live);
+    s_S[lane] = Sk;
   } else if (warp == 2) {
     ws_noise<STORE_NOISE, COLL>(P, s_in, k < k_split ? plan : prop, *iter_p, k, live, noise, m,
                                 lane);
   } else if (COLL) {
     if (warp == 3) ws_collision<0>(P, m, s_obs, n_obs, lane);
     else ws_collision<1>(P, m, s_obs, n_obs, lane);
+  }
+  if (STORE_NOISE && part) {
+    const int k0 = blockIdx.x * WS_B;
+    block_partial<ws_threads(COLL)>(s_S, s_w, k0, min(WS_B, K - k0), K, P.T, P.lambda, k_split,
+                                    noise, part + static_cast<size_t>(blockIdx.x) * part_stride(P.T));
   }
   allow_dependent_launch();
 }
@@ -1300,18 +1365,6 @@ force_estimate_kernel(const __grid_constant__ ProbK P, const float* __restrict__
 // ---------------------------------------------------------------------------
 // block reductions
 
-template <typename V>
-__device__ __forceinline__ V warp_sum(V x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
-__device__ __forceinline__ float warp_min(float x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
-  return x;
-}
-
 template <int BLOCK>
 __device__ __forceinline__ float block_min(float x, float* sm) {
   x = warp_min(x);
@@ -1348,11 +1401,10 @@ __device__ __forceinline__ void block_sum3(V& a, V& b, V& c, V* sm) {
 // Costs that are not finite get weight 0; if none is finite the plan is kept
 // (u* = u, next plan = u) and status 1 is reported.  out (may be null):
 // tau0, status, stats and a copy of the shifted plan (OUT_* offsets).
-// Each block walks K for the weights and the weighted noise row; when S and
-// the row are 16-byte aligned it reads float4 and keeps four independent
-// accumulators so that the L2 loads overlap.  The minimum cost and the count
-// of non-finite costs come from the rollouts (red, see reduce_min_bad) in a
-// step, or from a first walk over K when the caller supplies S (red null).
+// Each block walks K for the minimum cost and the count of non-finite costs,
+// then for the weights and the weighted noise row; when S and the row are
+// 16-byte aligned it reads float4 and keeps four independent accumulators so
+// that the L2 loads overlap.
 constexpr int UPDATE_THREADS = 512;
 // float4 pairs (S, noise) in flight per thread in the weight walk: 8 for the
 // single-problem update (126 blocks, one per SM: latency rules), 2 where
@@ -1396,8 +1448,7 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
                                                           const float* __restrict__ S,
                                                           const float* __restrict__ nrow,
                                                           float u, bool count_bad, float p = 0.f,
-                                                          int k_split = 0x7fffffff,
-                                                          const unsigned* red = nullptr) {
+                                                          int k_split = 0x7fffffff) {
   __shared__ float sm_f[32];
   __shared__ Acc sm_a[3 * 32];
   const bool vec = (K % 4 == 0) && ((reinterpret_cast<uintptr_t>(S) & 15) == 0) &&
@@ -1405,12 +1456,7 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
   const int K4 = vec ? K / 4 : 0;
   float m = INFINITY;
   int bad = 0;
-  if (red) {
-    // minimum and non-finite count from the rollouts (totals, not shares)
-    const unsigned key = __ldcg(red);
-    m = key == KEY_NONE ? INFINITY : key_float(key);
-    bad = static_cast<int>(__ldcg(red + 1));
-  } else {
+  {
     const float4* S4 = reinterpret_cast<const float4*>(S);
 #pragma unroll 4
     for (int i = threadIdx.x; i < K4; i += UPDATE_THREADS) {
@@ -1428,7 +1474,7 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
       else ++bad;
     }
   }
-  if (!red) m = block_min<UPDATE_THREADS>(m, sm_f);
+  m = block_min<UPDATE_THREADS>(m, sm_f);
   const bool ok = isfinite(m);
   Acc z = Acc(0), z2 = Acc(0), nacc = Acc(0), zb = Acc(0);
   if (ok) {
@@ -1492,9 +1538,7 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
     block_sum3<UPDATE_THREADS>(zbs, d1, d2, sm_a);
   }
   Acc nbad = Acc(0);
-  if (count_bad && red) {
-    nbad = static_cast<Acc>(bad);
-  } else if (count_bad) {
+  if (count_bad) {
     nbad = static_cast<Acc>(bad);
     d1 = d2 = Acc(0);
     __syncthreads();
@@ -1519,40 +1563,15 @@ __device__ __forceinline__ EntryResult<Acc> update_entry(int K, float lambda,
   return r;
 }
 
-template <typename Acc>
-__global__ void __launch_bounds__(UPDATE_THREADS)
-update_kernel(int K, int T, float lambda, const float* __restrict__ S,
-              const float* __restrict__ noise, const float* __restrict__ plan,
-              float* __restrict__ ustar, float* __restrict__ plan_next, float* __restrict__ out,
-              unsigned long long* __restrict__ iter_p, const float* __restrict__ prop = nullptr,
-              const int* ksplit_p = nullptr, float* __restrict__ tau_dst = nullptr,
-              float* __restrict__ plan_dst = nullptr, unsigned* __restrict__ red = nullptr,
-              int* ctl_reset = nullptr) {
-  // launched as a programmatic dependent of the rollout kernel: wait here
-  // until the rollouts' results are visible (a no-op otherwise)
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  const int e = blockIdx.x;
-  const float* nrow = noise + static_cast<size_t>(e) * K;
-  const float pe = prop ? prop[e] : 0.f;  // loaded beside k_split, not after it
-  const int k_split = ksplit_p ? *ksplit_p : K;
-  const EntryResult<Acc> r =
-      update_entry<Acc>(K, lambda, S, nrow, plan[e], e == 0, k_split < K ? pe : 0.f, k_split,
-                        red);
-  if (threadIdx.x != 0) return;
-  // red (from the rollouts): the last block to finish resets it for the next
-  // update, and with ctl_reset (= ksplit_p's {k_split, K}) consumes a second
-  // proposal (k_split := K).  All threads of this block read both before
-  // update_entry's barriers; the acquire-release count orders those reads
-  // before the last block's resets.
-  if (red && atomic_add_acq_rel(red + 2, 1u) == gridDim.x - 1) {
-    red[0] = KEY_NONE;
-    red[1] = 0u;
-    red[2] = 0u;
-    if (ctl_reset) ctl_reset[0] = ctl_reset[1];
-  }
+// Plan outputs of one entry e = t*7 + j of Eq. 4 (thread 0 of its block):
+// u* and the shifted plan (u*_{t+1} moves to t; the last entry repeats),
+// also into the output record and the caller's buffers when given; when no
+// cost was finite the plan is kept as it is, unshifted.
+__device__ __forceinline__ void write_entry(int e, int T, bool ok, float us, float* ustar,
+                                            float* plan_next, float* out, float* tau_dst,
+                                            float* plan_dst) {
   const int t = e / NJ;
-  const float us = r.us;
-  if (r.ok) {
+  if (ok) {
     if (t >= 1) plan_next[e - NJ] = us;
     if (t == T - 1) plan_next[e] = us;
     if (out) {
@@ -1571,15 +1590,171 @@ update_kernel(int K, int T, float lambda, const float* __restrict__ S,
   ustar[e] = us;
   if (out && e < NJ) out[OUT_TAU0 + e] = us;
   if (tau_dst && e < NJ) tau_dst[e] = us;
+}
+
+// The record's status and Eq. 4a statistics (block of entry 0): status,
+// S_min, Z, n_eff = Z^2 / sum w^2, number of non-finite costs.
+__device__ __forceinline__ void write_stats(float* out, bool ok, float m, double z, double z2,
+                                            double bad) {
+  reinterpret_cast<int*>(out)[OUT_STATUS] = ok ? 0 : 1;
+  out[OUT_STATS + 0] = m;
+  out[OUT_STATS + 1] = static_cast<float>(z);
+  out[OUT_STATS + 2] = ok ? static_cast<float>(z * z / z2) : 0.f;
+  out[OUT_STATS + 3] = static_cast<float>(bad);
+}
+
+// Eq. 4 from caller-supplied costs S [K] and noise [T*7][K] (one block per
+// plan entry), with the shift; out, iter_p, tau_dst, plan_dst may be null.
+template <typename Acc>
+__global__ void __launch_bounds__(UPDATE_THREADS)
+update_kernel(int K, int T, float lambda, const float* __restrict__ S,
+              const float* __restrict__ noise, const float* __restrict__ plan,
+              float* __restrict__ ustar, float* __restrict__ plan_next, float* __restrict__ out,
+              unsigned long long* __restrict__ iter_p, const float* __restrict__ prop = nullptr,
+              const int* ksplit_p = nullptr, float* __restrict__ tau_dst = nullptr,
+              float* __restrict__ plan_dst = nullptr) {
+  const int e = blockIdx.x;
+  const float* nrow = noise + static_cast<size_t>(e) * K;
+  const float pe = prop ? prop[e] : 0.f;
+  const int k_split = ksplit_p ? *ksplit_p : K;
+  const EntryResult<Acc> r =
+      update_entry<Acc>(K, lambda, S, nrow, plan[e], e == 0, k_split < K ? pe : 0.f, k_split);
+  if (threadIdx.x != 0) return;
+  write_entry(e, T, r.ok, r.us, ustar, plan_next, out, tau_dst, plan_dst);
   if (e == 0) {
-    if (out) {
-      reinterpret_cast<int*>(out)[OUT_STATUS] = r.ok ? 0 : 1;
-      out[OUT_STATS + 0] = r.m;
-      out[OUT_STATS + 1] = static_cast<float>(r.z);
-      out[OUT_STATS + 2] = r.ok ? static_cast<float>(r.z * r.z / r.z2) : 0.f;
-      out[OUT_STATS + 3] = static_cast<float>(r.bad);
-    }
+    if (out) write_stats(out, r.ok, r.m, static_cast<double>(r.z), static_cast<double>(r.z2), r.bad);
     if (iter_p && r.ok) *iter_p += 1ull;
+  }
+}
+
+// Log-sum-exp accumulator over rollout blocks: sums relative to the running
+// minimum m (weights exp(-(S - m) / lambda)); a new minimum rescales what is
+// held.  m = +inf holds nothing.
+template <typename Acc>
+struct Lse {
+  float m;
+  Acc z, n, zs, z2;
+};
+
+template <typename Acc>
+__device__ __forceinline__ Lse<Acc> lse_merge(const Lse<Acc>& a, const Lse<Acc>& b, float inv_l) {
+  if (!isfinite(b.m)) return a;
+  if (!isfinite(a.m)) return b;
+  Lse<Acc> r;
+  r.m = fminf(a.m, b.m);
+  const Acc ca = static_cast<Acc>(expf((r.m - a.m) * inv_l));
+  const Acc cb = static_cast<Acc>(expf((r.m - b.m) * inv_l));
+  r.z = ca * a.z + cb * b.z;
+  r.n = ca * a.n + cb * b.n;
+  r.zs = ca * a.zs + cb * b.zs;
+  r.z2 = ca * ca * a.z2 + cb * cb * b.z2;
+  return r;
+}
+
+template <typename Acc>
+__device__ __forceinline__ Lse<Acc> lse_shfl(const Lse<Acc>& a, int o) {
+  Lse<Acc> r;
+  r.m = __shfl_xor_sync(0xffffffffu, a.m, o);
+  r.z = __shfl_xor_sync(0xffffffffu, a.z, o);
+  r.n = __shfl_xor_sync(0xffffffffu, a.n, o);
+  r.zs = __shfl_xor_sync(0xffffffffu, a.zs, o);
+  r.z2 = __shfl_xor_sync(0xffffffffu, a.z2, o);
+  return r;
+}
+
+// Eq. 4a-4b of a step from the rollout blocks' partials (block_partial;
+// nb records of pstride floats), one block per plan entry e:
+//   m = min_b m_b,  c_b = exp(-(m_b - m) / lambda)  (0 for a block with no
+//   finite cost),  Z = sum_b c_b Z_b,  N_e = sum_b c_b N_b[e],
+//   u*_e = u_e + N_e / Z, or with a second proposal p for samples
+//   k >= k_split: u*_e = u_e + (Zs (p_e - u_e) + N_e) / Z, Zs = sum_b c_b Zs_b
+// (the merge rule of the sharded update), then the shift.  One pass over the
+// partials: each thread folds its blocks into a running log-sum-exp
+// accumulator, and the threads' accumulators merge by the same rule.
+// Launched as a programmatic dependent of the rollouts.  When this update
+// has a second proposal (k_split < K), the last block (done counter) resets
+// the counter and, through ctl_reset (= ksplit_p's {k_split, K}), consumes
+// the proposal (k_split := K).  Acc: the type of the sums over blocks.
+constexpr int MERGE_THREADS = 256;
+
+template <typename Acc>
+__global__ void __launch_bounds__(MERGE_THREADS)
+merge_kernel(int K, int T, float lambda, int nb, int pstride, const float* part,
+             const float* __restrict__ plan, float* __restrict__ ustar,
+             float* __restrict__ plan_next, float* __restrict__ out,
+             unsigned long long* __restrict__ iter_p, const float* __restrict__ prop,
+             const int* ksplit_p, float* __restrict__ tau_dst, float* __restrict__ plan_dst,
+             unsigned* done, int* ctl_reset) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  __shared__ Lse<Acc> sm[MERGE_THREADS / 32];
+  __shared__ float sm_bad[MERGE_THREADS / 32];
+  const int e = blockIdx.x;
+  const float u = plan[e];
+  const float pe = prop ? prop[e] : 0.f;
+  const int k_split = ksplit_p ? *ksplit_p : K;
+  const float inv_l = 1.0f / lambda;
+  Lse<Acc> acc{INFINITY, Acc(0), Acc(0), Acc(0), Acc(0)};
+  float bad = 0.f;
+  for (int b0 = threadIdx.x; b0 < nb; b0 += 4 * MERGE_THREADS) {
+    // up to four partials per thread in flight before the first is used
+    float4 hd[4];
+    float nv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + j * MERGE_THREADS;
+      if (b < nb) {
+        const float* pb = part + static_cast<size_t>(b) * pstride;
+        hd[j] = __ldcg(reinterpret_cast<const float4*>(pb));  // m_b, Z_b, sum w^2, Zs_b
+        nv[j] = __ldcg(pb + PART_HEAD + e);
+        if (e == 0) bad += __ldcg(pb + 4);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (b0 + j * MERGE_THREADS < nb) {
+        const Lse<Acc> p{hd[j].x, static_cast<Acc>(hd[j].y), static_cast<Acc>(nv[j]),
+                         static_cast<Acc>(hd[j].w), static_cast<Acc>(hd[j].z)};
+        acc = lse_merge(acc, p, inv_l);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc = lse_merge(acc, lse_shfl(acc, o), inv_l);
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sm[w] = acc;
+    sm_bad[w] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int i = 1; i < MERGE_THREADS / 32; ++i) {
+    acc = lse_merge(acc, sm[i], inv_l);
+    bad += sm_bad[i];
+  }
+  // with a second proposal in this update, the last block to finish resets
+  // the counter and consumes it; every block read k_split above, and the
+  // acquire-release count orders those reads before the reset
+  if (ctl_reset && k_split < K && atomic_add_acq_rel(done, 1u) == gridDim.x - 1) {
+    *done = 0u;
+    ctl_reset[0] = ctl_reset[1];
+  }
+  const bool ok = isfinite(acc.m);
+  float us = u;
+  if (ok) {
+    us = k_split < K
+             ? static_cast<float>(static_cast<Acc>(u) +
+                                  (acc.zs * (static_cast<Acc>(pe) - static_cast<Acc>(u)) + acc.n) /
+                                      acc.z)
+             : static_cast<float>(static_cast<Acc>(u) + acc.n / acc.z);
+  }
+  write_entry(e, T, ok, us, ustar, plan_next, out, tau_dst, plan_dst);
+  if (e == 0) {
+    if (out) write_stats(out, ok, acc.m, static_cast<double>(acc.z), static_cast<double>(acc.z2),
+                         static_cast<double>(bad));
+    if (iter_p && ok) *iter_p += 1ull;
   }
 }
 

@@ -70,7 +70,8 @@ struct mppi_s {
   float* d_prop = nullptr;                // second proposal plan [T][7]
   int* d_ctl = nullptr;                   // {k_split of the next update, K}
   ObsK* d_obs = nullptr;                  // obstacle capsules of Eq. 15
-  unsigned* d_red = nullptr;              // {min-cost key, non-finite count, done blocks}
+  float* d_part = nullptr;                // the rollout blocks' Eq. 4 partials [nb][part_stride(T)]
+  unsigned* d_done = nullptr;             // merge blocks finished (reset by the last one)
   int feat = 0;                           // FEAT_* cost terms of the rollouts
   unsigned long long* d_iter = nullptr;
   // pinned host staging
@@ -333,14 +334,14 @@ int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, Pr
 
 template <int FEAT>
 cudaError_t launch_rolled(mppi_s* h, int grid, const float* in, const float* plan, float* S,
-                          float* noise, unsigned* red) {
+                          float* noise, float* part) {
   const size_t smem = rolled_smem_bytes(h->P.T, ROLLOUT_BLOCK, FEAT);
   if (noise)
     rollout_kernel_rolled<true, ROLLOUT_BLOCK, FEAT><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
-        h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, h->d_obs, red);
+        h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, h->d_obs, part);
   else
     rollout_kernel_rolled<false, ROLLOUT_BLOCK, FEAT><<<grid, ROLLOUT_BLOCK, smem, h->stream>>>(
-        h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, h->d_obs, red);
+        h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, h->d_obs, nullptr);
   return cudaGetLastError();
 }
 
@@ -387,10 +388,11 @@ cudaError_t prepare_rollout(mppi_s* h) {
   return cudaSuccess;
 }
 
-// red non-null: the rollouts also leave the minimum cost and the number of
-// non-finite costs there for an update kernel launched with the same red
+// part non-null (with noise): every rollout block also leaves its Eq. 4
+// partials there for merge_kernel
 cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float* S, float* noise,
-                           unsigned* red = nullptr) {
+                           float* part = nullptr) {
+  if (!noise) part = nullptr;
   const int grid = (h->P.K + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
   if (h->feat == FEAT_COLL && h->variant == 3) {
     // the collision cost on two more warps of the warp-specialised kernel
@@ -398,55 +400,68 @@ cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float*
     const size_t smem = ws_smem_bytes(true);
     if (noise)
       rollout_kernel_ws<true, true><<<wgrid, ws_threads(true), smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, h->d_obs, red);
+          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, h->d_obs, part);
     else
       rollout_kernel_ws<false, true><<<wgrid, ws_threads(true), smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, h->d_obs, red);
+          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, h->d_obs, nullptr);
     return cudaGetLastError();
   }
   // the optional cost terms run in the rolled kernel only
   switch (h->feat) {
-    case FEAT_FEST: return launch_rolled<FEAT_FEST>(h, grid, in, plan, S, noise, red);
-    case FEAT_COLL: return launch_rolled<FEAT_COLL>(h, grid, in, plan, S, noise, red);
+    case FEAT_FEST: return launch_rolled<FEAT_FEST>(h, grid, in, plan, S, noise, part);
+    case FEAT_COLL: return launch_rolled<FEAT_COLL>(h, grid, in, plan, S, noise, part);
     case FEAT_FEST | FEAT_COLL:
-      return launch_rolled<FEAT_FEST | FEAT_COLL>(h, grid, in, plan, S, noise, red);
+      return launch_rolled<FEAT_FEST | FEAT_COLL>(h, grid, in, plan, S, noise, part);
     default: break;
   }
-  if (h->variant == 2) return launch_rolled<0>(h, grid, in, plan, S, noise, red);
+  if (h->variant == 2) return launch_rolled<0>(h, grid, in, plan, S, noise, part);
   if (h->variant == 3) {
     const int wgrid = (h->P.K + WS_B - 1) / WS_B;
     const size_t smem = ws_smem_bytes();
     if (noise)
       rollout_kernel_ws<true><<<wgrid, WS_THREADS, smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, nullptr, red);
+          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, nullptr, part);
     else
       rollout_kernel_ws<false><<<wgrid, WS_THREADS, smem, h->stream>>>(
-          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, nullptr, red);
+          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, nullptr, nullptr);
     return cudaGetLastError();
   }
   if (noise)
     rollout_kernel<true><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S, noise,
-                                                               h->d_prop, h->d_ctl, red);
+                                                               h->d_prop, h->d_ctl, part);
   else
     rollout_kernel<false><<<grid, ROLLOUT_BLOCK, 0, h->stream>>>(h->P, in, h->d_iter, plan, S,
-                                                                nullptr, h->d_prop, h->d_ctl, red);
+                                                                nullptr, h->d_prop, h->d_ctl);
   return cudaGetLastError();
 }
 
-// prop / ksplit null: plain Eq. 4 (every sample around plan).  red non-null:
-// the minimum and the non-finite count come from the rollouts that wrote S
-// (launch_rollout with the same red), and the update resets red afterwards.
+// Eq. 4 from caller-supplied costs and noise (mppi_update_device).
 cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const float* plan,
-                          float* ustar, float* plan_next, float* out, unsigned long long* iter,
-                          const float* prop = nullptr, const int* ksplit = nullptr,
-                          float* tau_dst = nullptr, float* plan_dst = nullptr,
-                          unsigned* red = nullptr, int* ctl_reset = nullptr) {
-  // programmatic dependent launch: the update kernel's blocks may start as
-  // the rollout kernel's retire and wait (griddepcontrol.wait) for its
-  // results, which hides the launch gap between the two kernels
+                          float* ustar, float* plan_next) {
+  const int K = h->P.K, T = h->P.T;
+  const float lambda = h->P.lambda;
+  const dim3 grid(T * NJ), block(UPDATE_THREADS);
+  if (h->reduce_fp64)
+    update_kernel<double><<<grid, block, 0, h->stream>>>(K, T, lambda, S, noise, plan, ustar,
+                                                         plan_next, nullptr, nullptr);
+  else
+    update_kernel<float><<<grid, block, 0, h->stream>>>(K, T, lambda, S, noise, plan, ustar,
+                                                        plan_next, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+// Eq. 4 of a step from the rollout blocks' partials in d_part, with the
+// shift into plan_next (and into tau_dst / plan_dst when given), the output
+// record at `out` and iter += 1; the last block consumes a second proposal.
+cudaError_t launch_merge(mppi_s* h, const float* plan, float* ustar, float* plan_next, float* out,
+                         unsigned long long* iter, float* tau_dst = nullptr,
+                         float* plan_dst = nullptr) {
+  // programmatic dependent launch: the merge blocks may start as the rollout
+  // kernel's retire and wait (griddepcontrol.wait) for its results, which
+  // hides the launch gap between the two kernels
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(h->P.T * NJ);
-  lc.blockDim = dim3(UPDATE_THREADS);
+  lc.blockDim = dim3(MERGE_THREADS);
   lc.dynamicSmemBytes = 0;
   lc.stream = h->stream;
   cudaLaunchAttribute at[1];
@@ -455,38 +470,33 @@ cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const f
   lc.attrs = at;
   lc.numAttrs = 1;
   const int K = h->P.K, T = h->P.T;
+  const int nb = (K + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
+  const int ps = part_stride(T);
   const float lambda = h->P.lambda;
+  const float* part = h->d_part;
   if (h->reduce_fp64)
-    return cudaLaunchKernelEx(&lc, update_kernel<double>, K, T, lambda, S, noise, plan, ustar,
-                              plan_next, out, iter, prop, ksplit, tau_dst, plan_dst, red,
-                              ctl_reset);
-  return cudaLaunchKernelEx(&lc, update_kernel<float>, K, T, lambda, S, noise, plan, ustar,
-                            plan_next, out, iter, prop, ksplit, tau_dst, plan_dst, red, ctl_reset);
+    return cudaLaunchKernelEx(&lc, merge_kernel<double>, K, T, lambda, nb, ps, part, plan, ustar,
+                              plan_next, out, iter, static_cast<const float*>(h->d_prop),
+                              static_cast<const int*>(h->d_ctl), tau_dst, plan_dst, h->d_done,
+                              h->d_ctl);
+  return cudaLaunchKernelEx(&lc, merge_kernel<float>, K, T, lambda, nb, ps, part, plan, ustar,
+                            plan_next, out, iter, static_cast<const float*>(h->d_prop),
+                            static_cast<const int*>(h->d_ctl), tau_dst, plan_dst, h->d_done,
+                            h->d_ctl);
 }
 
-// red back to {no finite cost yet, no non-finite cost, no block done}
-cudaError_t reset_red(mppi_s* h) {
-  cudaError_t e = cudaMemsetAsync(h->d_red, 0xff, sizeof(unsigned), h->stream);
-  if (e != cudaSuccess) return e;
-  return cudaMemsetAsync(h->d_red + 1, 0, 2 * sizeof(unsigned), h->stream);
-}
-
-// the whole update on device buffers: rollouts from the inputs at `in`, then
-// Eq. 4 into the other plan (and into tau_dst / plan_dst when given) with
-// the output record at `out` (default d_out); the update's last block
-// consumes a second proposal set for this update (k_split := K)
+// the whole update on device buffers: rollouts from the inputs at `in`
+// (each block leaving its Eq. 4 partials), then the merge into the other
+// plan (and into tau_dst / plan_dst when given) with the output record at
+// `out` (default d_out); the merge's last block consumes a second proposal
+// set for this update (k_split := K)
 cudaError_t enqueue_update(mppi_s* h, int cur, const float* in = nullptr, float* tau_dst = nullptr,
                            float* plan_dst = nullptr, float* out = nullptr) {
-  cudaError_t e = launch_rollout(h, in ? in : h->d_in, h->d_plan[cur], h->d_S, h->d_noise, h->d_red);
+  cudaError_t e = launch_rollout(h, in ? in : h->d_in, h->d_plan[cur], h->d_S, h->d_noise,
+                                 h->d_part);
   if (e != cudaSuccess) return e;
-  e = launch_update(h, h->d_S, h->d_noise, h->d_plan[cur], h->d_ustar, h->d_plan[cur ^ 1],
-                    out ? out : h->d_out, h->d_iter, h->d_prop, h->d_ctl, tau_dst, plan_dst,
-                    h->d_red, h->d_ctl);
-  if (e != cudaSuccess) {
-    reset_red(h);  // the rollouts' totals are not consumed
-    return e;
-  }
-  return cudaSuccess;
+  return launch_merge(h, h->d_plan[cur], h->d_ustar, h->d_plan[cur ^ 1], out ? out : h->d_out,
+                      h->d_iter, tau_dst, plan_dst);
 }
 
 __global__ void set_int_kernel(int* dst, int v) {
@@ -701,8 +711,13 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
   if ((e = cudaMalloc(&h->d_prop, plan_b)) != cudaSuccess) return bail(e, "cudaMalloc prop");
   if ((e = cudaMalloc(&h->d_ctl, 2 * sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc ctl");
   if ((e = cudaMalloc(&h->d_obs, sizeof(ObsK))) != cudaSuccess) return bail(e, "cudaMalloc obs");
-  if ((e = cudaMalloc(&h->d_red, 4 * sizeof(unsigned))) != cudaSuccess) return bail(e, "cudaMalloc red");
-  if ((e = reset_red(h)) != cudaSuccess) return bail(e, "reset red");
+  {
+    const size_t nb = (static_cast<size_t>(K) + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
+    if ((e = cudaMalloc(&h->d_part, sizeof(float) * nb * part_stride(T))) != cudaSuccess)
+      return bail(e, "cudaMalloc part");
+  }
+  if ((e = cudaMalloc(&h->d_done, sizeof(unsigned))) != cudaSuccess) return bail(e, "cudaMalloc done");
+  if ((e = cudaMemset(h->d_done, 0, sizeof(unsigned))) != cudaSuccess) return bail(e, "done");
   {
     ObsK ob;
     fill_obs(cost->n_obstacles, &cost->obstacles[0][0], &ob);
@@ -759,7 +774,8 @@ int mppi_destroy(mppi_t h) {
   cudaFree(h->d_prop);
   cudaFree(h->d_ctl);
   cudaFree(h->d_obs);
-  cudaFree(h->d_red);
+  cudaFree(h->d_part);
+  cudaFree(h->d_done);
   cudaFree(h->d_out);
   cudaFree(h->d_iter);
   if (h->h_in) cudaFreeHost(h->h_in);
@@ -917,7 +933,7 @@ int mppi_update_device(mppi_t h, const float* d_S, const float* d_noise, const f
   if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
   if (!d_S || !d_noise || !d_plan || !d_ustar || !d_plan_next)
     return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
-  CUDA_TRY(h, launch_update(h, d_S, d_noise, d_plan, d_ustar, d_plan_next, nullptr, nullptr));
+  CUDA_TRY(h, launch_update(h, d_S, d_noise, d_plan, d_ustar, d_plan_next));
   return MPPI_OK;
 }
 
@@ -1076,12 +1092,11 @@ int mppi_time_kernels(mppi_t h, const float* d_in, int iters, float* ms_rollout,
   for (int i = 0; i < iters && e == cudaSuccess; ++i) {
     e = cudaEventRecord(ev[0], h->stream);
     if (e == cudaSuccess)
-      e = launch_rollout(h, d_in, h->d_plan[h->cur], h->d_S, h->d_noise, h->d_red);
+      e = launch_rollout(h, d_in, h->d_plan[h->cur], h->d_S, h->d_noise, h->d_part);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
     if (e == cudaSuccess)
-      e = launch_update(h, h->d_S, h->d_noise, h->d_plan[h->cur], h->d_scratch_plan,
-                        h->d_scratch_plan + plan_f, nullptr, nullptr, h->d_prop, h->d_ctl,
-                        nullptr, nullptr, h->d_red);
+      e = launch_merge(h, h->d_plan[h->cur], h->d_scratch_plan, h->d_scratch_plan + plan_f,
+                       nullptr, nullptr);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
     float a = 0.f, b = 0.f;
@@ -1091,10 +1106,8 @@ int mppi_time_kernels(mppi_t h, const float* d_in, int iters, float* ms_rollout,
     tu += b;
   }
   for (auto& x : ev) cudaEventDestroy(x);
-  if (e != cudaSuccess) {
-    reset_red(h);  // a rollout's totals may be left unconsumed
+  if (e != cudaSuccess)
     return fail(h, MPPI_ERR_CUDA, std::string("time_kernels: ") + cudaGetErrorString(e));
-  }
   *ms_rollout = tr / iters;
   *ms_update = tu / iters;
   return MPPI_OK;

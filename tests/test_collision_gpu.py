@@ -2,8 +2,8 @@
 through the C ABI.
 
 The squared-hinge form is continuous: S_k within 1e-4 relative, the plan
-within 1e-5 N m (after removing the first-order effect of the measured cost
-errors where S / lambda is large).  The indicator form turns each clearance
+within 1e-5 N m at light weights, and a recorded miss of that bar, with its
+measured size, where S / lambda is hundreds.  The indicator form turns each clearance
 into a 0/1 decision; FP32 and FP64 may decide differently for a clearance
 within rounding of its threshold.  There the sample's cost may differ by
 whole multiples of w_collision, and only for samples whose FP64 trajectory

@@ -66,11 +66,14 @@ def test_each_result_same_alone_and_in_the_mix(variant):
             assert rc1 == rc == mppi.OK
             assert np.array_equal(tau1, tau0) and np.array_equal(srv.get_plan(i), plan)
     # and alone on a single-problem handle (mppi_step).  The rolled and the
-    # warp-specialised serving kernels reproduce it bit for bit.  The register
+    # warp-specialised serving kernels reproduce its costs bit for bit; the
+    # handle sums Eq. 4 by rollout block and merges the blocks' log-sum-exp
+    # partials, the server walks all K samples per entry, so the two plans
+    # agree to the FP32 rounding of the weights (1e-6 N m).  The register
     # kernel is compiled twice under register pressure, and the two builds
     # contract FP32 multiply-adds differently; each result is within the plan
     # tolerance of the exact (FP64) update, so the two are within twice it.
-    tol = 2 * PLAN_TOL if variant == 1 else 0.0
+    tol = 2 * PLAN_TOL if variant == 1 else 1e-6
     for c, (rc, tau0), plan in zip(cases, res, plans):
         t_ref, p_ref, it = alone(c, variant)
         assert it == 1
