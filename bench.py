@@ -40,16 +40,28 @@ K_DEFAULT, T_DEFAULT, DT = 16384, 18, 0.01
 SIGMA, LAMBDA, SEED = 2.0, 1.0, 0xC0FFEE
 L2_FLUSH_BYTES = 256 << 20  # twice the 126 MB L2
 
-# FP32 floating-point operations of one rollout-step (one sample advanced by
-# one step: noise, kinematics, RNEA, CRBA, LDL^T solve, Euler step, contact
-# and costs) per cost workload: FADD + FMUL + 2 x FFMA executed by the
-# rollout kernel, counted by ncu
-# (smsp__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on) and divided
-# by K*T, on rollout_kernel_rolled at K=16384, T=18 (bench.py's own
-# workloads, two launches each).  The same count serves every kernel of a
-# workload: it is the method's arithmetic (the warp-specialised kernel
-# executes 4766 for contact and 6607 for collision: within 1 %).
-FLOP_PER_ROLLOUT_STEP = {"contact": 4808.1, "force_estimate": 6004.6, "collision": 6692.8}
+# Algorithmic FP32 operations of one rollout-step (one sample advanced by one
+# step) of the contact workload, counted by hand on the formulation the
+# kernels run (world-frame RNEA + CRBA + LDL^T; an FMA counts 2, structural
+# zeros are not counted, special functions - sin/cos, log, sqrt, atan2,
+# reciprocals - are listed apart and not counted):
+#   forward sweep, 7 links x 380 (frame 90, motion 48, inertia + force 242)
+#     + end-effector pose and velocity 75                             2735
+#   backward sweep: suffix sums 96, h 91, composite momenta 294, M 315  796
+#   LDL^T factor 154 + two triangular solves 91                          245
+#   contact force and tau_ext = J^T F_ext (contact active)               124
+#   running cost: motion 81, force 7, joint hinges 133, sum 2            223
+#   noise: Box-Muller arithmetic 76, v = u + sigma z 14                   90
+#   compensated Euler step (Eq. 7), 7 joints x 12                         84
+#   this block's share of Eq. 4 (N_b sums: 126 x 2 / 18)                  14
+#                                                                 total 4311
+# The term-by-term derivation is in the design notes.  The executed count of
+# the warp-specialised kernel (ncu FADD + FMUL + 2 FFMA, special functions'
+# polynomials included) is kept beside it.  The optional cost terms have no
+# hand count; their lines use the executed count and say so.
+FLOP_PER_ROLLOUT_STEP = {"contact": 4311.0}
+FLOP_EXECUTED_PER_ROLLOUT_STEP = {"contact": 4766.0, "force_estimate": 6004.6,
+                                  "collision": 6692.8}
 # DRAM read + write bytes of one rollout launch at K=16384, T=18 per (cost,
 # kernel) (ncu dram__bytes_{read,write}.sum, mean of two launches).  The
 # 8.3 MB of stored noise stays in L2 for update_kernel and is not written
@@ -72,6 +84,8 @@ def parse():
     ap.add_argument("--K", type=int, default=K_DEFAULT)
     ap.add_argument("--T", type=int, default=T_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="update mode: leave out the compact serving measurement")
     ap.add_argument("--budget-s", type=float, default=120.0,
                     help="reference arm: wall-clock budget of the whole run [s]")
     ap.add_argument("--variant", type=int, default=0,
@@ -361,7 +375,12 @@ def run_ours(args, rank, world):
             raise RuntimeError(f"update failed with status {rc}")
         step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
         mean_ms = float(step_ms.mean())
-        launches = 2 * args.steps  # rollout_kernel + update_kernel per update
+        launches = 2 * args.steps  # rollout kernel + merge kernel per update
+
+        # --- latency: the update's p50/p99 over at least LAT_UPDATES updates
+        #     and LAT_SECONDS of wall time (so that the clock samples cover
+        #     it), after LAT_WARMUP warm-ups, L2 flushed before each update
+        lat_ms = latency_loop(ctl, d_in, d_tau, d_plan, flush, stream, barrier, clk, spans)
 
         # --- per-kernel times for the roofline (events on the library stream)
         ms_roll, ms_upd = ctl.time_kernels(d_in, 200)
@@ -372,7 +391,7 @@ def run_ours(args, rank, world):
         barrier()
         a = clk.mark()
         e2e_ms = []
-        for _ in range(args.steps):
+        for _ in range(max(args.steps, LAT_UPDATES)):
             flush.zero_()  # L2 flushed before every timed call, as above
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -383,69 +402,110 @@ def run_ours(args, rank, world):
     e2e_ms = np.array(e2e_ms)
 
     # --- aggregate over ranks -------------------------------------------------
-    total_ms, e2e_total = max_over_ranks([float(step_ms.sum()), float(e2e_ms.sum())], world,
-                                         "cuda")
+    total_ms, e2e_mean = max_over_ranks([float(step_ms.sum()), float(e2e_ms.mean())], world,
+                                        "cuda")
     units = K * T * args.steps * world
     value = units / (total_ms * 1e-3)
-    e2e_value = units / (e2e_total * 1e-3)
+    e2e_value = K * T * world / (e2e_mean * 1e-3)
 
     if rank != 0:
         ctl.close()
         return
     clocks = clk.summary(spans)
-    sm_mhz = clocks.get("sm_mhz") or 2032.0
     peak_max = SM_COUNT * FP32_LANES_PER_SM * 2 * 2032e6 / 1e12
-    roof = None
-    flop = FLOP_PER_ROLLOUT_STEP[args.cost]
-    if flop:
-        achieved = flop * K * T / (ms_roll * 1e-3) / 1e12
-        traffic = (ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH.get((args.cost, kname))
-                   if (K, T) == (K_DEFAULT, T_DEFAULT) else None)
-        fma = mppi.measure_fp32_peak()  # outside the timed regions
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
-                "frac": achieved / peak_max, "traffic": traffic,
-                "kernel": kname, "kernel_ms": ms_roll,
-                "peak_note": "FP32 peak of 148 SMs x 128 lanes x 2 FLOP at the 2032 MHz "
-                             "maximum SM clock (derived; no measured FP32 peak is on file); "
-                             "peak_fma_measured: independent FMA chains on every SM of this "
-                             "GPU, median of five launches",
-                "peak_fma_measured": fma, "frac_of_fma_measured": achieved / fma}
+    flop = FLOP_PER_ROLLOUT_STEP.get(args.cost)
+    flop_exec = FLOP_EXECUTED_PER_ROLLOUT_STEP[args.cost]
+    num = flop if flop else flop_exec
+    achieved = num * K * T / (ms_roll * 1e-3) / 1e12
+    traffic = (ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH.get((args.cost, kname))
+               if (K, T) == (K_DEFAULT, T_DEFAULT) else None)
+    fma = mppi.measure_fp32_peak()  # outside the timed regions
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
+            "frac": achieved / peak_max, "traffic": traffic,
+            "kernel": kname, "kernel_ms": ms_roll,
+            "flop_per_rollout_step": num,
+            "flop_source": ("algorithmic, counted by hand on the formulation" if flop else
+                            "executed (ncu FADD + FMUL + 2 FFMA); no hand count for this cost"),
+            "flop_executed_per_rollout_step": flop_exec,
+            "frac_executed": flop_exec * K * T / (ms_roll * 1e-3) / 1e12 / peak_max,
+            "peak_note": "FP32 peak of 148 SMs x 128 lanes x 2 FLOP at the 2032 MHz "
+                         "maximum SM clock (derived; no measured FP32 peak is on file); "
+                         "peak_fma_measured: independent FMA chains on every SM of this "
+                         "GPU, median of five launches",
+            "peak_fma_measured": fma, "frac_of_fma_measured": achieved / fma}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(K, T, world, args.cost),
-            "p50_ms": float(np.percentile(step_ms, 50)),
-            "p99_ms": float(np.percentile(step_ms, 99)),
+            "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)),
+            "latency": {"updates": int(lat_ms.size), "warmup": LAT_WARMUP,
+                        "mean_ms": float(lat_ms.mean()), "p50_ms": float(np.percentile(lat_ms, 50)),
+                        "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(lat_ms.max()),
+                        "timing": "CUDA events around each update on the library's stream, "
+                                  "L2 flushed before each"},
             "update_hz": 1e3 / mean_ms,
-            "kernels_ms": {kname: ms_roll, "update_kernel": ms_upd},
+            "kernels_ms": {kname: ms_roll, "merge_kernel": ms_upd},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 25 * 4,
-                    "d2h_bytes_per_step": (16 + T * 7) * 4,
+                    "d2h_bytes_per_step": (16 + T * 7) * 4, "calls": int(e2e_ms.size),
                     "p50_ms": float(np.percentile(e2e_ms, 50)),
                     "p99_ms": float(np.percentile(e2e_ms, 99)),
                     "api": "mppi_step (host buffers, CUDA graph replay: H2D copy of the "
-                           "inputs, two kernels, the update kernel writing tau0, status and "
-                           "plan into pinned host memory)"},
+                           "inputs, two kernels, the merge kernel writing tau0, status and "
+                           "plan into pinned host memory), host clock per call"},
             "roofline": roof,
             "clocks": clocks,
             "gpu_launches": launches,
             "wall_s": t_wall}
+    ctl.close()
+    if not args.no_serve:
+        line["serve"] = serve_summary(rank)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(K, T, cost_name=args.cost)
-    ctl.close()
     print(json.dumps(line), flush=True)
 
 
+LAT_UPDATES, LAT_WARMUP, LAT_SECONDS = 1000, 50, 1.2
 
-def run_serve(args, rank, world):
-    """Batched serving: many problems with uneven K and T, Poisson arrivals,
-    memory-based admission, continuous batching (include/mppi_serve.h)."""
+
+def latency_loop(ctl, d_in, d_tau, d_plan, flush, stream, barrier, clk, spans):
+    """Device time of single updates (events around each on the library's
+    stream, L2 flushed before each): at least LAT_UPDATES updates and
+    LAT_SECONDS of wall time after LAT_WARMUP warm-ups; returns ms per update."""
     import torch
+    for _ in range(LAT_WARMUP):
+        ctl.step_device(d_in, d_tau, d_plan)
+    barrier()
+    a = clk.mark()
+    out = []
+    t_end = time.perf_counter() + LAT_SECONDS
+    while len(out) < LAT_UPDATES or time.perf_counter() < t_end:
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(250)]
+        for st, en in ev:
+            flush.zero_()
+            st.record(stream)
+            ctl.step_device(d_in, d_tau, d_plan)
+            en.record(stream)
+        torch.cuda.synchronize()
+        out.extend(st.elapsed_time(en) for st, en in ev)
+    barrier()
+    spans.append((a, clk.mark()))
+    if ctl.sync() != 0:
+        raise RuntimeError("update failed in the latency loop")
+    return np.array(out)
+
+
+SERVE_RATES = (10_000.0, 60_000.0)  # below and above the 256-problem mix's capacity
+SERVE_SECONDS = 1.0
+
+
+def serve_server(rank, n, pool_mb):
+    """The batched-serving workload: n seeded problems, uneven K and T, half
+    with plane contact; returns (server, all scratch bytes)."""
     from paper_2609_02020_b300 import mppi, synth
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    n = args.problems
     Ks, Ts = synth.serving_mix(17 + rank, n)
-    srv = mppi.Server(pool_bytes=args.pool_mb << 20, max_problems=n, max_batch=min(n, 1024),
-                      lanes=3)
+    srv = mppi.Server(pool_bytes=pool_mb << 20, max_problems=n, max_batch=min(n, 1024), lanes=3)
     total_scratch = 0
     for i in range(n):
         arm = synth.arm(10_000 * rank + i)
@@ -458,6 +518,43 @@ def run_serve(args, rank, world):
         srv.set_input(pid, mppi.pack_inputs(q, qd, goal, plane if not cost["contact"] else
                                             np.array([0.0, 0.0, 1.0, -10.0])))
         total_scratch += 4 * int(Ks[i]) * (7 * int(Ts[i]) + 1)
+    return srv, total_scratch
+
+
+def serve_summary(rank, n=256, pool_mb=1024):
+    """Compact serving measurement for the update line: the 256-problem mix
+    under Poisson arrivals for SERVE_SECONDS at 10 k/s and at a saturating
+    60 k/s (latency = completion minus scheduled arrival, host clock)."""
+    t0 = time.perf_counter()
+    srv, scratch = serve_server(rank, n, pool_mb)
+    best = srv.autotune()
+    st = srv.stats()
+    srv.start()
+    setup = time.perf_counter() - t0
+    pts = []
+    for rate in SERVE_RATES:
+        r = srv.load_test(rate, SERVE_SECONDS, seed=int(rate))
+        pts.append({"rate_hz": rate, "p50_ms": float(r["p50_ms"]), "p99_ms": float(r["p99_ms"]),
+                    "updates_per_s": float(r["updates_per_s"]),
+                    "rollout_steps_per_s": float(r["rollout_steps_per_s"]),
+                    "mean_batch": float(r["mean_batch"]), "completed": int(r["completed"])})
+    srv.stop()
+    srv.close()
+    return {"workload": f"{n} seeded 7-DoF problems, K~U{{512..8192}}, T~U{{10..50}}, half with "
+                        "plane contact, Poisson arrivals",
+            "seconds_per_rate": SERVE_SECONDS, "setup_s": setup,
+            "autotune": {"variant": st["variant"], "tile": st["block"], "rollout_ms": best},
+            "points": pts}
+
+
+def run_serve(args, rank, world):
+    """Batched serving: many problems with uneven K and T, Poisson arrivals,
+    memory-based admission, continuous batching (include/mppi_serve.h)."""
+    import torch
+    from paper_2609_02020_b300 import mppi, synth
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n = args.problems
+    srv, total_scratch = serve_server(rank, n, args.pool_mb)
     best = srv.autotune()
     st = srv.stats()
     srv.start()
