@@ -326,10 +326,14 @@ MPPI_API int mppi_noise_words(mppi_t h, uint64_t iter, uint32_t k0, int count, u
  * for callers that cannot allocate device memory while they run, such as a
  * hard-real-time control thread (cudaMalloc may block on the device and has
  * no latency bound) or a plug-in whose host application owns all device
- * memory through its own pool.  It runs one update (rollouts, Eq. 4 and the
- * shift) like mppi_step_device, without a handle and without any allocation:
+ * memory through its own pool.  It runs one update (the rollouts, the
+ * weighted update of the plan and the shift, as mppi_step_device does),
+ * without a handle and without any allocation:
  *   robot, cost, cfg: as for mppi_create (host records, copied per call);
  *     cfg->K must be <= MPPI_STATIC_K_MAX, else MPPI_ERR_INVALID_ARG;
+ *     cfg->reduce_fp64 selects FP32 or FP64 sums over K as for a handle;
+ *     the rollouts always run the register kernel, so cfg->variant must be
+ *     0 or 1 (else MPPI_ERR_INVALID_ARG); neither optional cost term;
  *   iter: the update counter used in the Philox counter;
  *   d_in: 25 device floats (q, qd, goal, plane); d_plan: nominal plan [T][7];
  *   d_ustar, d_plan_next: device outputs [T][7] (u* and the shifted plan;
@@ -343,7 +347,9 @@ MPPI_API int mppi_noise_words(mppi_t h, uint64_t iter, uint32_t k0, int count, u
  * GPU (different streams, or different host threads, on the same device)
  * race and must be serialised by the caller.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Errors
+ * device current; make that first call before any stream capture.  The
+ * address is kept for the process, so the entry point must not be used
+ * across a cudaDeviceReset of that device.  Errors
  * are reported by the return code, with the message in
  * mppi_last_error(NULL). */
 #define MPPI_STATIC_K_MAX 65536

@@ -69,14 +69,17 @@ __global__ void static_set_iter_kernel(StaticScratch* sc, unsigned long long ite
   if (threadIdx.x == 0 && blockIdx.x == 0) sc->iter = iter;
 }
 
-// Eq. 4a-4b and the shift for plan entry e = blockIdx.x with the noise
-// regenerated instead of read back (same reductions as update_kernel).
+// The weighted update of the plan and the shift for plan entry e =
+// blockIdx.x, with the noise regenerated instead of read back: the weights
+// exp(-(S_k - S_min) / lambda) in FP32, their sums in Acc (float, or double
+// when cfg->reduce_fp64 asks for it, as for a handle).
+template <typename Acc>
 __global__ void __launch_bounds__(UPDATE_BLOCK)
 update_regen_kernel(const __grid_constant__ ProbK P, const StaticScratch* __restrict__ sc,
                     const float* __restrict__ plan, float* __restrict__ ustar,
                     float* __restrict__ plan_next) {
   __shared__ float sm_f[32];
-  __shared__ float sm_a[3 * 32];
+  __shared__ Acc sm_a[3 * 32];
   const int K = P.K, T = P.T;
   const int e = blockIdx.x;
   const int t = e / NJ, j = e % NJ;
@@ -89,23 +92,23 @@ update_regen_kernel(const __grid_constant__ ProbK P, const StaticScratch* __rest
   }
   m = block_min<UPDATE_BLOCK>(m, sm_f);
   const bool ok = isfinite(m);
-  float z = 0.f, z2 = 0.f, nacc = 0.f;
+  Acc z = Acc(0), z2 = Acc(0), nacc = Acc(0);
   if (ok) {
     const float inv_l = 1.0f / P.lambda;
     for (int k = threadIdx.x; k < K; k += UPDATE_BLOCK) {
       const float s = S[k];
-      const float w = isfinite(s) ? expf((m - s) * inv_l) : 0.f;
+      const Acc w = static_cast<Acc>(isfinite(s) ? expf((m - s) * inv_l) : 0.f);
       z += w;
       z2 += w * w;
-      nacc += w * regen_noise(P.key0, P.key1, iter, static_cast<uint32_t>(k),
-                              static_cast<uint32_t>(t), j, P.sigma[j]);
+      nacc += w * static_cast<Acc>(regen_noise(P.key0, P.key1, iter, static_cast<uint32_t>(k),
+                                               static_cast<uint32_t>(t), j, P.sigma[j]));
     }
   }
   block_sum3<UPDATE_BLOCK>(z, z2, nacc, sm_a);
   if (threadIdx.x != 0) return;
   const float u = plan[e];
   if (ok) {
-    const float us = u + nacc / z;
+    const float us = static_cast<float>(static_cast<Acc>(u) + nacc / z);
     ustar[e] = us;
     if (t >= 1) plan_next[e - NJ] = us;
     if (t == T - 1) plan_next[e] = us;
@@ -115,7 +118,10 @@ update_regen_kernel(const __grid_constant__ ProbK P, const StaticScratch* __rest
   }
 }
 
-// Looks up (once per device) the device address of the static scratch.
+// Looks up (once per device) the device address of the static scratch.  The
+// address belongs to the device's primary context as it was at the lookup;
+// a cudaDeviceReset ends that context, so the entry point is not for use
+// across a device reset.
 int scratch_for_current_device(StaticScratch** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -144,6 +150,9 @@ int mppi_step_static(const mppi_robot* robot, const mppi_cost* cost, const mppi_
     return fail(MPPI_ERR_INVALID_ARG, "null argument");
   if (cfg->K > MPPI_STATIC_K_MAX)
     return fail(MPPI_ERR_INVALID_ARG, "K exceeds MPPI_STATIC_K_MAX (65536) for mppi_step_static");
+  if (cfg->variant != 0 && cfg->variant != 1)
+    return fail(MPPI_ERR_INVALID_ARG,
+                "mppi_step_static runs the register rollout kernel: variant must be 0 or 1");
   ProbK P;
   std::string why;
   if (mppi_convert_params(robot, cost, cfg, &P, &why) != 0) return fail(MPPI_ERR_INVALID_ARG, why);
@@ -157,7 +166,10 @@ int mppi_step_static(const mppi_robot* robot, const mppi_cost* cost, const mppi_
   static_set_iter_kernel<<<1, 32, 0, st>>>(sc, static_cast<unsigned long long>(iter));
   const int grid = (P.K + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
   rollout_kernel<false><<<grid, ROLLOUT_BLOCK, 0, st>>>(P, d_in, &sc->iter, d_plan, sc->S, nullptr);
-  update_regen_kernel<<<P.T * NJ, UPDATE_BLOCK, 0, st>>>(P, sc, d_plan, d_ustar, d_plan_next);
+  if (cfg->reduce_fp64)
+    update_regen_kernel<double><<<P.T * NJ, UPDATE_BLOCK, 0, st>>>(P, sc, d_plan, d_ustar, d_plan_next);
+  else
+    update_regen_kernel<float><<<P.T * NJ, UPDATE_BLOCK, 0, st>>>(P, sc, d_plan, d_ustar, d_plan_next);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(MPPI_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
   return MPPI_OK;

@@ -519,13 +519,16 @@ class MPPI:
 
 
 def step_static(robot: dict, cost: dict, *, dt: float, T: int, K: int, lam: float, sigma,
-                seed: int, it: int, d_in, d_plan, d_ustar, d_plan_next, stream=None) -> None:
+                seed: int, it: int, d_in, d_plan, d_ustar, d_plan_next, stream=None,
+                reduce_fp64: bool = False, variant: int = 0) -> None:
     """mppi_step_static: one update without any device allocation (torch
     CUDA tensors in and out; queued on `stream`, torch's current stream when
     None)."""
     L = load()
     cfg = Config()
     cfg.dt, cfg.T, cfg.K, cfg.lambda_ = float(dt), int(T), int(K), float(lam)
+    cfg.reduce_fp64 = int(bool(reduce_fp64))
+    cfg.variant = int(variant)
     s = np.broadcast_to(np.asarray(sigma, dtype=np.float64), (NJ,))
     for j in range(NJ):
         cfg.sigma[j] = float(s[j])
