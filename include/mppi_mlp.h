@@ -7,8 +7,9 @@
  * produce, and the update samples around that prediction.  The network is
  *   x (n_in) -> [Linear -> GELU] x n_layers (width n_hidden) -> Linear (n_out)
  * with BF16 weights and activations and FP32 accumulation on the tensor
- * cores (mma.sync m16n8k16), FP32 master weights and Adam.  Inputs and
- * outputs are standardised with fixed per-feature means and deviations.
+ * cores (tcgen05.mma into tensor memory, operands staged by TMA), FP32
+ * master weights and Adam.  Inputs and outputs are standardised with fixed
+ * per-feature means and deviations.
  * The loss is the mean squared error of the standardised outputs.
  * Parameters are flat FP32: W_1 [n_hidden][n_in] row-major, b_1, W_2, b_2,
  * ..., W_L [n_out][n_hidden], b_L.  All device pointers are caller-owned
@@ -54,7 +55,9 @@ MPPI_API int mppi_mlp_forward(mppi_mlp_t m, const float* d_x, int n, float* d_y)
 MPPI_API int mppi_mlp_loss_grad(mppi_mlp_t m, const float* d_x, const float* d_y, int n,
                                 float* loss, float* grad_host);
 /* One Adam step (learning rate lr) on n rows; *loss (may be NULL: no wait)
- * receives the batch loss before the step. */
+ * receives the batch loss before the step.  The calls that wait (loss_grad,
+ * train_step with a loss) return MPPI_ERR_TIMEOUT if a tensor-core GEMM
+ * gave up waiting for its operands (a bounded wait; the work is skipped). */
 MPPI_API int mppi_mlp_train_step(mppi_mlp_t m, const float* d_x, const float* d_y, int n,
                                  float lr, float* loss);
 /* Learned proposal for an MPPI handle: x = (q, qd, goal from d_in [25
@@ -62,10 +65,11 @@ MPPI_API int mppi_mlp_train_step(mppi_mlp_t m, const float* d_x, const float* d_
  * predicts the correction that plain MPPI would make to u, and u + net(x)
  * is installed as the second proposal of the handle's next update with
  * n_plain samples kept around the plain warm start (mppi_set_proposal_device;
- * n_plain = 0 samples only around the network's plan).  Queued on the
- * handle's stream; the network's buffers must not be in use by a training
- * step at the same time.  Needs n_in = 21 + 7T and n_out = 7T, at most 3
- * hidden layers and widths <= 256 (MPPI_ERR_INVALID_ARG otherwise). */
+ * n_plain = 0 samples only around the network's plan).  One launch of a
+ * cluster of 8 CTAs, queued on the handle's stream; it reads the network's
+ * weights, which a training step must not be changing at the same time.
+ * Needs n_in = 21 + 7T and n_out = 7T, at most 3 hidden layers and widths
+ * <= 256 (MPPI_ERR_INVALID_ARG otherwise). */
 MPPI_API int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain);
 
 #ifdef __cplusplus
