@@ -101,7 +101,7 @@ def parse():
                          "learned proposal and compare it with plain MPPI; sweep: the update "
                          "over K x T with FP32 and FP64 reductions")
     ap.add_argument("--pairs", type=int, default=200_000, help="learned mode: training pairs")
-    ap.add_argument("--train-steps", type=int, default=12_000, help="learned mode: Adam steps")
+    ap.add_argument("--train-steps", type=int, default=3000, help="learned mode: Adam steps")
     ap.add_argument("--episodes", type=int, default=12, help="learned mode: eval episodes")
     ap.add_argument("--rates", default="2000,5000,10000,20000,100000",
                     help="serve mode: arrival rates [updates/s]")
@@ -647,45 +647,71 @@ def run_sweep(args, rank, world):
 
 
 def run_learned(args, rank, world):
-    """Learned proposal: pairs from plain MPPI at K=16384, training on the GPU
-    with the library's BF16 tensor-core kernels, then closed-loop tracking
-    cost and update latency of plain MPPI (K=16384 and fewer samples) and of
-    MPPI with the learned proposal."""
+    """Learned proposal on the reaching task where plain MPPI at K=16384
+    converges (learned.tracking_problem): pairs from plain MPPI at K=16384,
+    training on the GPU with the library's tcgen05 BF16 kernels, then
+    closed-loop tracking cost, final position error and update latency of
+    plain MPPI (K=16384 and fewer samples) and of MPPI with the learned
+    proposal."""
     import torch
-    from paper_2609_02020_b300 import learned, synth
+    from paper_2609_02020_b300 import learned, mppi, synth
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    cost = synth.cost_free_space()
-    cost["w_pos"] = np.full(3, 100.0)
-    cost["w_ori"] = np.full(3, 10.0)
-    prob = learned.Problem(arm=synth.arm(rank), cost=cost)
+    prob = learned.tracking_problem(rank)
     s = torch.cuda.Stream()
     t0 = time.perf_counter()
-    X, Y = learned.generate(prob, args.pairs, K=16384, seed=rank, stream=s)
+    X, Y = learned.generate(prob, args.pairs, K=16384, seed=rank, episode_len=1000, stream=s)
     t_gen = time.perf_counter() - t0
     net, info = learned.train(X, Y, steps=args.train_steps, batch=1024, lr=1e-3, stream=s)
+    dims = [X.shape[1], 256, 256, 256, Y.shape[1]]
+    flop_step = 3 * 2 * sum(dims[i] * dims[i + 1] for i in range(4)) * 1024
+    # the proposal kernel alone: events around single launches on the handle's stream
+    ctl = prob.controller(512, seed=1, stream=s)
+    q, qd, goal = prob.episode_start(123, ctl)
+    d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, prob.plane), device="cuda")
+    for _ in range(20):
+        net.propose(ctl, d_in, 256)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(500)]
+    for a, b in ev:
+        a.record(s)
+        net.propose(ctl, d_in, 256)
+        b.record(s)
+    s.synchronize()
+    prop_us = np.array([a.elapsed_time(b) for a, b in ev]) * 1e3
+    ctl.close()
     rows = []
     for name, K, mk in (
-            [("plain", 16384, lambda K: learned.PlainMPPI(prob, K, seed=5, stream=s))] +
-            [("plain", K, lambda K: learned.PlainMPPI(prob, K, seed=5, stream=s)) for K in (512, 2048, 4096)] +
-            [("learned", K, lambda K: learned.LearnedMPPI(prob, net, K, seed=5, stream=s))
-             for K in (512, 2048, 4096)]):
+            [("plain", K, lambda K: learned.PlainMPPI(prob, K, seed=5, stream=s))
+             for K in (16384, 512, 2048)] +
+            [("learned", K, lambda K: learned.LearnedMPPI(prob, net, K, seed=5, stream=s,
+                                                           plain_frac=0.5))
+             for K in (512, 2048)]):
         c = mk(K)
-        r = learned.evaluate(prob, c, episodes=args.episodes, steps=150, seed=1, stream=s)
+        r = learned.evaluate(prob, c, episodes=args.episodes, steps=1000, seed=1, stream=s)
         c.close()
         r.pop("tracking_cost_per_episode")
         rows.append({"controller": name, "K": K, **r})
     if rank == 0:
         print(json.dumps({
             "mode": "learned",
-            "metric": "closed-loop tracking cost and update latency, learned proposal vs plain MPPI",
-            "unit": "cost (mean of W_pos|dp|^2 + W_ori theta^2) / ms", "n_gpus": world,
+            "metric": "closed-loop tracking cost, final error and update latency, learned "
+                      "proposal vs plain MPPI",
+            "unit": "cost (mean of W_pos|dp|^2) / m / ms", "n_gpus": world,
             "dtype": "f32 rollouts, bf16 network", "data": "synthetic",
-            "config": {"workload": "7-DoF seeded arm, reachable goals, gravity-compensated start, "
-                                   "T=18 dt=0.01, W_pos=100, W_ori=10, 150-step episodes",
+            "config": {"workload": "7-DoF seeded gravity-compensated arm (damping 5), "
+                                   "position-only goals 0.2 rad per joint away, W_pos=300, "
+                                   "sigma=2, lambda=3, T=18 dt=0.01, 1000-step (10 s) episodes",
                        "pairs": args.pairs, "pairs_K": 16384,
-                       "network": "147 -> 3 x 256 GELU -> 126, BF16 mma.sync, FP32 accumulate",
-                       "plain_fallback_fraction": 0.25},
-            "generation_s": t_gen, "training": {k: v for k, v in info.items()},
+                       "network": "147 -> 3 x 256 GELU -> 126, BF16 tcgen05, FP32 accumulate",
+                       "plain_fallback_fraction": 0.5},
+            "generation_s": t_gen,
+            "training": {**{k: v for k, v in info.items()},
+                         "gflop_per_step": flop_step / 1e9,
+                         "tflops": flop_step * info["steps"] / info["seconds"] / 1e12,
+                         "frac_of_bf16_peak": flop_step * info["steps"] / info["seconds"] / 1e12
+                                              / 1786.4},
+            "propose_kernel_us": {"p50": float(np.percentile(prop_us, 50)),
+                                  "p99": float(np.percentile(prop_us, 99))},
             "rows": rows}), flush=True)
 
 

@@ -288,6 +288,14 @@ MPPI_API int mppi_set_obstacles_device(mppi_t h, int n, const float* d_obs);
 MPPI_API int mppi_force_estimate_device(mppi_t h, const float* d_q, const float* d_v, int n,
                                         float* d_F);
 
+/* The correction the last update made to its nominal plan, u* - u [T][7]
+ * (Eq. 4b's weighted noise sum, plus the second proposal's share when one
+ * was set), into the caller's device array d_out; queued on the handle's
+ * stream.  Before any update it is u* - u of the initial buffers (zero).
+ * For building training pairs of a learned proposal; the paper has no
+ * counterpart. */
+MPPI_API int mppi_get_correction_device(mppi_t h, float* d_out);
+
 /* The rollout kernel the handle runs (1, 2 or 3 as in mppi_config.variant;
  * variant 0 resolves at creation: with the wrench-estimate cost the rolled
  * kernel; otherwise the warp-specialised kernel while its blocks for K

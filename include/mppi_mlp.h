@@ -48,6 +48,12 @@ MPPI_API int mppi_mlp_set_params(mppi_mlp_t m, const float* host);
 /* Per-feature standardisation (host arrays; deviations must be > 0). */
 MPPI_API int mppi_mlp_set_normalization(mppi_mlp_t m, const float* mean_in, const float* std_in,
                                         const float* mean_out, const float* std_out);
+/* The standardisation fitted to training data on the device: per-feature
+ * means and deviations (unbiased, FP64 sums) of d_x [n][n_in] and d_y
+ * [n][n_out], deviations below floor raised to it (floor > 0, n >= 2);
+ * blocks until done. */
+MPPI_API int mppi_mlp_fit_normalization(mppi_mlp_t m, const float* d_x, const float* d_y, int n,
+                                        float floor);
 /* y = net(x) for n rows of raw inputs d_x [n][n_in]; raw outputs d_y [n][n_out]. */
 MPPI_API int mppi_mlp_forward(mppi_mlp_t m, const float* d_x, int n, float* d_y);
 /* Loss and gradient for n rows (d_y: raw targets); grad_host (num_params

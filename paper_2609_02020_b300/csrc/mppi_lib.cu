@@ -559,6 +559,7 @@ int mppi_internal_T(mppi_t h) { return h->P.T; }
 cudaStream_t mppi_internal_stream(mppi_t h) { return h->stream; }
 float* mppi_internal_prop(mppi_t h) { return h->d_prop; }
 int mppi_internal_K(mppi_t h) { return h->P.K; }
+int* mppi_internal_ctl(mppi_t h) { return h->d_ctl; }
 cudaError_t mppi_internal_set_split(mppi_t h, int k_split) {
   set_int_kernel<<<1, 32, 0, h->stream>>>(h->d_ctl, k_split);
   return cudaGetLastError();
@@ -1003,6 +1004,23 @@ int mppi_get_updated_plan_device(mppi_t h, float* d_u) {
   if (!h || !d_u) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
   CUDA_TRY(h, cudaMemcpyAsync(d_u, h->d_ustar, sizeof(float) * h->P.T * NJ,
                               cudaMemcpyDeviceToDevice, h->stream));
+  return MPPI_OK;
+}
+
+// out[e] = ustar[e] - nominal[e]
+__global__ void correction_kernel(const float* __restrict__ ustar, const float* __restrict__ nominal,
+                                  int n, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = ustar[i] - nominal[i];
+}
+
+int mppi_get_correction_device(mppi_t h, float* d_out) {
+  if (!h || !d_out) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  // the last update read its nominal plan from the buffer it did not write
+  const int n = h->P.T * NJ;
+  correction_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>(h->d_ustar, h->d_plan[h->cur ^ 1], n,
+                                                            d_out);
+  CUDA_TRY(h, cudaGetLastError());
   return MPPI_OK;
 }
 

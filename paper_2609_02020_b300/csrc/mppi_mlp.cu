@@ -35,7 +35,7 @@ int mppi_internal_T(mppi_t h);
 cudaStream_t mppi_internal_stream(mppi_t h);
 float* mppi_internal_prop(mppi_t h);
 int mppi_internal_K(mppi_t h);
-cudaError_t mppi_internal_set_split(mppi_t h, int k_split);
+int* mppi_internal_ctl(mppi_t h);
 
 namespace {
 
@@ -97,6 +97,45 @@ __global__ void loss_grad_kernel(const float* __restrict__ y, const float* __res
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
   if ((threadIdx.x & 31) == 0 && e2 != 0.f) atomicAdd(loss, e2 / (static_cast<float>(n) * d));
+}
+
+// Per-column mean and deviation (unbiased) of X [n][d] in FP64, two passes;
+// deviations below floor are raised to it.  One block per column.
+__global__ void colstats_kernel(const float* __restrict__ X, int n, int d, float floor,
+                                float* __restrict__ mean, float* __restrict__ sd) {
+  const int f = blockIdx.x;
+  __shared__ double part[8];
+  __shared__ double s_mean;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += X[static_cast<long long>(i) * d + f];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += part[w];
+    s_mean = t / n;
+  }
+  __syncthreads();
+  const double mu = s_mean;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double e = X[static_cast<long long>(i) * d + f] - mu;
+    v += e * e;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += part[w];
+    const double sdv = n > 1 ? sqrt(t / (n - 1)) : 0.0;
+    mean[f] = static_cast<float>(mu);
+    sd[f] = fmaxf(static_cast<float>(sdv), floor);
+  }
 }
 
 // y = yn * std + mean (in place allowed)
@@ -168,6 +207,8 @@ struct ProposeArgs {
   int L;
   const float *mean_in, *sd_in, *mean_out, *sd_out;
   float* dst;           // [n_out]
+  int* k_split;         // the handle's k_split of its next update
+  int n_plain;
 };
 
 __device__ __forceinline__ void cluster_sync_all() {
@@ -195,6 +236,20 @@ propose_kernel(const ProposeArgs a) {
                                                           col * a.ldw[l + 1]) + lane);
       }
     }
+  // the biases of this warp's columns and the output layer's constants,
+  // also before the first layer (lane 0 uses them)
+  float bias[PC_LMAX][PC_COLS], oplan[PC_COLS], omean[PC_COLS], osd[PC_COLS];
+#pragma unroll
+  for (int c = 0; c < PC_COLS; ++c) {
+    const int col = static_cast<int>(rank) * (PC_COLS * PC_THREADS / 32) + warp * PC_COLS + c;
+#pragma unroll
+    for (int l = 0; l < PC_LMAX; ++l)
+      bias[l][c] = (l < a.L && col < a.dims[l + 1]) ? __ldg(a.p + a.boff[l + 1] + col) : 0.f;
+    const bool oc = col < a.dims[a.L];
+    oplan[c] = oc ? a.plan[col] : 0.f;
+    omean[c] = oc ? __ldg(a.mean_out + col) : 0.f;
+    osd[c] = oc ? __ldg(a.sd_out + col) : 0.f;
+  }
   const int n0 = a.dims[0];
   for (int i = tid; i < MAXW; i += PC_THREADS) {
     float x = 0.f;
@@ -203,6 +258,7 @@ propose_kernel(const ProposeArgs a) {
     act[0][i] = x;
     act[1][i] = 0.f;
   }
+  if (rank == 0 && tid == 0) *a.k_split = a.n_plain;  // samples k >= n_plain use the proposal
   __syncthreads();
   cluster_sync_all();  // every CTA of the cluster runs and has its buffers set
   int cur = 0;
@@ -227,9 +283,9 @@ propose_kernel(const ProposeArgs a) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0 && col < out) {
-        const float z = s + a.p[a.boff[l + 1] + col];
+        const float z = s + bias[l][c];
         if (last) {
-          a.dst[col] = a.plan[col] + (z * a.sd_out[col] + a.mean_out[col]);
+          a.dst[col] = oplan[c] + (z * osd[c] + omean[c]);
         } else {
           const float h = __bfloat162float(__float2bfloat16(gelu_f(z)));
           const uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(&act[cur ^ 1][col]));
@@ -327,7 +383,7 @@ cudaError_t gemm_tc(mppi_mlp_s* m, const bf16* A, long long lda, const bf16* B, 
     return cudaErrorInvalidValue;
   g.err = m->err;
   const dim3 grid((g.N + mppi_tc::BN - 1) / mppi_tc::BN, (g.M + mppi_tc::BM - 1) / mppi_tc::BM);
-  mppi_tc::gemm_tc_kernel<<<grid, 128, mppi_tc::SMEM_BYTES, m->st>>>(ta, tb, g);
+  mppi_tc::gemm_tc_kernel<<<grid, mppi_tc::THREADS, mppi_tc::SMEM_BYTES, m->st>>>(ta, tb, g);
   return cudaGetLastError();
 }
 
@@ -598,6 +654,19 @@ int mppi_mlp_set_normalization(mppi_mlp_t m, const float* mean_in, const float* 
   return e == cudaSuccess ? MPPI_OK : fail(MPPI_ERR_CUDA, cudaGetErrorString(e));
 }
 
+int mppi_mlp_fit_normalization(mppi_mlp_t m, const float* d_x, const float* d_y, int n,
+                               float floor) {
+  if (!m || !d_x || !d_y) return fail(MPPI_ERR_INVALID_ARG, "null argument");
+  if (n < 2) return fail(MPPI_ERR_INVALID_ARG, "n must be at least 2");
+  if (!(floor > 0.f)) return fail(MPPI_ERR_INVALID_ARG, "floor must be > 0");
+  colstats_kernel<<<m->cfg.n_in, 256, 0, m->st>>>(d_x, n, m->cfg.n_in, floor, m->mean_in, m->sd_in);
+  colstats_kernel<<<m->cfg.n_out, 256, 0, m->st>>>(d_y, n, m->cfg.n_out, floor, m->mean_out,
+                                                   m->sd_out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  return e == cudaSuccess ? MPPI_OK : fail(MPPI_ERR_CUDA, cudaGetErrorString(e));
+}
+
 int mppi_mlp_forward(mppi_mlp_t m, const float* d_x, int n, float* d_y) {
   if (!m || !d_x || !d_y) return fail(MPPI_ERR_INVALID_ARG, "null argument");
   if (n < 1 || n > m->cfg.max_batch) return fail(MPPI_ERR_INVALID_ARG, "n must be in 1..max_batch");
@@ -678,10 +747,11 @@ int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain) {
   a.mean_out = m->mean_out;
   a.sd_out = m->sd_out;
   a.dst = mppi_internal_prop(h);
-  if (!a.dst) return fail(MPPI_ERR_INVALID_ARG, "proposal buffer missing");
+  a.k_split = mppi_internal_ctl(h);
+  a.n_plain = n_plain;
+  if (!a.dst || !a.k_split) return fail(MPPI_ERR_INVALID_ARG, "proposal buffers missing");
   propose_kernel<<<PC_CTAS, PC_THREADS, 0, hs>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = mppi_internal_set_split(h, n_plain);
+  const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? MPPI_OK : fail(MPPI_ERR_CUDA, cudaGetErrorString(e));
 }
 

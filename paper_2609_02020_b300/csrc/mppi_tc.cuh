@@ -3,7 +3,7 @@
 // K-major (row-major with K contiguous), FP32 accumulation in tensor memory
 // (TMEM), fused epilogues.
 //
-// One CTA of four warps computes a 128 x 64 tile of C:
+// One CTA of eight warps computes a 128 x 64 tile of C:
 //   - thread 0 stages 128 x 64 (A) and 64 x 64 (B) BF16 tiles of a K slice
 //     into shared memory with TMA (cp.async.bulk.tensor, 128-byte swizzle,
 //     zero fill beyond the tensors' edges) through a ring of STAGES slots,
@@ -12,9 +12,10 @@
 //     instruction) from shared-memory matrix descriptors into a 128-lane x
 //     64-column FP32 accumulator in TMEM, and tcgen05.commit returns each
 //     slot to the ring once the MMAs that read it are done;
-//   - after the last slice, all four warps read the accumulator back with
-//     tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. rows of the tile)
-//     and apply the epilogue.
+//   - after the last slice, all eight warps read the accumulator back with
+//     tcgen05.ld (warp w reaches TMEM lanes 32(w % 4)..32(w % 4)+31, i.e.
+//     rows of the tile; warps w and w + 4 take the two halves of the
+//     columns) and apply the epilogue.
 // Every mbarrier wait gives up after WAIT_CYCLES and sets an error flag; the
 // kernel then skips its stores, still waits (bounded) for its MMAs and
 // frees its TMEM.
@@ -164,7 +165,9 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(128, 1)
+constexpr int THREADS = 256;
+
+__global__ void __launch_bounds__(THREADS, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
                const TcArgs g) {
   extern __shared__ uint8_t dsm_raw[];
@@ -245,39 +248,96 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ C
   const bool got = __syncthreads_and(mbar_wait(done, 0) ? 1 : 0) != 0;
   tc_fence_after();
   if (got && !s_abort) {
-    const int m = m0 + 32 * warp + lane;
-    const uint32_t trow = taddr + (static_cast<uint32_t>(32 * warp) << 16);
+    const int quad = warp & 3;  // the TMEM lanes this warp may read
+    const int m = m0 + 32 * quad + lane;
+    const uint32_t trow = taddr + (static_cast<uint32_t>(32 * quad) << 16);
+    const int cbeg = (warp >> 2) * (BN / 2);
+    const float* __restrict__ bias = g.bias;
+    const float* __restrict__ zin = g.Zin;
+    float* __restrict__ cf = g.Cf;
+    bf16* __restrict__ ch = g.Ch;
+    bf16* __restrict__ cht = g.ChT;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
+    for (int c0 = cbeg; c0 < cbeg + BN / 2; c0 += 16) {
       float v[16];
       tc_ld16(trow + c0, v);
-      if (m >= g.M) continue;
+      const int nb = n0 + c0;
+      // every operand of the chunk is loaded before the first use, so that
+      // the loads overlap (one memory latency per chunk)
+      float aux[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const int n = n0 + c0 + j;
-        if (n >= g.N) continue;
-        switch (g.epi) {
-          case EPI_F32:
-            g.Cf[m * g.ldc + n] = v[j] + (g.bias ? g.bias[n] : 0.f);
-            break;
-          case EPI_GELU: {
-            const float z = v[j] + (g.bias ? g.bias[n] : 0.f);
-            g.Cf[m * g.ldc + n] = z;
-            const bf16 h = __float2bfloat16(gelu_f(z));
-            g.Ch[m * g.ldh + n] = h;
-            if (g.ChT) g.ChT[n * g.ldht + m] = h;
-            break;
+        const int n = nb + j;
+        aux[j] = 0.f;
+        if (n < g.N) {
+          if (g.epi == EPI_GELU_GRAD) {
+            if (m < g.M) aux[j] = __ldg(zin + m * g.ldz + n);
+          } else if (bias) {
+            aux[j] = __ldg(bias + n);
           }
-          case EPI_GELU_GRAD: {
-            const bf16 d = __float2bfloat16(v[j] * gelu_grad_f(g.Zin[m * g.ldz + n]));
-            g.Ch[m * g.ldh + n] = d;
-            if (g.ChT) g.ChT[n * g.ldht + m] = d;
-            break;
-          }
-          default:
-            g.Cf[m * g.ldc + n] += v[j];
-            break;
         }
+      }
+      if (m >= g.M) continue;
+      const bool full = nb + 16 <= g.N;
+      // vector stores only where the whole row chunk is 16-byte aligned
+      const bool cf_vec = full && (g.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(cf) & 15) == 0;
+      const bool ch_vec = full && (g.ldh & 7) == 0 && (reinterpret_cast<uintptr_t>(ch) & 15) == 0;
+      if (g.epi == EPI_F32 || g.epi == EPI_F32_ACC) {
+        float o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) o[j] = v[j] + aux[j];
+        float* row = cf + m * g.ldc + nb;
+        if (g.epi == EPI_F32_ACC) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (nb + j < g.N) row[j] += o[j];
+        } else if (cf_vec) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4*>(row + j) = make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (nb + j < g.N) row[j] = o[j];
+        }
+        continue;
+      }
+      bf16 hv[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (g.epi == EPI_GELU) {
+          const float z = v[j] + aux[j];
+          v[j] = z;
+          hv[j] = __float2bfloat16(gelu_f(z));
+        } else {  // EPI_GELU_GRAD
+          hv[j] = __float2bfloat16(v[j] * gelu_grad_f(aux[j]));
+        }
+      }
+      if (g.epi == EPI_GELU) {
+        float* row = cf + m * g.ldc + nb;
+        if (cf_vec) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4*>(row + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (nb + j < g.N) row[j] = v[j];
+        }
+      }
+      bf16* hrow = ch + m * g.ldh + nb;
+      if (ch_vec) {
+        *reinterpret_cast<uint4*>(hrow) = *reinterpret_cast<const uint4*>(hv);
+        *reinterpret_cast<uint4*>(hrow + 8) = *reinterpret_cast<const uint4*>(hv + 8);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (nb + j < g.N) hrow[j] = hv[j];
+      }
+      if (cht) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (nb + j < g.N) cht[(nb + j) * g.ldht + m] = hv[j];
       }
     }
   } else if (tid == 0 && !got) {

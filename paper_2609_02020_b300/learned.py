@@ -5,13 +5,14 @@ Pipeline (every numerical step runs in the CUDA library):
      on the model used as a plant; every update gives one training pair
      x = (q, qd, goal, nominal plan u) -> y = u* - u (the correction plain
      MPPI makes to its nominal plan).
-  2. ``train``: standardise x and y, then Adam on the mean squared error with
-     the library's BF16 tensor-core forward and backward kernels.
+  2. ``train``: standardise x and y (statistics fitted by the library), then
+     Adam on the mean squared error with the library's BF16 tensor-core
+     (tcgen05) forward and backward kernels.
   3. ``LearnedMPPI``: each update samples most trajectories around the
      network's plan and the rest around the plain warm start (the fallback);
      the importance weights of Eq. 4a decide between them.
-  4. ``evaluate``: closed-loop tracking cost and update latency of any
-     controller on held-out episodes.
+  4. ``evaluate``: closed-loop tracking cost, final position error and
+     update latency of any controller on held-out episodes.
 The torch tensors here are device buffers handed to the C ABI as pointers.
 """
 from __future__ import annotations
@@ -31,7 +32,9 @@ def n_in(T: int) -> int:
 
 @dataclass
 class Problem:
-    """One arm and cost; the network is trained for this arm."""
+    """One arm and cost; the network is trained for this arm.  Episodes start
+    at q ~ U(-start_range, start_range) (synth.state when start_range is 0)
+    and aim at the end-effector pose of q + N(0, goal_spread) per joint."""
     arm: dict
     cost: dict
     T: int = 18
@@ -40,6 +43,8 @@ class Problem:
     sigma: float = 2.0
     substeps: int = 10
     plane: np.ndarray = field(default_factory=lambda: synth.NO_PLANE.copy())
+    start_range: float = 0.0
+    goal_spread: float = 0.6
 
     def controller(self, K: int, seed: int, stream=None) -> mppi.MPPI:
         return mppi.MPPI(self.arm, self.cost, dt=self.dt, T=self.T, K=K, lam=self.lam,
@@ -51,17 +56,39 @@ class Problem:
 
     def episode_start(self, seed: int, helper: mppi.MPPI):
         """Start state and a reachable goal: the end-effector pose of a
-        configuration within N(0, 0.6) rad per joint of the start (FK on the
-        device)."""
-        q, qd = synth.state(seed, self.arm)
+        configuration within N(0, goal_spread) rad per joint of the start (FK
+        on the device)."""
+        if self.start_range > 0.0:
+            g0 = np.random.default_rng([seed, 78])
+            q = g0.uniform(-self.start_range, self.start_range, 7)
+            qd = g0.normal(0.0, 0.1, 7)
+        else:
+            q, qd = synth.state(seed, self.arm)
         g = np.random.default_rng([seed, 77])
-        qg = np.clip(q + g.normal(0.0, 0.6, 7), self.arm["q_min"], self.arm["q_max"])
+        qg = np.clip(q + g.normal(0.0, self.goal_spread, 7), self.arm["q_min"], self.arm["q_max"])
         goal = helper.ee_pose(qg).astype(np.float64)
         return q, qd, goal
 
 
+def tracking_problem(seed: int = 0) -> Problem:
+    """The reaching task of the learned-proposal study, on which plain MPPI at
+    K=16384 converges: a gravity-compensated arm (the commanded torque comes
+    on top of the robot's own gravity compensation, as with a torque-controlled
+    Franka arm: gravity 0 in model and plant), joint damping 5 N m s/rad,
+    position-only goals (W_pos = 300, W_ori = 0, no posture term) reached
+    from q ~ U(-1.2, 1.2) rad with goals 0.2 rad per joint away, sigma = 2 N m,
+    lambda = 3."""
+    arm = synth.arm(seed, damping=5.0)
+    arm["gravity"] = np.zeros(3)
+    cost = synth.cost_free_space()
+    cost["w_pos"] = np.full(3, 300.0)
+    cost["w_ori"] = np.zeros(3)
+    cost["w_posture"] = 0.0
+    return Problem(arm=arm, cost=cost, sigma=2.0, lam=3.0, start_range=1.2, goal_spread=0.2)
+
+
 def generate(prob: Problem, n_pairs: int, *, K: int = 16384, seed: int = 0,
-             episode_len: int = 100, stream=None):
+             episode_len: int = 200, stream=None):
     """Training pairs from plain MPPI: X [n, 21 + 7T], Y [n, 7T] (device);
     Y is the correction u* - u to the nominal plan held in X[:, 21:]."""
     import torch
@@ -82,8 +109,7 @@ def generate(prob: Problem, n_pairs: int, *, K: int = 16384, seed: int = 0,
                 X[i, :21].copy_(d_in[0, :21])
                 ctl.get_plan_device(X[i, 21:])
                 ctl.step_device(d_in[0], d_tau[0], None)
-                ctl.get_updated_plan_device(Y[i])
-                Y[i].sub_(X[i, 21:])
+                ctl.correction_device(Y[i])  # u* - u, formed by the library
                 ctl.simulate_device(d_in, d_tau, d_x, prob.substeps)
                 d_in[0, :14].copy_(d_x[0])
                 i += 1
@@ -92,12 +118,6 @@ def generate(prob: Problem, n_pairs: int, *, K: int = 16384, seed: int = 0,
         s.synchronize()
         ctl.close()
     return X, Y
-
-
-def standardisation(X, Y, floor: float = 1e-3):
-    mx, sx = X.mean(0), X.std(0).clamp_min(floor)
-    my, sy = Y.mean(0), Y.std(0).clamp_min(floor)
-    return [t.cpu().numpy() for t in (mx, sx, my, sy)]
 
 
 def train(X, Y, *, steps: int = 4000, batch: int = 1024, lr: float = 1e-3, hidden: int = 256,
@@ -115,7 +135,7 @@ def train(X, Y, *, steps: int = 4000, batch: int = 1024, lr: float = 1e-3, hidde
         Xt, Yt = X[perm[nval:]].contiguous(), Y[perm[nval:]].contiguous()
         net = mppi.MLP(X.shape[1], hidden, layers, Y.shape[1], max_batch=max(batch, min(nval, 65536)),
                        seed=seed, stream=s)
-        net.set_normalization(*standardisation(Xt, Yt))
+        net.fit_normalization(Xt, Yt)  # per-feature means and deviations, on the device
         nt = Xt.shape[0]
         losses = []
         t0 = time.perf_counter()
@@ -182,7 +202,8 @@ def evaluate(prob: Problem, controller, *, episodes: int, steps: int, seed: int,
     import torch
     w_pos = float(np.mean(prob.cost["w_pos"]))
     w_ori = float(np.mean(prob.cost["w_ori"]))
-    costs, pos_err, ori_err, lat_ms = [], [], [], []
+    costs, pos_err, ori_err, lat_ms, fin_err = [], [], [], [], []
+    tail = min(steps, max(1, int(round(1.0 / prob.dt))))  # the last second
     d_in = torch.empty(1, 25, device="cuda")
     d_tau = torch.empty(1, 7, device="cuda")
     d_x = torch.empty(1, 14, device="cuda")
@@ -205,7 +226,7 @@ def evaluate(prob: Problem, controller, *, episodes: int, steps: int, seed: int,
             stream.synchronize()
             lat_ms += [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
             tr = traj.cpu().numpy()
-            c, pe, oe = 0.0, [], []
+            c, pe, oe, fe = 0.0, [], [], []
             for t in range(steps):
                 pose = helper.ee_pose(tr[t, :7])
                 dp = float(np.linalg.norm(pose[:3] - goal[:3]))
@@ -214,11 +235,16 @@ def evaluate(prob: Problem, controller, *, episodes: int, steps: int, seed: int,
                 if t >= steps // 2:
                     pe.append(dp)
                     oe.append(th)
+                if t >= steps - tail:
+                    fe.append(dp)
             costs.append(c / steps)
             pos_err.append(float(np.mean(pe)))
             ori_err.append(float(np.mean(oe)))
+            fin_err.append(float(np.mean(fe)))
     helper.close()
     lat = np.array(lat_ms)
     return dict(tracking_cost=float(np.mean(costs)), tracking_cost_per_episode=costs,
                 pos_err_m=float(np.mean(pos_err)), ori_err_rad=float(np.mean(ori_err)),
+                final_err_m=float(np.median(fin_err)), final_err_per_episode=fin_err,
+                within_2cm=float(np.mean(np.array(fin_err) < 0.02)),
                 p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)))

@@ -134,7 +134,7 @@ EXPORTS = [
     "mppi_simulate_device", "mppi_set_plan_device", "mppi_get_plan_device",
     "mppi_get_updated_plan_device", "mppi_set_proposal_device", "mppi_gravity_torque",
     "mppi_force_estimate_device", "mppi_set_obstacles", "mppi_set_obstacles_device",
-    "mppi_get_variant", "mppi_measure_fp32_peak",
+    "mppi_get_variant", "mppi_measure_fp32_peak", "mppi_get_correction_device",
     # include/mppi_serve.h
     "mppi_pool_create", "mppi_pool_destroy", "mppi_pool_alloc", "mppi_pool_free",
     "mppi_pool_stats", "mppi_server_create", "mppi_server_destroy", "mppi_server_add_problem",
@@ -144,7 +144,8 @@ EXPORTS = [
     "mppi_server_set_input", "mppi_server_load_test",
     # include/mppi_mlp.h
     "mppi_mlp_create", "mppi_mlp_destroy", "mppi_mlp_num_params", "mppi_mlp_get_params",
-    "mppi_mlp_set_params", "mppi_mlp_set_normalization", "mppi_mlp_forward",
+    "mppi_mlp_set_params", "mppi_mlp_set_normalization", "mppi_mlp_fit_normalization",
+    "mppi_mlp_forward",
     "mppi_mlp_loss_grad", "mppi_mlp_train_step", "mppi_mlp_propose",
 ]
 
@@ -191,6 +192,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_set_plan_device": ([H, vp], C.c_int),
         "mppi_get_plan_device": ([H, vp], C.c_int),
         "mppi_get_updated_plan_device": ([H, vp], C.c_int),
+        "mppi_get_correction_device": ([H, vp], C.c_int),
         "mppi_set_proposal_device": ([H, vp, C.c_int], C.c_int),
         "mppi_gravity_torque": ([H, fp, fp], C.c_int),
         "mppi_force_estimate_device": ([H, vp, vp, C.c_int, vp], C.c_int),
@@ -227,6 +229,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_mlp_get_params": ([H, fp], C.c_int),
         "mppi_mlp_set_params": ([H, fp], C.c_int),
         "mppi_mlp_set_normalization": ([H, fp, fp, fp, fp], C.c_int),
+        "mppi_mlp_fit_normalization": ([H, vp, vp, C.c_int, C.c_float], C.c_int),
         "mppi_mlp_forward": ([H, vp, C.c_int, vp], C.c_int),
         "mppi_mlp_loss_grad": ([H, vp, vp, C.c_int, fp, fp], C.c_int),
         "mppi_mlp_train_step": ([H, vp, vp, C.c_int, C.c_float, fp], C.c_int),
@@ -504,6 +507,10 @@ class MPPI:
     def get_updated_plan_device(self, d_u):
         self._check(self.lib.mppi_get_updated_plan_device(self.h, _dptr(d_u)))
 
+    def correction_device(self, d_out):
+        """u* - u of the last update into a device tensor [T, 7] (stream-ordered)."""
+        self._check(self.lib.mppi_get_correction_device(self.h, _dptr(d_out)))
+
     def noise_words(self, it: int, k0: int, count: int, t: int) -> np.ndarray:
         """Raw Philox words [count, 8] of the device generator."""
         out = np.zeros((count, 8), dtype=np.uint32)
@@ -774,6 +781,11 @@ class MLP:
         self._check(self.lib.mppi_mlp_set_normalization(
             self.h, _fp(_f32(mean_in, self.dims[0])), _fp(_f32(std_in, self.dims[0])),
             _fp(_f32(mean_out, self.dims[-1])), _fp(_f32(std_out, self.dims[-1]))))
+
+    def fit_normalization(self, d_x, d_y, floor: float = 1e-3):
+        """Standardisation fitted on the device to training rows d_x [n, n_in], d_y [n, n_out]."""
+        self._check(self.lib.mppi_mlp_fit_normalization(self.h, _dptr(d_x), _dptr(d_y),
+                                                        int(d_x.shape[0]), float(floor)))
 
     def forward(self, d_x, d_y):
         self._check(self.lib.mppi_mlp_forward(self.h, _dptr(d_x), int(d_x.shape[0]), _dptr(d_y)))
