@@ -6,7 +6,7 @@ plane contact, dt = 0.01 s.  Prints one JSON line on rank 0.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--cost contact|force_estimate|collision]
-                    [--mode update|serve|learned|sweep]
+                    [--mode update|serve|learned|sweep|mlp]
 
 `value` times the update on device-resident inputs with CUDA events on the
 library's stream, L2 flushed between steps; `e2e` times the public host call
@@ -60,15 +60,15 @@ L2_FLUSH_BYTES = 256 << 20  # twice the 126 MB L2
 # polynomials included) is kept beside it.  The optional cost terms have no
 # hand count; their lines use the executed count and say so.
 FLOP_PER_ROLLOUT_STEP = {"contact": 4311.0}
-FLOP_EXECUTED_PER_ROLLOUT_STEP = {"contact": 4766.0, "force_estimate": 6004.6,
+FLOP_EXECUTED_PER_ROLLOUT_STEP = {"contact": 4908.5, "force_estimate": 6004.6,
                                   "collision": 6692.8}
 # DRAM read + write bytes of one rollout launch at K=16384, T=18 per (cost,
 # kernel) (ncu dram__bytes_{read,write}.sum, mean of two launches).  The
-# 8.3 MB of stored noise stays in L2 for update_kernel and is not written
-# back inside the launch.
+# 8.3 MB of stored noise stays in L2 and is not written back inside the
+# launch.
 # Only kernels captured since their last change are listed; the others
 # report null.
-ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel_ws"): 67328,
+ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel_ws"): 68096,
                                     ("collision", "rollout_kernel_ws"): 175360}
 COSTS = ("contact", "force_estimate", "collision")
 SM_COUNT = 148
@@ -95,11 +95,12 @@ def parse():
                     help="update mode: the plane-contact workload (default), or the same with "
                          "C_force on the wrench estimate of Eq. 13, or with the collision "
                          "indicator of Eq. 15 against 3 obstacles")
-    ap.add_argument("--mode", default="update", choices=["update", "serve", "learned", "sweep"],
+    ap.add_argument("--mode", default="update", choices=["update", "serve", "learned", "sweep", "mlp"],
                     help="update: the headline single-update benchmark; serve: batched "
                          "serving of 256 problems under Poisson load; learned: train the "
                          "learned proposal and compare it with plain MPPI; sweep: the update "
-                         "over K x T with FP32 and FP64 reductions")
+                         "over K x T with FP32 and FP64 reductions; mlp: the learned "
+                         "proposal's network kernels alone")
     ap.add_argument("--pairs", type=int, default=200_000, help="learned mode: training pairs")
     ap.add_argument("--train-steps", type=int, default=3000, help="learned mode: Adam steps")
     ap.add_argument("--episodes", type=int, default=12, help="learned mode: eval episodes")
@@ -646,6 +647,60 @@ def run_sweep(args, rank, world):
             "clocks": clocks, "points": rows}), flush=True)
 
 
+def run_mlp(args, rank, world):
+    """The learned proposal's network kernels alone (tcgen05 BF16, FP32
+    accumulate): Adam training steps of 1024 and 4096 rows, the batched
+    forward of 4096 rows, and the single-row proposal kernel; device time by
+    CUDA events on the network's stream, after warm-up."""
+    import torch
+    from paper_2609_02020_b300 import learned, mppi
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    s = torch.cuda.Stream()
+    torch.cuda.set_stream(s)
+    dims = [147, 256, 256, 256, 126]
+    net = mppi.MLP(dims[0], dims[1], 3, dims[-1], max_batch=4096, seed=1, stream=s)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    X = torch.randn(16 * 4096, dims[0], device="cuda", generator=g)
+    Y = torch.randn(16 * 4096, dims[-1], device="cuda", generator=g)
+    fwd = 2 * sum(dims[i] * dims[i + 1] for i in range(4))
+
+    def timed(fn, n):
+        for _ in range(max(args.warmup, 3)):
+            fn(0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for i in range(n):
+            fn(i)
+        b.record(s)
+        s.synchronize()
+        return a.elapsed_time(b) / n
+
+    out = {}
+    for B in (1024, 4096):
+        ms = timed(lambda i: net.train_step(X[(i % 16) * B:(i % 16 + 1) * B],
+                                            Y[(i % 16) * B:(i % 16 + 1) * B], 1e-4), 300)
+        flop = 3 * fwd * B
+        out[f"train_{B}"] = {"ms_per_step": ms, "gflop_per_step": flop / 1e9,
+                             "tflops": flop / (ms * 1e-3) / 1e12,
+                             "frac_of_bf16_peak": flop / (ms * 1e-3) / 1e12 / 1786.4}
+    dY = torch.empty(4096, dims[-1], device="cuda")
+    ms = timed(lambda i: net.forward(X[:4096], dY), 300)
+    out["forward_4096"] = {"ms": ms, "tflops": fwd * 4096 / (ms * 1e-3) / 1e12}
+    prob = learned.tracking_problem()
+    ctl = prob.controller(512, seed=1, stream=s)
+    q, qd, goal = prob.episode_start(123, ctl)
+    d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, prob.plane), device="cuda")
+    out["propose_us"] = timed(lambda i: net.propose(ctl, d_in, 256), 500) * 1e3
+    ctl.close()
+    net.close()
+    if rank == 0:
+        print(json.dumps({"mode": "mlp", "metric": "learned-proposal network kernels on tcgen05",
+                          "unit": "ms / TFLOP/s / us", "n_gpus": world, "dtype": "bf16 in, f32 accumulate",
+                          "data": "synthetic", "config": {"network": "147 -> 3 x 256 GELU -> 126"},
+                          "peak_bf16_tflops": 1786.4, **out}), flush=True)
+
+
 def run_learned(args, rank, world):
     """Learned proposal on the reaching task where plain MPPI at K=16384
     converges (learned.tracking_problem): pairs from plain MPPI at K=16384,
@@ -735,6 +790,8 @@ def main():
             run_learned(args, rank, world)
         elif args.mode == "sweep":
             run_sweep(args, rank, world)
+        elif args.mode == "mlp":
+            run_mlp(args, rank, world)
         else:
             run_ours(args, rank, world)
     finally:
