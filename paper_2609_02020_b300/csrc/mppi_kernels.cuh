@@ -722,9 +722,11 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
 // runs on a single dependency chain.  For each state x_s (s = 0..T):
 //   link phase: warp 0 walks the kinematic chain (link frames, joint axes,
 //     velocities and bias accelerations) and hands each link over; warp 1
-//     forms the link inertias and RNEA forces of the even links, warp 2 of
-//     the odd ones, and warp 2 then forms the end-effector point and contact
-//     force for the dynamics.
+//     forms the link inertias and RNEA forces of links 0, 2, 4, warp 2 of
+//     links 1, 3, 5, and warp 2 then forms the end-effector point and
+//     contact force for the dynamics; warp 0 forms the last link's inertia
+//     and force itself, from the chain state it holds (warp 1 with the
+//     collision cost).
 //   For s < T, after the forces: h and the rows of M are split over the
 //     three warps (each forms the composite inertias it needs); warp 0
 //     factorises M, waits for the step's inputs, solves for qdd and takes the
@@ -764,13 +766,15 @@ __device__ __forceinline__ void bar_arrive(int id, int count) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// Threads at link i's barrier: warp 0 and the force warp of link i, and for
-// the last link also the other force warp (it forms the end-effector state)
-// while s < T; at s = T only the last link's barrier runs, for warp 1 and,
-// with the collision cost, warps 3 and 4 (they read the last state's link
-// points after it).
-__host__ __device__ constexpr int ws_link_count(int i, bool last_state, bool coll = false) {
-  return last_state ? (coll ? 4 : 2) * WS_B : (i == NJ - 1 ? 3 * WS_B : 2 * WS_B);
+// Threads at link i's barrier while s < T: warp 0 and the force warp of
+// link i; for the last link warp 2, which forms the end-effector state, and
+// its force warp (warp 1) only with the collision cost: without it warp 0
+// forms the last link's force itself (with it, the register budget of four
+// 160-thread blocks per SM leaves no room for that).  At s = T only the last
+// link's barrier runs, for warp 1 and, with the collision cost, warps 3 and
+// 4 (they read the last state's link points after it).
+__host__ __device__ constexpr int ws_link_count(int i, bool last_state, bool coll) {
+  return last_state ? (coll ? 4 : 2) * WS_B : (coll && i == NJ - 1 ? 3 : 2) * WS_B;
 }
 // Warps of the kernel, and threads at the barriers every warp meets.
 __host__ __device__ constexpr int ws_warps(bool coll) { return coll ? 5 : 3; }
@@ -978,6 +982,13 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
       if (!last || i == NJ - 1) bar_arrive(BAR_LINK0 + i, ws_link_count(i, last, COLL));
     }
     if (last) break;
+    // the last link's force here, from the chain state in registers: no
+    // hand-off on the way to the backward sweep
+    if (!COLL) {
+      float In[10], F[6];
+      forward_link_force(P.rb.L[NJ - 1], c.R, c.p, c.Vw, c.Vv, c.Aw, c.Av, In, F);
+      ws_store_force(m.sl, NJ - 1, tid, F, In);
+    }
     bar_sync(BAR_FORCES, NA);
     ws_backward_h(P.rb, m, tid);
     bar_sync(BAR_MROWS, 3 * B);
@@ -1018,11 +1029,13 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
   }
 }
 
-// warps 1 and 2, link phase: inertias and forces of links first, first + 2, ...
+// warps 1 and 2, link phase: inertias and forces of links first, first + 2,
+// ... (the last link's only with the collision cost)
+template <bool COLL>
 __device__ __forceinline__ void ws_forces(const ProbK& P, const WsSmem& m, int first, int tid) {
 #pragma unroll 1
-  for (int i = first; i < NJ; i += 2) {
-    bar_sync(BAR_LINK0 + i, ws_link_count(i, false));
+  for (int i = first; i < (COLL ? NJ : NJ - 1); i += 2) {
+    bar_sync(BAR_LINK0 + i, ws_link_count(i, false, COLL));
     ChainState c;
     ws_load_chain(m.sc, i, tid, c);
     float In[10], F[6];
@@ -1031,7 +1044,8 @@ __device__ __forceinline__ void ws_forces(const ProbK& P, const WsSmem& m, int f
   }
 }
 
-// warp 1: forces of the even links and the running cost; returns S_k
+// warp 1: forces of links 0, 2, 4 (and 6 with the collision cost) and the
+// running cost; returns S_k
 template <bool COLL>
 __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const WsSmem& m,
                                           int tid) {
@@ -1051,8 +1065,8 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
   for (int s = 0; s <= T; ++s) {
     ChainState c;
     if (s < T) {
-      ws_forces(P, m, 0, tid);  // ends with the last link (even)
-      ws_load_chain(m.sc, NJ - 1, tid, c);
+      ws_forces<COLL>(P, m, 0, tid);
+      if (COLL) ws_load_chain(m.sc, NJ - 1, tid, c);
       bar_sync(BAR_FORCES, NA);
       ws_backward_rows(P.rb, m, WS_ROWS1, tid);
       bar_arrive(BAR_MROWS, 3 * B);
@@ -1142,11 +1156,11 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
   const float plane[4] = {in[21], in[22], in[23], in[24]};
   double S2 = 0.0;
   for (int s = 0; s < T; ++s) {
-    ws_forces(P, m, 1, tid);
+    ws_forces<COLL>(P, m, 1, tid);
     EEState ee;
     float f;
     {
-      bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, false));
+      bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, false, COLL));
       ChainState c;
       ws_load_chain(m.sc, NJ - 1, tid, c);
       chain_ee(P.rb, c, ee);

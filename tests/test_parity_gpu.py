@@ -357,6 +357,23 @@ def test_ee_pose_matches_oracle():
             assert np.abs(Rg - Re).max() < 2e-6
 
 
+@pytest.mark.parametrize("scale", [1.0, 40.0, 3000.0])
+def test_ee_pose_at_large_joint_angles(scale):
+    # the kernels' sin and cos of a joint angle reduce by pi/2 in three parts:
+    # angles of several turns (and far outside any arm's range) keep the pose
+    # within the same bound as angles in (-pi, pi)
+    c = make_case(3)
+    rng = np.random.default_rng(int(scale))
+    with gpu_controller(c) as g:
+        for _ in range(20):
+            q = f32(rng.uniform(-scale * np.pi, scale * np.pi, 7))
+            pose = g.ee_pose(q)
+            _, _, Re, pe = oracle.fk(c["rb"], q)
+            assert np.abs(pose[:3] - pe).max() < 2e-6, q
+            Rg = oracle.quat_matrix(pose[3:].astype(np.float64))
+            assert np.abs(Rg - Re).max() < 2e-6, q
+
+
 def test_gravity_torque_matches_oracle():
     c = make_case(4)
     with gpu_controller(c) as g:

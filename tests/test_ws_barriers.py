@@ -4,14 +4,15 @@
 Each warp's barrier operations are listed in program order, as the kernel
 issues them for states s = 0..T.  Warp 0 arrives at one barrier per link
 once the link's frame and motion are written (at s = T only at the last
-link's), then, for s < T, waits for the link forces, the rows of M and the
-step's inputs.  Warp 1 waits for the even links (the last one included),
-then for the forces, arrives with its rows of M and with its copy of x_s;
-at s = T it waits for the last link only.  Warp 2 waits for the odd links
-and for the last link (it forms the end-effector state for the dynamics),
-then for the forces, and arrives with its rows of M and with the step's
-input; after the last state warp 2 hands its partial cost to warp 1 (one
-more barrier).  With the collision cost two more warps wait for the forces,
+link's), then, for s < T, forms the last link's force itself and waits for
+the link forces, the rows of M and the step's inputs.  Warp 1 waits for
+links 0, 2 and 4 (and 6 with the collision cost, where it forms the last
+link's force instead of warp 0), then for the forces, arrives with its rows of M and with
+its copy of x_s; at s = T it waits for the last link only.  Warp 2 waits for
+links 1, 3 and 5 and for the last link (it forms the end-effector state for
+the dynamics), then for the forces, and arrives with its rows of M and with
+the step's input; after the last state warp 2 hands its partial cost to
+warp 1 (one more barrier).  With the collision cost two more warps wait for the forces,
 arrive once they have copied the link points, wait for the last state's last
 link and hand over their partial costs.  The model runs the programs under named-barrier semantics (a
 phase completes when `count` threads have arrived or waited) in random
@@ -33,7 +34,9 @@ COLL = False  # the collision-cost kernel: two more warps (see below)
 
 
 def link_count(i, last):
-    return (4 if COLL else 2) * B if last else (3 * B if i == NJ - 1 else 2 * B)
+    if last:
+        return (4 if COLL else 2) * B
+    return 3 * B if COLL and i == NJ - 1 else 2 * B
 
 
 def na():
@@ -56,7 +59,7 @@ def warp0(T):
 def warp1(T):
     for s in range(T + 1):
         if s < T:
-            for i in range(0, NJ, 2):
+            for i in range(0, NJ if COLL else NJ - 1, 2):
                 yield ("sync", BAR_LINK0 + i, link_count(i, False), s)
             yield ("sync", BAR_FORCES, na(), s)
             yield ("arrive", BAR_MROWS, 3 * B, s)
