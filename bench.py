@@ -650,8 +650,9 @@ def run_sweep(args, rank, world):
 def run_mlp(args, rank, world):
     """The learned proposal's network kernels alone (tcgen05 BF16, FP32
     accumulate): Adam training steps of 1024 and 4096 rows, the batched
-    forward of 4096 rows, and the single-row proposal kernel; device time by
-    CUDA events on the network's stream, after warm-up."""
+    forward of 4096 rows, and the single-row proposal kernel (launched one
+    by one from the host, and 200 launches replayed from one CUDA graph);
+    device time by CUDA events on the network's stream, after warm-up."""
     import torch
     from paper_2609_02020_b300 import learned, mppi
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -691,7 +692,13 @@ def run_mlp(args, rank, world):
     ctl = prob.controller(512, seed=1, stream=s)
     q, qd, goal = prob.episode_start(123, ctl)
     d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, prob.plane), device="cuda")
-    out["propose_us"] = timed(lambda i: net.propose(ctl, d_in, 256), 500) * 1e3
+    out["propose_us_stream"] = timed(lambda i: net.propose(ctl, d_in, 256), 500) * 1e3
+    # the kernel without the host's launch rate: 200 launches in one CUDA graph
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(200):
+            net.propose(ctl, d_in, 256)
+    out["propose_us_graph"] = timed(lambda i: g.replay(), 5) * 1e3 / 200
     ctl.close()
     net.close()
     if rank == 0:

@@ -186,8 +186,13 @@ __global__ void to_bf16_kernel(const float* __restrict__ W, int out, int in, bf1
 // output columns 32 r .. 32 r + 31 (warp w: four of them, lane l: inputs
 // 8 l .. 8 l + 7, a shuffle sum over the lanes), rounds hidden outputs to
 // BF16 after the GELU as the batched path does, and stores them into every
-// CTA's activation buffer through distributed shared memory; a cluster
-// barrier separates the layers.  All weight fragments (16 B per lane,
+// CTA's activation buffer through distributed shared memory with st.async
+// (lane r of the column's warp stores into CTA r), each store counting its
+// 4 bytes on the receiving CTA's mbarrier of that
+// buffer; a CTA starts layer l + 1 once its barrier has counted all of
+// layer l's outputs (no cluster-wide barrier between layers).  A buffer is
+// written again two layers later, which no CTA reaches before every CTA has
+// read it (each CTA's next outputs follow its reads).  All weight fragments (16 B per lane,
 // column and layer) are loaded before the first layer, so the network's
 // 400 KB of BF16 weights cost one L2 round trip, spread over 8 SMs.  The
 // output is the correction to the nominal plan: dst = plan + net(x).
@@ -209,6 +214,7 @@ struct ProposeArgs {
   float* dst;           // [n_out]
   int* k_split;         // the handle's k_split of its next update
   int n_plain;
+  int* err;             // set when a wait for a layer's inputs gave up
 };
 
 __device__ __forceinline__ void cluster_sync_all() {
@@ -216,9 +222,39 @@ __device__ __forceinline__ void cluster_sync_all() {
                "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// One activation store into CTA r's buffer, counted on CTA r's mbarrier.
+__device__ __forceinline__ void st_async_remote(const float* local_dst, const uint64_t* local_bar,
+                                                uint32_t r, float v) {
+  uint32_t dst, bar;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(dst) : "r"(mppi_tc::smem_u32(local_dst)), "r"(r));
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(bar) : "r"(mppi_tc::smem_u32(local_bar)), "r"(r));
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+               ::"r"(dst), "r"(__float_as_uint(v)), "r"(bar) : "memory");
+}
+
+// Bounded wait for phase `parity` of a local barrier that other CTAs'
+// st.async complete (acquire at cluster scope).
+__device__ __forceinline__ bool wait_cluster_tx(const uint64_t* bar, uint32_t parity) {
+  const uint32_t b = mppi_tc::smem_u32(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(b), "r"(parity) : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > mppi_tc::WAIT_CYCLES) return false;
+  }
+}
+
 __global__ void __cluster_dims__(PC_CTAS, 1, 1) __launch_bounds__(PC_THREADS)
 propose_kernel(const ProposeArgs a) {
   __shared__ float act[2][MAXW];
+  __shared__ __align__(8) uint64_t bar[2];  // one per activation buffer
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t rank;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
@@ -259,14 +295,28 @@ propose_kernel(const ProposeArgs a) {
     act[1][i] = 0.f;
   }
   if (rank == 0 && tid == 0) *a.k_split = a.n_plain;  // samples k >= n_plain use the proposal
+  if (tid == 0) {
+    mppi_tc::mbar_init(mppi_tc::smem_u32(&bar[0]), 1);
+    mppi_tc::mbar_init(mppi_tc::smem_u32(&bar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
-  cluster_sync_all();  // every CTA of the cluster runs and has its buffers set
-  int cur = 0;
+  cluster_sync_all();  // every CTA of the cluster runs and has its barriers set
+  bool ok = true;
 #pragma unroll
   for (int l = 0; l < PC_LMAX; ++l) {
     if (l >= a.L) break;
     const int out = a.dims[l + 1];
     const bool last = l + 1 == a.L;
+    const int cur = l & 1;
+    // every store of this CTA is issued before the last layer: arrive now,
+    // wait before leaving (no CTA leaves while another may store into it)
+    if (last) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    // layer l's inputs: for l >= 1 the (l - 1) / 2-th use of buffer l % 2
+    if (l > 0) ok = ok && wait_cluster_tx(&bar[cur], static_cast<uint32_t>((l - 1) >> 1) & 1u);
+    // the next layer's buffer: its previous use was waited for a layer ago
+    if (!last && tid == 0) mppi_tc::mbar_expect_tx(mppi_tc::smem_u32(&bar[cur ^ 1]), 4u * out);
+    if (!ok) continue;
     float x[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = act[cur][8 * lane + j];
@@ -282,27 +332,23 @@ propose_kernel(const ProposeArgs a) {
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0 && col < out) {
+      // every lane holds the sum: lane r < PC_CTAS stores it into CTA r
+      if (col < out) {
         const float z = s + bias[l][c];
         if (last) {
-          a.dst[col] = oplan[c] + (z * osd[c] + omean[c]);
-        } else {
+          if (lane == 0) a.dst[col] = oplan[c] + (z * osd[c] + omean[c]);
+        } else if (lane < PC_CTAS) {
           const float h = __bfloat162float(__float2bfloat16(gelu_f(z)));
-          const uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(&act[cur ^ 1][col]));
-#pragma unroll
-          for (uint32_t r = 0; r < PC_CTAS; ++r) {
-            uint32_t remote;
-            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(r));
-            asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(h) : "memory");
-          }
+          st_async_remote(&act[cur ^ 1][col], &bar[cur ^ 1], static_cast<uint32_t>(lane), h);
         }
       }
     }
-    if (!last) {
-      cluster_sync_all();
-      cur ^= 1;
-    }
   }
+  if (!ok && tid == 0) {
+    *a.err = 1;
+    *a.k_split = 0x7fffffff;  // the next update samples around the plain warm start only
+  }
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 int fail(int code, const std::string& msg) {
@@ -749,6 +795,7 @@ int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain) {
   a.dst = mppi_internal_prop(h);
   a.k_split = mppi_internal_ctl(h);
   a.n_plain = n_plain;
+  a.err = m->err;
   if (!a.dst || !a.k_split) return fail(MPPI_ERR_INVALID_ARG, "proposal buffers missing");
   propose_kernel<<<PC_CTAS, PC_THREADS, 0, hs>>>(a);
   const cudaError_t e = cudaGetLastError();
