@@ -355,6 +355,16 @@ __device__ __forceinline__ void chain_ee(const RobotK& rb, const ChainState& c, 
   ee.v[0] = c.Vv[0] + wp[0]; ee.v[1] = c.Vv[1] + wp[1]; ee.v[2] = c.Vv[2] + wp[2];
 }
 
+// End-effector position and linear velocity only (as chain_ee computes them).
+__device__ __forceinline__ void chain_ee_pv(const RobotK& rb, const ChainState& c, EEState& ee) {
+  float de[3];
+  mv3(c.R, rb.ee, de);
+  ee.p[0] = c.p[0] + de[0]; ee.p[1] = c.p[1] + de[1]; ee.p[2] = c.p[2] + de[2];
+  float wp[3];
+  cross3(c.Vw, ee.p, wp);
+  ee.v[0] = c.Vv[0] + wp[0]; ee.v[1] = c.Vv[1] + wp[1]; ee.v[2] = c.Vv[2] + wp[2];
+}
+
 // Forward sweep at state (q, qd): kinematics (Fig. 1), RNEA forward
 // recursion with qdd = 0, end-effector pose and velocity.
 __device__ __forceinline__ void forward_sweep(const RobotK& rb, const float q[NJ],

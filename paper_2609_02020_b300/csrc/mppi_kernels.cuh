@@ -730,8 +730,9 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
 //   For s < T, after the forces: h and the rows of M are split over the
 //     three warps (each forms the composite inertias it needs); warp 0
 //     factorises M, waits for the step's inputs, solves for qdd and takes the
-//     Euler step to x_{s+1}; warp 1 copies x_s and then charges
-//     l(x_s, v_{s-1}); warp 2 draws v_{s+1} one step ahead (v_0 at s = 0).
+//     Euler step to x_{s+1}; warp 1 copies x_s and the last link's chain
+//     state and then charges all of l(x_s, v_{s-1}); warp 2 draws v_{s+1}
+//     one step ahead (v_0 at s = 0).
 //   At s = T warp 1 charges l(x_T, v_{T-1}) and phi(x_T).
 // Hand-offs go through shared memory under named barriers with fixed
 // arrival counts.  Per state every barrier sees the same arrivals, and each
@@ -756,7 +757,8 @@ constexpr int BAR_LINK0 = 1, BAR_FORCES = 8, BAR_MROWS = 9, BAR_STEP = 10, BAR_D
 constexpr int WS_FLOATS_PER_SAMPLE = NJ * WS_REC + NJ * (NJ + 1) / 2 + NJ /* h */ +
                                      2 * NJ /* q, qd */ + V_SLOTS * NJ /* v ring */;
 // The last float4 of each record is free: link 0's holds the end-effector
-// point and contact force for the dynamics, link 1's warp 2's partial cost.
+// point and contact force for the dynamics, links 1 and 2's the collision
+// warps' partial costs.
 constexpr int WS_PAD = 48;
 
 __device__ __forceinline__ void bar_sync(int id, int count) {
@@ -812,12 +814,13 @@ __device__ __forceinline__ const float4* ws_rec(const float* base, int i, int ti
   return reinterpret_cast<const float4*>(base + (i * WS_B + tid) * WS_REC);
 }
 
-// end-effector point (3) and contact force of sample tid, and warp 2's
-// partial cost of sample tid, in the free tails of records 0 and 1
+// end-effector point (3) and contact force of sample tid in the free tail
+// of record 0, and the collision warps' partial costs of sample tid in those
+// of records 1 and 2
 __device__ __forceinline__ float* ws_ee(const WsSmem& m, int tid) {
   return m.sl + tid * WS_REC + WS_PAD;
 }
-__device__ __forceinline__ double* ws_s2(const WsSmem& m, int tid, int slot = 0) {
+__device__ __forceinline__ double* ws_s2(const WsSmem& m, int tid, int slot) {
   return reinterpret_cast<double*>(m.sl + ((1 + slot) * WS_B + tid) * WS_REC + WS_PAD);
 }
 
@@ -1066,10 +1069,11 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
     ChainState c;
     if (s < T) {
       ws_forces<COLL>(P, m, 0, tid);
-      if (COLL) ws_load_chain(m.sc, NJ - 1, tid, c);
       bar_sync(BAR_FORCES, NA);
       ws_backward_rows(P.rb, m, WS_ROWS1, tid);
       bar_arrive(BAR_MROWS, 3 * B);
+      // x_s's last link, read before warp 0 may overwrite it
+      if (s > 0) ws_load_chain(m.sc, NJ - 1, tid, c);
     } else {
       bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, true, COLL));
       ws_load_chain(m.sc, NJ - 1, tid, c);
@@ -1085,18 +1089,14 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
     }
     if (s < T) bar_arrive(BAR_STEP, NA);
     if (s == 0) continue;
-    // running cost l(x_s, v_{s-1}), Eq. 9-14: the joint terms here, the
-    // motion and force terms on warp 2 for s < T and here for s = T
-    float cst = 0.f;
+    // running cost l(x_s, v_{s-1}), Eq. 9-14
     EEState ee;
-    if (s == T) {
-      chain_ee(P.rb, c, ee);
-      cst = motion_cost(C, pdes, Rd, ee);
-      if (contact) {
-        const float f = contact_force(C, plane, ee);
-        const float ef = C.fdes - f;
-        cst += C.wforce * ef * ef + C.wreg * f * f;
-      }
+    chain_ee(P.rb, c, ee);
+    float cst = motion_cost(C, pdes, Rd, ee);
+    if (contact) {
+      const float f = contact_force(C, plane, ee);
+      const float ef = C.fdes - f;
+      cst += C.wforce * ef * ef + C.wreg * f * f;
     }
     float cj = 0.f;
 #pragma unroll
@@ -1111,9 +1111,11 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
     if (s == T && C.wterm != 0.f)
       Sacc += static_cast<double>(C.wterm * motion_cost(C, pdes, Rd, ee));
   }
-  bar_sync(BAR_DONE, (COLL ? 4 : 2) * B);
-  double S = Sacc + *ws_s2(m, tid);
-  if (COLL) S += *ws_s2(m, tid, 1) + *ws_s2(m, tid, 2);
+  double S = Sacc;
+  if (COLL) {
+    bar_sync(BAR_DONE, 3 * B);
+    S += *ws_s2(m, tid, 0) + *ws_s2(m, tid, 1);
+  }
   return static_cast<float>(S);
 }
 
@@ -1135,9 +1137,8 @@ __device__ __forceinline__ void ws_draw(const ProbK& P, const float* plan, uint6
   }
 }
 
-// warp 2: forces of the odd links, the end-effector state and contact force
-// (for the dynamics and for the motion and force terms of l(x_s, v_{s-1}),
-// s = 1..T-1), and the inputs one step ahead
+// warp 2: forces of the odd links, the end-effector point and contact force
+// for the dynamics, and the inputs one step ahead
 template <bool STORE_NOISE, bool COLL>
 __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const float* plan,
                                          uint64_t iter, int k, bool live,
@@ -1147,24 +1148,16 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
   const int T = P.T;
   const CostK& C = P.cost;
   const bool contact = C.contact != 0;
-  const float pdes[3] = {in[14], in[15], in[16]};
-  float Rd[9];
-  {
-    const float qt[4] = {in[17], in[18], in[19], in[20]};
-    quat_to_R(qt, Rd);
-  }
   const float plane[4] = {in[21], in[22], in[23], in[24]};
-  double S2 = 0.0;
   for (int s = 0; s < T; ++s) {
     ws_forces<COLL>(P, m, 1, tid);
-    EEState ee;
-    float f;
     {
       bar_sync(BAR_LINK0 + NJ - 1, ws_link_count(NJ - 1, false, COLL));
       ChainState c;
       ws_load_chain(m.sc, NJ - 1, tid, c);
-      chain_ee(P.rb, c, ee);
-      f = contact ? contact_force(C, plane, ee) : 0.f;
+      EEState ee;
+      chain_ee_pv(P.rb, c, ee);
+      const float f = contact ? contact_force(C, plane, ee) : 0.f;
       float* ees = ws_ee(m, tid);
 #pragma unroll
       for (int a = 0; a < 3; ++a) ees[a] = ee.p[a];
@@ -1176,17 +1169,7 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
     if (s == 0) ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, 0, tid);
     bar_arrive(BAR_STEP, NA);
     if (s + 1 < T) ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, s + 1, tid);
-    if (s >= 1) {
-      float cst = motion_cost(C, pdes, Rd, ee);
-      if (contact) {
-        const float ef = C.fdes - f;
-        cst += C.wforce * ef * ef + C.wreg * f * f;
-      }
-      S2 += static_cast<double>(cst);
-    }
   }
-  *ws_s2(m, tid) = S2;
-  bar_arrive(BAR_DONE, (COLL ? 4 : 2) * B);
 }
 
 // Warps 3 and 4 (collision cost, Eq. 15): the link points of x_s are copied
@@ -1266,8 +1249,8 @@ __device__ __forceinline__ void ws_collision(const ProbK& P, const WsSmem& m, co
     if (s == 0) continue;
     Sc += static_cast<double>(C.wcoll * ws_collision_pairs<PART>(C, pts, s_obs, n_obs));
   }
-  *ws_s2(m, tid, 1 + PART) = Sc;
-  bar_arrive(BAR_DONE, 4 * WS_B);
+  *ws_s2(m, tid, PART) = Sc;
+  bar_arrive(BAR_DONE, 3 * WS_B);
 }
 
 template <bool STORE_NOISE, bool COLL = false>
