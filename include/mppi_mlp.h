@@ -77,6 +77,13 @@ MPPI_API int mppi_mlp_train_step(mppi_mlp_t m, const float* d_x, const float* d_
  * Needs n_in = 21 + 7T and n_out = 7T, at most 3 hidden layers and widths
  * <= 256 (MPPI_ERR_INVALID_ARG otherwise). */
 MPPI_API int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain);
+/* The timeout path of the bounded device waits: one mbarrier wait that
+ * nothing completes, given up after `cycles` SM clock cycles (1 ..
+ * about 2e9, the limit of the GEMMs' own waits) through the same helper and
+ * error flag; blocks until done and returns MPPI_ERR_TIMEOUT (clearing the
+ * flag), MPPI_ERR_INVALID_ARG for a bad argument.  The paper has no
+ * counterpart. */
+MPPI_API int mppi_mlp_check_wait(mppi_mlp_t m, long long cycles);
 
 #ifdef __cplusplus
 }

@@ -519,6 +519,15 @@ cudaError_t refresh_bf16(mppi_mlp_s* m) {
 }
 
 // MPPI_ERR_TIMEOUT when a GEMM's bounded wait gave up (read after a sync)
+// One bounded wait on an mbarrier that nothing completes, with the GEMMs'
+// wait helper and error flag (the flag set when the wait gives up).
+__global__ void wait_check_kernel(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mppi_tc::mbar_init(mppi_tc::smem_u32(&bar), 1);
+  __syncthreads();
+  if (!mppi_tc::mbar_wait(mppi_tc::smem_u32(&bar), 0, limit) && threadIdx.x == 0) *err = 1;
+}
+
 int check_err(mppi_mlp_s* m) {
   int h = 0;
   if (cudaMemcpy(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -657,6 +666,16 @@ int mppi_mlp_destroy(mppi_mlp_t m) {
   if (m->own_stream && m->st) cudaStreamDestroy(m->st);
   delete m;
   return MPPI_OK;
+}
+
+int mppi_mlp_check_wait(mppi_mlp_t m, long long cycles) {
+  if (!m || cycles < 1 || cycles > mppi_tc::WAIT_CYCLES)
+    return fail(MPPI_ERR_INVALID_ARG, "bad argument");
+  wait_check_kernel<<<1, 32, 0, m->st>>>(m->err, cycles);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  if (e != cudaSuccess) return fail(MPPI_ERR_CUDA, cudaGetErrorString(e));
+  return check_err(m);
 }
 
 int mppi_mlp_num_params(mppi_mlp_t m, size_t* n) {

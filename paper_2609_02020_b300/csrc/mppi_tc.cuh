@@ -95,10 +95,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
   return ok != 0;
 }
 // Bounded wait for the completion of phase `phase` of the barrier.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase,
+                                          long long limit = WAIT_CYCLES) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, phase))
-    if (clock64() - t0 > WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 

@@ -146,7 +146,7 @@ EXPORTS = [
     "mppi_mlp_create", "mppi_mlp_destroy", "mppi_mlp_num_params", "mppi_mlp_get_params",
     "mppi_mlp_set_params", "mppi_mlp_set_normalization", "mppi_mlp_fit_normalization",
     "mppi_mlp_forward",
-    "mppi_mlp_loss_grad", "mppi_mlp_train_step", "mppi_mlp_propose",
+    "mppi_mlp_loss_grad", "mppi_mlp_train_step", "mppi_mlp_propose", "mppi_mlp_check_wait",
 ]
 
 _lib = None
@@ -234,6 +234,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_mlp_loss_grad": ([H, vp, vp, C.c_int, fp, fp], C.c_int),
         "mppi_mlp_train_step": ([H, vp, vp, C.c_int, C.c_float, fp], C.c_int),
         "mppi_mlp_propose": ([H, H, vp, C.c_int], C.c_int),
+        "mppi_mlp_check_wait": ([H, C.c_longlong], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -807,6 +808,11 @@ class MLP:
         """Install the network's plan as ctl's second proposal for its next
         update, keeping n_plain samples around ctl's warm start."""
         self._check(self.lib.mppi_mlp_propose(self.h, ctl.h, _dptr(d_in), int(n_plain)))
+
+    def check_wait(self, cycles: int) -> int:
+        """Status of one bounded device wait that nothing completes
+        (ERR_TIMEOUT when the timeout path works)."""
+        return int(self.lib.mppi_mlp_check_wait(self.h, int(cycles)))
 
     def close(self):
         if getattr(self, "h", None):

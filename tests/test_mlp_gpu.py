@@ -131,3 +131,21 @@ def test_propose_installs_the_network_plan_as_second_proposal():
         ctl.close()
     for a, b in zip(res[0], res[1]):
         assert np.allclose(a, b, rtol=1e-4, atol=1e-4)
+
+
+def test_bounded_wait_reports_timeout():
+    # one mbarrier wait that nothing completes, given up after about 1 ms of
+    # SM clock through the GEMMs' wait helper and error flag: the status is
+    # TIMEOUT, the flag is cleared, and the context stays usable
+    import torch
+    m = net()
+    try:
+        assert m.check_wait(2_000_000) == mppi.ERR_TIMEOUT
+        assert m.check_wait(0) == mppi.ERR_INVALID_ARG
+        dX = torch.tensor(RNG.normal(size=(8, 147)).astype(np.float32), device="cuda")
+        dY = torch.zeros(8, 126, device="cuda")
+        m.forward(dX, dY)
+        torch.cuda.synchronize()
+        assert torch.isfinite(dY).all()
+    finally:
+        m.close()
