@@ -124,17 +124,22 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, fl
   z1 = __fmul_rn(r, fmaf(e, c, s));
 }
 
+// Normals 4 call .. 4 call + 3 of (sample k, step t, update iter): one
+// Philox4x32-10 call, two Box-Muller pairs.
+__device__ __forceinline__ void normals4(uint32_t k0, uint32_t k1, uint64_t iter, uint32_t k,
+                                         uint32_t t, uint32_t call, float z[4]) {
+  uint32_t c[4] = {k, 2u * t + call, static_cast<uint32_t>(iter),
+                   static_cast<uint32_t>(iter >> 32)};
+  philox4x32_10(c, k0, k1);
+  box_muller(c[0], c[1], z[0], z[1]);
+  box_muller(c[2], c[3], z[2], z[3]);
+}
+
 // The 8 normals of (sample k, step t, update iter); joints use z[0..6].
 __device__ __forceinline__ void normals8(uint32_t k0, uint32_t k1, uint64_t iter, uint32_t k,
                                          uint32_t t, float z[8]) {
-#pragma unroll
-  for (uint32_t call = 0; call < 2; ++call) {
-    uint32_t c[4] = {k, 2u * t + call, static_cast<uint32_t>(iter),
-                     static_cast<uint32_t>(iter >> 32)};
-    philox4x32_10(c, k0, k1);
-    box_muller(c[0], c[1], z[4 * call + 0], z[4 * call + 1]);
-    box_muller(c[2], c[3], z[4 * call + 2], z[4 * call + 3]);
-  }
+  normals4(k0, k1, iter, k, t, 0u, z);
+  normals4(k0, k1, iter, k, t, 1u, z + 4);
 }
 
 // ---------------------------------------------------------------------------
