@@ -745,10 +745,10 @@ def run_learned(args, rank, world):
     rows = []
     for name, K, mk in (
             [("plain", K, lambda K: learned.PlainMPPI(prob, K, seed=5, stream=s))
-             for K in (16384, 512, 2048)] +
+             for K in (16384, 512, 2048, 4096)] +
             [("learned", K, lambda K: learned.LearnedMPPI(prob, net, K, seed=5, stream=s,
                                                            plain_frac=0.5))
-             for K in (512, 2048)]):
+             for K in (512, 2048, 4096)]):
         c = mk(K)
         r = learned.evaluate(prob, c, episodes=args.episodes, steps=1000, seed=1, stream=s)
         c.close()
