@@ -752,7 +752,8 @@ constexpr int WS_REC = 52;
 constexpr int WS_HANDOFF = 6;  // float4 offset of the hand-off part
 constexpr int V_SLOTS = 3;            // ring of inputs v_s, slot s % 3
 // named barriers (0 is __syncthreads): one per link, link forces complete,
-// rows of M complete, inputs of the step complete
+// rows of M complete, inputs of the step complete, and (collision cost) the
+// collision warps' partial costs handed to warp 1
 constexpr int BAR_LINK0 = 1, BAR_FORCES = 8, BAR_MROWS = 9, BAR_STEP = 10, BAR_DONE = 11;
 constexpr int WS_FLOATS_PER_SAMPLE = NJ * WS_REC + NJ * (NJ + 1) / 2 + NJ /* h */ +
                                      2 * NJ /* q, qd */ + V_SLOTS * NJ /* v ring */;
