@@ -89,7 +89,11 @@ MPPI_API int mppi_server_poll(mppi_server_t srv, uint64_t ticket, float tau0[7],
 /* Blocks until the request has finished; as poll otherwise. */
 MPPI_API int mppi_server_wait(mppi_server_t srv, uint64_t ticket, float tau0[7]);
 
-/* Background scheduler thread (continuous batching) on/off. */
+/* Background scheduler thread (continuous batching) on/off.  While ticks
+ * are in flight, and for 2 ms after its last tick or request, the thread
+ * polls (yielding its core) rather than sleeping, so that new requests are
+ * admitted without a thread wake-up; after that it sleeps until a request
+ * arrives. */
 MPPI_API int mppi_server_start(mppi_server_t srv);
 MPPI_API int mppi_server_stop(mppi_server_t srv);
 /* One scheduling round from the calling thread, for use without the thread:

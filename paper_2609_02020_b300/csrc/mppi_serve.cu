@@ -636,8 +636,15 @@ bool idle_locked(const mppi_server_s* s) {
   return true;
 }
 
+// After the last tick or request the scheduler keeps polling (yielding its
+// core) for this long before it sleeps on the condition variable: a request
+// that arrives meanwhile is admitted within microseconds instead of after a
+// thread wake-up (tens of microseconds).
+constexpr double kSpinSeconds = 2e-3;
+
 void scheduler_main(mppi_server_s* s) {
   std::unique_lock<std::mutex> lk(s->mu);
+  double t_active = now_s();
   while (!s->stop_flag.load()) {
     int launched = 0;
     bool progress = false;
@@ -647,12 +654,13 @@ void scheduler_main(mppi_server_s* s) {
     }
     if (progress) {
       s->cv.notify_all();
+      t_active = now_s();
       continue;
     }
     bool any_busy = false;
     for (int l = 0; l < s->n_lanes; ++l) any_busy |= s->lanes[l].busy;
-    if (any_busy) {
-      // a tick is on the GPU: poll its event at a fine grain
+    if (any_busy || now_s() - t_active < kSpinSeconds) {
+      // a tick is on the GPU, or one may come soon: poll at a fine grain
       lk.unlock();
       std::this_thread::yield();
       lk.lock();
