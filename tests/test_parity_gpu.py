@@ -136,7 +136,8 @@ def test_contact_plan_matches_oracle(seed, variant):
 # here) even with exact arithmetic; the measured cost errors are 1e-7 to 8e-6
 # relative, well inside the 1e-4 cost bar.  Measured max |du*| (N m):
 # c22 weights, seeds 0-5: 5e-7 to 5.6e-5; contact seed 4 (n_eff 1.5, the two
-# best samples 1.4 lambda apart): 2.7e-3.  The bounds below guard those sizes.
+# best samples 1.4 lambda apart): 2.7e-3; contact at K = 4,194,304, T = 2
+# (n_eff 1.009, S_min 2169 lambda): 1.5e-4.  The bounds below guard those sizes.
 HEAVY_MISS_BOUND = {"c22": 1e-4, "contact": 5e-3}
 
 
@@ -445,6 +446,62 @@ def test_sweep_points_match_oracle(K, T, fp64):
     library's kernel choice, FP32 or FP64 reduction)."""
     c, o = oracle_full(1, K, T)
     assert_full_update(c, o, 0, fp64)
+
+
+@pytest.mark.parametrize("kind", ["free", "contact"])
+def test_max_samples_match_oracle(kind):
+    """K = MPPI_K_MAX (4,194,304) at T = 2: every cost, u*, tau0 and the
+    shifted plan against the oracle, and the noise of sampled columns (the
+    first and last 64 samples and 128 seeded ones) against the oracle's
+    Philox draw of Eq. 2.  Free space (parity weights) puts the weights of
+    Eq. 4a on nearly all 4M samples, so u* rests on the longest reduction the
+    library accepts, and meets the 1e-5 N m bar.  Contact puts them on one
+    sample (n_eff 1.009), but S_min is 2169 lambda and the second-best
+    sample, 5.4 lambda behind, still carries 0.4 % of the weight: one FP32
+    ulp of S_k is there 1.3e-4 lambda, the recorded-miss regime of
+    test_plan_recorded_miss_at_heavy_weights (measured max |du*| 1.5e-4 N m),
+    so it asserts that case's bound."""
+    K = 1 << 22
+    c = (make_case(2, cost=parity_cost(), K=K, T=2) if kind == "free"
+         else make_case(2, contact=True, K=K, T=2))
+    o = oracle_step(c, want_noise=False, nthreads=os.cpu_count() or 8)
+    assert o["rc"] == 0
+    with gpu_controller(c) as g:
+        tau0, plan = g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        out = dict(tau0=tau0, plan=plan, S=g.costs(), ustar=g.updated_plan())
+        noise = g.noise()
+    assert_costs(out["S"], o["S"])
+    assert np.argmin(out["S"]) == np.argmin(o["S"])
+    if kind == "free":
+        assert_plan(out, o)
+    else:
+        assert max(plan_errors(out, o)) <= HEAVY_MISS_BOUND["contact"]
+    cols = np.concatenate([np.arange(64), np.arange(K - 64, K),
+                           np.random.default_rng(9).integers(64, K - 64, 128)])
+    sig = np.broadcast_to(np.asarray(c["sigma"], dtype=np.float64), (7,))
+    for k in cols:
+        for t in range(c["T"]):
+            ref = sig * oracle.normals(SEED, 0, int(k), t)[:7]
+            assert np.abs(noise[t * 7:(t + 1) * 7, k] - ref).max() <= 1e-5, (k, t)
+
+
+@pytest.mark.parametrize("lam", [1e-3, 1e3])
+@pytest.mark.parametrize("seed", range(3))
+def test_extreme_temperature_matches_oracle(seed, lam):
+    """lambda three decades either side of the workload's: at 1e-3 the cost
+    gap between the two best samples is 30-300 lambda, so the weights of
+    Eq. 4a are one-hot and u* is the best sample's control; at 1e3 every
+    weight is within 1e-3 of the others and u* is close to the plain mean of
+    the samples.  Both meet the 1e-5 N m plan bar."""
+    c = make_case(seed, cost=parity_cost(), lam=lam)
+    g, o = run_pair(c)
+    assert_costs(g["S"], o["S"])
+    assert_plan(g, o)
+    assert abs(g["stats"][2] - o["stats"][2]) <= 1e-3 * o["stats"][2]
+    if lam < 1.0:
+        assert np.argmin(g["S"]) == np.argmin(o["S"]) and o["stats"][2] < 1.0 + 1e-6
+    else:
+        assert o["stats"][2] > 0.999 * c["K"]
 
 
 def test_rollout_device_matches_step_costs():
