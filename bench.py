@@ -104,6 +104,12 @@ def parse():
                          "proposal's network kernels alone")
     ap.add_argument("--pairs", type=int, default=200_000, help="learned mode: training pairs")
     ap.add_argument("--train-steps", type=int, default=3000, help="learned mode: Adam steps")
+    ap.add_argument("--label-k", type=int, default=131072,
+                    help="learned mode: samples of the plain MPPI that labels the pairs")
+    ap.add_argument("--on-policy-rounds", type=int, default=1,
+                    help="learned mode: rounds of pairs at the learned controller's own states")
+    ap.add_argument("--on-policy-pairs", type=int, default=100_000,
+                    help="learned mode: pairs per on-policy round")
     ap.add_argument("--episodes", type=int, default=12, help="learned mode: eval episodes")
     ap.add_argument("--rates", default="2000,5000,10000,20000,100000",
                     help="serve mode: arrival rates [updates/s]")
@@ -711,20 +717,36 @@ def run_mlp(args, rank, world):
 
 def run_learned(args, rank, world):
     """Learned proposal on the reaching task where plain MPPI at K=16384
-    converges (learned.tracking_problem): pairs from plain MPPI at K=16384,
-    training on the GPU with the library's tcgen05 BF16 kernels, then
-    closed-loop tracking cost, final position error and update latency of
-    plain MPPI (K=16384 and fewer samples) and of MPPI with the learned
-    proposal."""
+    converges (learned.tracking_problem): pairs from plain MPPI at
+    --label-k samples along its own closed loop, then rounds of pairs at the
+    states the learned controller visits (same labels), training on the GPU
+    with the library's tcgen05 BF16 kernels, then closed-loop tracking cost,
+    final position error and update latency of plain MPPI (K=16384, fewer
+    samples, and the labelling K) and of MPPI with the learned proposal."""
     import torch
     from paper_2609_02020_b300 import learned, mppi, synth
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     prob = learned.tracking_problem(rank)
     s = torch.cuda.Stream()
     t0 = time.perf_counter()
-    X, Y = learned.generate(prob, args.pairs, K=16384, seed=rank, episode_len=1000, stream=s)
+    X, Y = learned.generate(prob, args.pairs, K=args.label_k, seed=rank, episode_len=1000,
+                            stream=s)
     t_gen = time.perf_counter() - t0
     net, info = learned.train(X, Y, steps=args.train_steps, batch=1024, lr=1e-3, stream=s)
+    on_policy = []
+    for rnd in range(args.on_policy_rounds):
+        t1 = time.perf_counter()
+        Xd, Yd = learned.generate_on_policy(prob, net, args.on_policy_pairs, K_label=args.label_k,
+                                            K_learner=2048, plain_frac=0.5, seed=rank + 17 * rnd,
+                                            stream=s)
+        t_op = time.perf_counter() - t1
+        X, Y = torch.cat([X, Xd]), torch.cat([Y, Yd])
+        del Xd, Yd
+        net.close()
+        net, info = learned.train(X, Y, steps=args.train_steps + 1000, batch=1024, lr=1e-3,
+                                  seed=rnd + 1, stream=s)
+        on_policy.append({"round": rnd + 1, "pairs": int(X.shape[0]), "generation_s": t_op,
+                          "val_loss": info["val_loss"]})
     dims = [X.shape[1], 256, 256, 256, Y.shape[1]]
     flop_step = 3 * 2 * sum(dims[i] * dims[i + 1] for i in range(4)) * 1024
     # the proposal kernel alone: events around single launches on the handle's stream
@@ -745,7 +767,7 @@ def run_learned(args, rank, world):
     rows = []
     for name, K, mk in (
             [("plain", K, lambda K: learned.PlainMPPI(prob, K, seed=5, stream=s))
-             for K in (16384, 512, 2048, 4096)] +
+             for K in (16384, 512, 2048, 4096, args.label_k)] +
             [("learned", K, lambda K: learned.LearnedMPPI(prob, net, K, seed=5, stream=s,
                                                            plain_frac=0.5))
              for K in (512, 2048, 4096)]):
@@ -764,10 +786,14 @@ def run_learned(args, rank, world):
             "config": {"workload": "7-DoF seeded gravity-compensated arm (damping 5), "
                                    "position-only goals 0.2 rad per joint away, W_pos=300, "
                                    "sigma=2, lambda=3, T=18 dt=0.01, 1000-step (10 s) episodes",
-                       "pairs": args.pairs, "pairs_K": 16384,
+                       "pairs": args.pairs, "pairs_K": args.label_k,
+                       "on_policy": {"rounds": args.on_policy_rounds,
+                                     "pairs_per_round": args.on_policy_pairs,
+                                     "learner": "learned proposal, K=2048, half plain"},
                        "network": "147 -> 3 x 256 GELU -> 126, BF16 tcgen05, FP32 accumulate",
                        "plain_fallback_fraction": 0.5},
             "generation_s": t_gen,
+            "on_policy_rounds": on_policy,
             "training": {**{k: v for k, v in info.items()},
                          "gflop_per_step": flop_step / 1e9,
                          "tflops": flop_step * info["steps"] / info["seconds"] / 1e12,

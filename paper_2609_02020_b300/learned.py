@@ -4,7 +4,11 @@ Pipeline (every numerical step runs in the CUDA library):
   1. ``generate``: closed-loop episodes of plain MPPI (the paper's update)
      on the model used as a plant; every update gives one training pair
      x = (q, qd, goal, nominal plan u) -> y = u* - u (the correction plain
-     MPPI makes to its nominal plan).
+     MPPI makes to its nominal plan).  ``generate_on_policy`` adds pairs at
+     the states and warm starts that MPPI with the learned proposal itself
+     visits, labelled by plain MPPI (dataset aggregation, Ross et al.,
+     AISTATS 2011), so that the network also sees where its own closed loop
+     goes.
   2. ``train``: standardise x and y (statistics fitted by the library), then
      Adam on the mean squared error with the library's BF16 tensor-core
      (tcgen05) forward and backward kernels.
@@ -117,6 +121,52 @@ def generate(prob: Problem, n_pairs: int, *, K: int = 16384, seed: int = 0,
         ctl.sync()
         s.synchronize()
         ctl.close()
+    return X, Y
+
+
+def generate_on_policy(prob: Problem, net: mppi.MLP, n_pairs: int, *, K_label: int,
+                       K_learner: int, plain_frac: float = 0.5, seed: int = 0,
+                       episode_len: int = 1000, stream=None):
+    """Pairs at the states MPPI with the learned proposal visits: the learned
+    controller (K_learner samples) drives the plant; at every update plain
+    MPPI with K_label samples starts from the same state and the learned
+    controller's warm start, and its correction u* - u is the label."""
+    import torch
+    s = stream or torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        lc = LearnedMPPI(prob, net, K_learner, seed=0xA11CE + seed, stream=s,
+                         plain_frac=plain_frac)
+        ex = prob.controller(K_label, seed=0xBEEF + seed, stream=s)
+        helper = prob.controller(1, seed=1, stream=s)
+        X = torch.empty(n_pairs, n_in(prob.T), device="cuda")
+        Y = torch.empty(n_pairs, 7 * prob.T, device="cuda")
+        d_in = torch.empty(1, 25, device="cuda")
+        d_tau = torch.empty(1, 7, device="cuda")
+        d_tau_ex = torch.empty(1, 7, device="cuda")
+        d_x = torch.empty(1, 14, device="cuda")
+        plan = torch.empty(prob.T * 7, device="cuda")
+        i, ep = 0, 0
+        while i < n_pairs:
+            q, qd, goal = prob.episode_start(3_000_000 * (seed + 1) + ep, helper)
+            d_in.copy_(torch.tensor(mppi.pack_inputs(q, qd, goal, prob.plane))[None])
+            lc.reset(prob.hold_plan(helper, q))
+            for _ in range(min(episode_len, n_pairs - i)):
+                X[i, :21].copy_(d_in[0, :21])
+                lc.ctl.get_plan_device(plan)
+                X[i, 21:].copy_(plan)
+                ex.set_plan_device(plan)
+                ex.step_device(d_in[0], d_tau_ex[0], None)
+                ex.correction_device(Y[i])
+                lc.step_device(d_in[0], d_tau[0])
+                helper.simulate_device(d_in, d_tau, d_x, prob.substeps)
+                d_in[0, :14].copy_(d_x[0])
+                i += 1
+            ep += 1
+        ex.sync()
+        s.synchronize()
+        lc.close()
+        ex.close()
+        helper.close()
     return X, Y
 
 
