@@ -60,8 +60,10 @@ L2_FLUSH_BYTES = 256 << 20  # twice the 126 MB L2
 # polynomials included) is kept beside it.  The optional cost terms have no
 # hand count; their lines use the executed count and say so.
 FLOP_PER_ROLLOUT_STEP = {"contact": 4311.0}
-FLOP_EXECUTED_PER_ROLLOUT_STEP = {"contact": 4970.2, "force_estimate": 6167.6,
-                                  "collision": 6811.0}
+FLOP_EXECUTED_PER_ROLLOUT_STEP = {("contact", "rollout_kernel_ws"): 4970.2,
+                                  ("force_estimate", "rollout_kernel_ws_fest"): 6159.1,
+                                  ("force_estimate", "rollout_kernel_rolled"): 6167.6,
+                                  ("collision", "rollout_kernel_ws"): 6811.0}
 # DRAM read + write bytes of one rollout launch at K=16384, T=18 per (cost,
 # kernel) (ncu dram__bytes_{read,write}.sum, mean of two launches).  The
 # 8.3 MB of stored noise stays in L2 and is not written back inside the
@@ -69,6 +71,7 @@ FLOP_EXECUTED_PER_ROLLOUT_STEP = {"contact": 4970.2, "force_estimate": 6167.6,
 # Only kernels captured since their last change are listed; the others
 # report null.
 ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel_ws"): 61184,
+                                    ("force_estimate", "rollout_kernel_ws_fest"): 73728,
                                     ("force_estimate", "rollout_kernel_rolled"): 67840,
                                     ("collision", "rollout_kernel_ws"): 132864}
 COSTS = ("contact", "force_estimate", "collision")
@@ -340,10 +343,11 @@ def run_ours(args, rank, world):
     if args.cost == "collision":
         ctl.set_obstacles(obstacles(rank, arm, pose[:3]))
     # variant 0 picks the warp-specialised kernel (with the collision cost on
-    # its two extra warps) while its blocks fit in one wave, the rolled kernel
-    # for the wrench-estimate cost, the register kernel for larger K
+    # two extra warps, the wrench estimate on one) while its blocks fit in one
+    # wave, else the register kernel, or the rolled one with an optional cost
     kname = {1: "rollout_kernel", 2: "rollout_kernel_rolled",
-             3: "rollout_kernel_ws"}[ctl.variant()]
+             3: "rollout_kernel_ws_fest" if args.cost == "force_estimate"
+             else "rollout_kernel_ws"}[ctl.variant()]
     plane = synth.plane_through(float(pose[2]))
     d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, plane), device="cuda")
     d_tau = torch.zeros(7, device="cuda")
@@ -422,25 +426,27 @@ def run_ours(args, rank, world):
     clocks = clk.summary(spans)
     peak_max = SM_COUNT * FP32_LANES_PER_SM * 2 * 2032e6 / 1e12
     flop = FLOP_PER_ROLLOUT_STEP.get(args.cost)
-    flop_exec = FLOP_EXECUTED_PER_ROLLOUT_STEP[args.cost]
+    flop_exec = FLOP_EXECUTED_PER_ROLLOUT_STEP.get((args.cost, kname))
     num = flop if flop else flop_exec
-    achieved = num * K * T / (ms_roll * 1e-3) / 1e12
+    achieved = num * K * T / (ms_roll * 1e-3) / 1e12 if num else None
     traffic = (ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH.get((args.cost, kname))
                if (K, T) == (K_DEFAULT, T_DEFAULT) else None)
     fma = mppi.measure_fp32_peak()  # outside the timed regions
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
-            "frac": achieved / peak_max, "traffic": traffic,
+            "frac": achieved / peak_max if achieved else None, "traffic": traffic,
             "kernel": kname, "kernel_ms": ms_roll,
             "flop_per_rollout_step": num,
             "flop_source": ("algorithmic, counted by hand on the formulation" if flop else
                             "executed (ncu FADD + FMUL + 2 FFMA); no hand count for this cost"),
             "flop_executed_per_rollout_step": flop_exec,
-            "frac_executed": flop_exec * K * T / (ms_roll * 1e-3) / 1e12 / peak_max,
+            "frac_executed": (flop_exec * K * T / (ms_roll * 1e-3) / 1e12 / peak_max
+                              if flop_exec else None),
             "peak_note": "FP32 peak of 148 SMs x 128 lanes x 2 FLOP at the 2032 MHz "
                          "maximum SM clock (derived; no measured FP32 peak is on file); "
                          "peak_fma_measured: independent FMA chains on every SM of this "
                          "GPU, median of five launches",
-            "peak_fma_measured": fma, "frac_of_fma_measured": achieved / fma}
+            "peak_fma_measured": fma,
+            "frac_of_fma_measured": achieved / fma if achieved else None}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -123,12 +123,12 @@ typedef struct mppi_robot {
  * The obstacles are read by every update from a device buffer of the handle,
  * set at creation from n_obstacles / obstacles and replaced by
  * mppi_set_obstacles[_device] between updates (also under CUDA graphs).
- * The wrench-estimate cost runs in the rolled rollout kernel (variant 0
- * selects it; variants 1 and 3 are rejected).  The collision cost alone runs
- * on two more warps of the warp-specialised kernel while its blocks for K
- * samples fit on the device at once, else in the rolled kernel (variant 0
- * chooses; 2 and 3 force one; 1 is rejected).  mppi_step_static and the
- * server take neither cost. */
+ * Either optional cost alone runs on more warps of the warp-specialised
+ * kernel (the collision cost on two, the wrench estimate on one) while its
+ * blocks for K samples fit on the device at once, else in the rolled kernel
+ * (variant 0 chooses; 2 and 3 force one; 1 is rejected).  Both together run
+ * in the rolled kernel (variant 0 or 2; 1 and 3 are rejected).
+ * mppi_step_static and the server take neither cost. */
 typedef struct mppi_cost {
   double w_pos[3], w_ori[3];
   double w_force, f_des, w_reg;
@@ -297,10 +297,10 @@ MPPI_API int mppi_force_estimate_device(mppi_t h, const float* d_q, const float*
 MPPI_API int mppi_get_correction_device(mppi_t h, float* d_out);
 
 /* The rollout kernel the handle runs (1, 2 or 3 as in mppi_config.variant;
- * variant 0 resolves at creation: with the wrench-estimate cost the rolled
- * kernel; otherwise the warp-specialised kernel while its blocks for K
- * samples fit on the device at once, else the register kernel, or the rolled
- * kernel when the collision cost is on; see mppi_cost). */
+ * variant 0 resolves at creation: the warp-specialised kernel while its
+ * blocks for K samples fit on the device at once, else the register kernel,
+ * or the rolled kernel when an optional cost is on; with both optional costs
+ * the rolled kernel; see mppi_cost). */
 MPPI_API int mppi_get_variant(mppi_t h, int* variant);
 
 /* End-effector pose (p xyz, quaternion wxyz) at joint angles q, computed on

@@ -734,6 +734,12 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
 //     state and then charges all of l(x_s, v_{s-1}); warp 2 draws v_{s+1}
 //     one step ahead (v_0 at s = 0).
 //   At s = T warp 1 charges l(x_T, v_{T-1}) and phi(x_T).
+// With the collision cost (Eq. 15) warps 3 and 4 charge it from the link
+// points; with the wrench-estimate cost (Eq. 12-13) warp 3 forms the
+// end-effector Jacobian and the gravity torque at x_s after the forces and,
+// past the step barrier (by then warp 0 has left the factors of M(x_s) in
+// the rows' slots and warp 2 has drawn v_s), the estimate and its cost, off
+// the critical path.
 // Hand-offs go through shared memory under named barriers with fixed
 // arrival counts.  Per state every barrier sees the same arrivals, and each
 // slot is rewritten only after its readers have passed a barrier that the
@@ -752,8 +758,8 @@ constexpr int WS_REC = 52;
 constexpr int WS_HANDOFF = 6;  // float4 offset of the hand-off part
 constexpr int V_SLOTS = 3;            // ring of inputs v_s, slot s % 3
 // named barriers (0 is __syncthreads): one per link, link forces complete,
-// rows of M complete, inputs of the step complete, and (collision cost) the
-// collision warps' partial costs handed to warp 1
+// rows of M complete, inputs of the step complete, and (collision or
+// wrench-estimate cost) the extra warps' partial costs handed to warp 1
 constexpr int BAR_LINK0 = 1, BAR_FORCES = 8, BAR_MROWS = 9, BAR_STEP = 10, BAR_DONE = 11;
 constexpr int WS_FLOATS_PER_SAMPLE = NJ * WS_REC + NJ * (NJ + 1) / 2 + NJ /* h */ +
                                      2 * NJ /* q, qd */ + V_SLOTS * NJ /* v ring */;
@@ -779,9 +785,15 @@ __device__ __forceinline__ void bar_arrive(int id, int count) {
 __host__ __device__ constexpr int ws_link_count(int i, bool last_state, bool coll) {
   return last_state ? (coll ? 4 : 2) * WS_B : (coll && i == NJ - 1 ? 3 : 2) * WS_B;
 }
-// Warps of the kernel, and threads at the barriers every warp meets.
-__host__ __device__ constexpr int ws_warps(bool coll) { return coll ? 5 : 3; }
-__host__ __device__ constexpr int ws_threads(bool coll) { return ws_warps(coll) * WS_B; }
+// Warps of the kernel, and threads at the barriers every warp meets: three,
+// two more for the collision cost, one more for the wrench-estimate cost
+// (the two optional costs together run in the rolled kernel).
+__host__ __device__ constexpr int ws_warps(bool coll, bool fest) {
+  return 3 + (coll ? 2 : 0) + (fest ? 1 : 0);
+}
+__host__ __device__ constexpr int ws_threads(bool coll, bool fest) {
+  return ws_warps(coll, fest) * WS_B;
+}
 
 // Dynamic shared memory of rollout_kernel_ws (independent of T: the plans
 // are read from global memory, where they stay in L1).  56.2 KB: four
@@ -954,10 +966,10 @@ constexpr unsigned WS_ROWS1 = (1u << 5) | (1u << 2) | (1u << 1);
 constexpr unsigned WS_ROWS2 = (1u << 4) | (1u << 3) | (1u << 0);
 
 // warp 0
-template <bool COLL>
+template <bool COLL, bool FEST>
 __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, const WsSmem& m,
                                             int tid) {
-  constexpr int NA = ws_threads(COLL);
+  constexpr int NA = ws_threads(COLL, FEST);
   constexpr int B = WS_B;
   const int T = P.T;
   const CostK& C = P.cost;
@@ -1000,6 +1012,17 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
 #pragma unroll
     for (int a = 0; a < NJ * (NJ + 1) / 2; ++a) M[a] = m.sM[a * B + tid];
     ldlt_factor<NJ, true>(M, invD);
+    if (FEST) {
+      // the factors of M(x_s) for warp 3's wrench estimate, in the rows'
+      // slots (free until the next state's rows): L below the diagonal,
+      // 1/D on it; warp 3 reads them past the step barrier
+#pragma unroll
+      for (int i = 0; i < NJ; ++i) {
+#pragma unroll
+        for (int j = 0; j < i; ++j) m.sM[(i * (i + 1) / 2 + j) * B + tid] = M[i * (i + 1) / 2 + j];
+        m.sM[(i * (i + 1) / 2 + i) * B + tid] = invD[i];
+      }
+    }
     bar_sync(BAR_STEP, NA);
     const float* v = m.sv + (s % V_SLOTS) * NJ * B + tid;
     const float* ees = ws_ee(m, tid);
@@ -1050,10 +1073,11 @@ __device__ __forceinline__ void ws_forces(const ProbK& P, const WsSmem& m, int f
 
 // warp 1: forces of links 0, 2, 4 (and 6 with the collision cost) and the
 // running cost; returns S_k
-template <bool COLL>
+template <bool COLL, bool FEST>
 __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const WsSmem& m,
                                           int tid) {
-  constexpr int NA = ws_threads(COLL);
+  static_assert(!(COLL && FEST), "the two optional costs together run in the rolled kernel");
+  constexpr int NA = ws_threads(COLL, FEST);
   constexpr int B = WS_B;
   const int T = P.T;
   const CostK& C = P.cost;
@@ -1095,7 +1119,7 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
     chain_ee(P.rb, c, ee);
     const float mc = motion_cost(C, pdes, Rd, ee);
     float cst = mc;
-    if (contact) {
+    if (contact && !FEST) {
       const float f = contact_force(C, plane, ee);
       const float ef = C.fdes - f;
       cst += C.wforce * ef * ef + C.wreg * f * f;
@@ -1117,6 +1141,10 @@ __device__ __forceinline__ float ws_costs(const ProbK& P, const float* in, const
   if (COLL) {
     bar_sync(BAR_DONE, 3 * B);
     S += *ws_s2(m, tid, 0) + *ws_s2(m, tid, 1);
+  }
+  if (FEST) {
+    bar_sync(BAR_DONE, 2 * B);
+    S += *ws_s2(m, tid, 0);
   }
   return static_cast<float>(S);
 }
@@ -1147,11 +1175,11 @@ __device__ __forceinline__ void ws_draw(const ProbK& P, const float* plan, uint6
 
 // warp 2: forces of the odd links, the end-effector point and contact force
 // for the dynamics, and the inputs one step ahead
-template <bool STORE_NOISE, bool COLL>
+template <bool STORE_NOISE, bool COLL, bool FEST>
 __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const float* plan,
                                          uint64_t iter, int k, bool live,
                                          float* __restrict__ noise, const WsSmem& m, int tid) {
-  constexpr int NA = ws_threads(COLL);
+  constexpr int NA = ws_threads(COLL, FEST);
   constexpr int B = WS_B;
   const int T = P.T;
   const CostK& C = P.cost;
@@ -1223,7 +1251,7 @@ __device__ __forceinline__ float ws_collision_pairs(const CostK& C, const float 
 template <int PART>
 __device__ __forceinline__ void ws_collision(const ProbK& P, const WsSmem& m, const float* s_obs,
                                              int n_obs, int tid) {
-  constexpr int NA = ws_threads(true);
+  constexpr int NA = ws_threads(true, false);
   const int T = P.T;
   const CostK& C = P.cost;
   double Sc = 0.0;
@@ -1261,14 +1289,121 @@ __device__ __forceinline__ void ws_collision(const ProbK& P, const WsSmem& m, co
   bar_arrive(BAR_DONE, 3 * WS_B);
 }
 
-template <bool STORE_NOISE, bool COLL = false>
-__global__ void __launch_bounds__(ws_threads(COLL))
-rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
-                  const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
-                  float* __restrict__ S, float* __restrict__ noise,
-                  const float* __restrict__ prop = nullptr,
-                  const int* __restrict__ ksplit_p = nullptr,
-                  const ObsK* __restrict__ obs = nullptr, float* __restrict__ part = nullptr) {
+// Warp 3 with the wrench-estimate cost (Eq. 12-13): for each x_s, s < T,
+// the rows of the end-effector Jacobian (linear: w_j + z_j x p; angular:
+// z_j) and g(q_s), from the subtree masses and first moments, are formed
+// from the hand-off records between the forces and the step barriers (warp
+// 0 rewrites the records only past the step barrier); past it, tau = v_s -
+// g, the factors of M(q_s) that warp 0 left in the rows' slots before the
+// barrier, and the estimate F = Jbar^T tau of force_estimate (Y = L^-1 J^T,
+// A = Y^T D^-1 Y, F = A^-1 Y^T D^-1 L^-1 tau) and its cost, NaN at a
+// kinematic singularity.  The rows' slots are rewritten only after the next
+// forces barrier, which this warp reaches once it is done.  Same terms, in
+// the same order per quantity, as force_estimate and force_estimate_cost,
+// with Y in registers.
+__device__ __forceinline__ void ws_estimate(const ProbK& P, const WsSmem& m, int tid) {
+  constexpr int NA = ws_threads(false, true);
+  constexpr int B = WS_B;
+  const int T = P.T;
+  const CostK& C = P.cost;
+  double Sf = 0.0;
+  for (int s = 0; s < T; ++s) {
+    float Y[6][NJ], g[NJ];
+    bar_sync(BAR_FORCES, NA);
+    {
+      const float* ees = ws_ee(m, tid);
+      const float p[3] = {ees[0], ees[1], ees[2]};
+      float Ic[4] = {0.f, 0.f, 0.f, 0.f};  // subtree mass and first moment
+#pragma unroll
+      for (int ii = 0; ii < NJ; ++ii) {
+        const int i = NJ - 1 - ii;
+        float z[3], w[3], zp[3];
+        ws_load_axis(m.sl, i, tid, z, w);
+        const float4* r = ws_rec(m.sl, i, tid);
+        const float4 b = r[3], c = r[4];  // (F4 F5 I0 I1)(I2 I3 I4 I5)
+        Ic[0] += b.z; Ic[1] += b.w; Ic[2] += c.x; Ic[3] += c.y;
+        float mcg[3];
+        cross3(Ic + 1, P.rb.g, mcg);
+        g[i] = -(dot3(z, mcg) + Ic[0] * dot3(w, P.rb.g));
+        cross3(z, p, zp);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          Y[a][i] = w[a] + zp[a];
+          Y[3 + a][i] = z[a];
+        }
+      }
+    }
+    bar_sync(BAR_STEP, NA);
+    float tau[NJ];
+    const float* v = m.sv + (s % V_SLOTS) * NJ * B + tid;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) tau[j] = v[j * B] - g[j];
+    float L[NJ * (NJ + 1) / 2], invD[NJ];
+#pragma unroll
+    for (int i = 0; i < NJ; ++i) {
+#pragma unroll
+      for (int j = 0; j < i; ++j) L[i * (i + 1) / 2 + j] = m.sM[(i * (i + 1) / 2 + j) * B + tid];
+      invD[i] = m.sM[(i * (i + 1) / 2 + i) * B + tid];
+      L[i * (i + 1) / 2 + i] = 1.f;
+    }
+    float lt[NJ];
+    unit_lower_solve<NJ>(L, tau, lt);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) lt[j] *= invD[j];  // D^-1 L^-1 tau
+    float b6[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      float y[NJ];
+      unit_lower_solve<NJ>(L, Y[r], y);
+      float br = 0.f;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        Y[r][j] = y[j];
+        br = fmaf(y[j], lt[j], br);
+      }
+      b6[r] = br;
+    }
+    float A[21];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      float u[NJ];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) u[j] = Y[r][j] * invD[j];
+#pragma unroll
+      for (int c = 0; c <= r; ++c) {
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) acc = fmaf(u[j], Y[c][j], acc);
+        A[r * (r + 1) / 2 + c] = acc;
+      }
+    }
+    float invDA[6], yb[6], F[6];
+    ldlt_factor<6>(A, invDA);
+    unit_lower_solve<6>(A, b6, yb);
+    ldlt_back<6>(A, invDA, yb, F);
+    bool ok = true;
+    float cf = 0.f;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      ok = ok && invDA[a] > 0.f && invDA[a] < INFINITY;
+      const float e = C.fdes6[a] - F[a];
+      cf = fmaf(C.wf6[a], e * e, fmaf(C.wreg6[a], F[a] * F[a], cf));
+    }
+    Sf += static_cast<double>(ok ? cf : NAN);
+  }
+  *ws_s2(m, tid, 0) = Sf;
+  bar_arrive(BAR_DONE, 2 * WS_B);
+}
+
+template <bool STORE_NOISE, bool COLL, bool FEST>
+__device__ __forceinline__ void rollout_ws_block(const ProbK& P, const float* __restrict__ in,
+                                                 const unsigned long long* __restrict__ iter_p,
+                                                 const float* __restrict__ plan,
+                                                 float* __restrict__ S, float* __restrict__ noise,
+                                                 const float* __restrict__ prop,
+                                                 const int* __restrict__ ksplit_p,
+                                                 const ObsK* __restrict__ obs,
+                                                 float* __restrict__ part) {
   extern __shared__ float4 dsm4[];
   float* dsm = reinterpret_cast<float*>(dsm4);
   const int K = P.K;
@@ -1305,24 +1440,53 @@ rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
   const int k = live ? k_raw : K - 1;
   __shared__ float s_S[WS_B], s_w[WS_B];
   if (warp == 0) {
-    ws_dynamics<COLL>(P, s_in, m, lane);
+    ws_dynamics<COLL, FEST>(P, s_in, m, lane);
   } else if (warp == 1) {
-    const float Sk = ws_costs<COLL>(P, s_in, m, lane);
+    const float Sk = ws_costs<COLL, FEST>(P, s_in, m, lane);
     if (live) S[k] = Sk;
     s_S[lane] = Sk;
   } else if (warp == 2) {
-    ws_noise<STORE_NOISE, COLL>(P, s_in, k < k_split ? plan : prop, *iter_p, k, live, noise, m,
-                                lane);
+    ws_noise<STORE_NOISE, COLL, FEST>(P, s_in, k < k_split ? plan : prop, *iter_p, k, live, noise,
+                                      m, lane);
   } else if (COLL) {
     if (warp == 3) ws_collision<0>(P, m, s_obs, n_obs, lane);
     else ws_collision<1>(P, m, s_obs, n_obs, lane);
+  } else if (FEST) {
+    ws_estimate(P, m, lane);
   }
   if (STORE_NOISE && part) {
     const int k0 = blockIdx.x * WS_B;
-    block_partial<ws_threads(COLL)>(s_S, s_w, k0, min(WS_B, K - k0), K, P.T, P.lambda, k_split,
+    block_partial<ws_threads(COLL, FEST)>(s_S, s_w, k0, min(WS_B, K - k0), K, P.T, P.lambda, k_split,
                                     noise, part + static_cast<size_t>(blockIdx.x) * part_stride(P.T));
   }
   allow_dependent_launch();
+}
+
+// The warp-specialised rollout (three warps per 32 samples, two more with the
+// collision cost).
+template <bool STORE_NOISE, bool COLL = false>
+__global__ void __launch_bounds__(ws_threads(COLL, false))
+rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
+                  const unsigned long long* __restrict__ iter_p, const float* __restrict__ plan,
+                  float* __restrict__ S, float* __restrict__ noise,
+                  const float* __restrict__ prop = nullptr,
+                  const int* __restrict__ ksplit_p = nullptr,
+                  const ObsK* __restrict__ obs = nullptr, float* __restrict__ part = nullptr) {
+  rollout_ws_block<STORE_NOISE, COLL, false>(P, in, iter_p, plan, S, noise, prop, ksplit_p, obs,
+                                             part);
+}
+
+// The same with the wrench-estimate warp: four 128-thread blocks per SM (the
+// shared-memory limit) need at most 128 registers per thread.
+template <bool STORE_NOISE>
+__global__ void __launch_bounds__(ws_threads(false, true), 4)
+rollout_kernel_ws_fest(const __grid_constant__ ProbK P, const float* __restrict__ in,
+                       const unsigned long long* __restrict__ iter_p,
+                       const float* __restrict__ plan, float* __restrict__ S,
+                       float* __restrict__ noise, const float* __restrict__ prop,
+                       const int* __restrict__ ksplit_p, float* __restrict__ part) {
+  rollout_ws_block<STORE_NOISE, false, true>(P, in, iter_p, plan, S, noise, prop, ksplit_p,
+                                             nullptr, part);
 }
 
 // Wrench estimates F = Jbar^T (v - g(q)) (Eq. 13) for n pairs (q_i, v_i),

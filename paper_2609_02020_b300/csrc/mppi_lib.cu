@@ -28,18 +28,24 @@ using namespace mppi_dev;
 //   ws        67      75      93     174     184     344
 //   rolled   114     104     103     139     139     268
 //   register 114     128     127     125     122     214
-// The rolled kernel carries the optional cost terms.
-// With the collision cost (coll) the alternative is the rolled kernel.
-static int default_variant(int K, bool coll = false) {
-  const int other = coll ? 2 : 1;
+// The rolled kernel carries every optional cost term; the warp-specialised
+// kernel the collision cost or the wrench-estimate cost alone.  With one of
+// those (coll, fest) the alternative is the rolled kernel.
+static int default_variant(int K, bool coll, bool fest) {
+  const int other = (coll || fest) ? 2 : 1;
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = coll ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel_ws<true, true>,
-                                                             ws_threads(true), ws_smem_bytes(true))
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rollout_kernel_ws<true>,
-                                                             ws_threads(false), ws_smem_bytes());
+    e = coll ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                   &per_sm, rollout_kernel_ws<true, true>, ws_threads(true, false),
+                   ws_smem_bytes(true))
+        : fest ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     &per_sm, rollout_kernel_ws_fest<true>, ws_threads(false, true),
+                     ws_smem_bytes(false))
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     &per_sm, rollout_kernel_ws<true, false>, ws_threads(false, false),
+                     ws_smem_bytes(false));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return other;
@@ -369,6 +375,14 @@ cudaError_t prepare_rollout(mppi_s* h) {
     return cudaFuncSetAttribute(rollout_kernel_ws<false, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   }
+  if (h->feat == FEAT_FEST && h->variant == 3) {
+    const int smem = static_cast<int>(ws_smem_bytes(false));
+    cudaError_t e = cudaFuncSetAttribute(rollout_kernel_ws_fest<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(rollout_kernel_ws_fest<false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
   switch (h->feat) {
     case FEAT_FEST: return prepare_rolled<FEAT_FEST>(h->P.T);
     case FEAT_COLL: return prepare_rolled<FEAT_COLL>(h->P.T);
@@ -378,11 +392,11 @@ cudaError_t prepare_rollout(mppi_s* h) {
   if (h->variant == 2) return prepare_rolled<0>(h->P.T);
   if (h->variant == 3) {
     const size_t smem = ws_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(rollout_kernel_ws<true>,
+    cudaError_t e = cudaFuncSetAttribute(rollout_kernel_ws<true, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(rollout_kernel_ws<false>,
+    return cudaFuncSetAttribute(rollout_kernel_ws<false, false>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   }
   return cudaSuccess;
@@ -399,11 +413,23 @@ cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float*
     const int wgrid = (h->P.K + WS_B - 1) / WS_B;
     const size_t smem = ws_smem_bytes(true);
     if (noise)
-      rollout_kernel_ws<true, true><<<wgrid, ws_threads(true), smem, h->stream>>>(
+      rollout_kernel_ws<true, true><<<wgrid, ws_threads(true, false), smem, h->stream>>>(
           h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, h->d_obs, part);
     else
-      rollout_kernel_ws<false, true><<<wgrid, ws_threads(true), smem, h->stream>>>(
+      rollout_kernel_ws<false, true><<<wgrid, ws_threads(true, false), smem, h->stream>>>(
           h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, h->d_obs, nullptr);
+    return cudaGetLastError();
+  }
+  if (h->feat == FEAT_FEST && h->variant == 3) {
+    // the wrench-estimate cost on a fourth warp of the warp-specialised kernel
+    const int wgrid = (h->P.K + WS_B - 1) / WS_B;
+    const size_t smem = ws_smem_bytes(false);
+    if (noise)
+      rollout_kernel_ws_fest<true><<<wgrid, ws_threads(false, true), smem, h->stream>>>(
+          h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, part);
+    else
+      rollout_kernel_ws_fest<false><<<wgrid, ws_threads(false, true), smem, h->stream>>>(
+          h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, nullptr);
     return cudaGetLastError();
   }
   // the optional cost terms run in the rolled kernel only
@@ -419,10 +445,10 @@ cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float*
     const int wgrid = (h->P.K + WS_B - 1) / WS_B;
     const size_t smem = ws_smem_bytes();
     if (noise)
-      rollout_kernel_ws<true><<<wgrid, WS_THREADS, smem, h->stream>>>(
+      rollout_kernel_ws<true, false><<<wgrid, WS_THREADS, smem, h->stream>>>(
           h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, nullptr, part);
     else
-      rollout_kernel_ws<false><<<wgrid, WS_THREADS, smem, h->stream>>>(
+      rollout_kernel_ws<false, false><<<wgrid, WS_THREADS, smem, h->stream>>>(
           h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, nullptr, nullptr);
     return cudaGetLastError();
   }
@@ -669,19 +695,19 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
     return fail(nullptr, MPPI_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   }
   h->feat = (h->P.cost.fest ? FEAT_FEST : 0) | (h->P.cost.coll ? FEAT_COLL : 0);
-  if ((h->feat && cfg->variant == 1) || ((h->feat & FEAT_FEST) && cfg->variant == 3)) {
+  if ((h->feat && cfg->variant == 1) || (h->feat == (FEAT_FEST | FEAT_COLL) && cfg->variant == 3)) {
     delete h;
     return fail(nullptr, MPPI_ERR_INVALID_ARG,
-                "the wrench-estimate cost needs the rolled rollout kernel (variant 0 or 2), "
-                "the collision cost the rolled or warp-specialised one (variant 0, 2 or 3)");
+                "the optional costs need the rolled rollout kernel (variant 0 or 2) or, one at a "
+                "time, the warp-specialised one (variant 3)");
   }
-  if ((h->feat == 0 || h->feat == FEAT_COLL) && cfg->variant == 0) {
+  if (h->feat != (FEAT_FEST | FEAT_COLL) && cfg->variant == 0) {
     // the occupancy query needs the ws kernel's shared-memory opt-in first
     h->variant = 3;
     if (prepare_rollout(h) != cudaSuccess) cudaGetLastError();
-    h->variant = default_variant(cfg->K, h->feat == FEAT_COLL);
+    h->variant = default_variant(cfg->K, h->feat == FEAT_COLL, h->feat == FEAT_FEST);
   } else {
-    h->variant = (h->feat & FEAT_FEST) ? 2 : cfg->variant;
+    h->variant = cfg->variant == 0 ? 2 : cfg->variant;
   }
   const int T = cfg->T, K = cfg->K;
   auto bail = [&](cudaError_t e, const char* what) {

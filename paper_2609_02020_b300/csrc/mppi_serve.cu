@@ -191,12 +191,12 @@ serve_rollout_kernel_ws(const char* __restrict__ desc, const ProbK* __restrict__
     const bool live = k_raw < I.K;
     const int k = live ? k_raw : I.K - 1;
     if (warp == 0) {
-      ws_dynamics<false>(*sP, s_in, m, lane);
+      ws_dynamics<false, false>(*sP, s_in, m, lane);
     } else if (warp == 1) {
-      const float Sk = ws_costs<false>(*sP, s_in, m, lane);
+      const float Sk = ws_costs<false, false>(*sP, s_in, m, lane);
       if (live) I.S[k] = Sk;
     } else {
-      ws_noise<true, false>(*sP, s_in, I.plan, I.iter, k, live, I.noise, m, lane);
+      ws_noise<true, false, false>(*sP, s_in, I.plan, I.iter, k, live, I.noise, m, lane);
     }
     __syncthreads();
   }

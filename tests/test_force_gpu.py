@@ -120,21 +120,25 @@ def _assert_costs(S_gpu, S_orc):
     assert bad.size == 0, f"{bad.size} costs off, worst rel {np.max(err / np.abs(S_orc)):.3e}"
 
 
+# variant 2: the rolled kernel; 3: the warp-specialised kernel with the
+# estimate on a fourth warp
+@pytest.mark.parametrize("variant", [2, 3])
 @pytest.mark.parametrize("seed", range(5))
 @pytest.mark.parametrize("contact", [False, True])
-def test_fest_costs_match_oracle(seed, contact):
+def test_fest_costs_match_oracle(seed, contact, variant):
     base = synth.cost_contact() if contact else synth.cost_free_space()
     c = make_case(seed, cost=synth.cost_force_estimate(base=base))
-    g, o = _run_fest(c, _hold_plan(c))
+    g, o = _run_fest(c, _hold_plan(c), variant=variant)
     assert np.isfinite(o["S"]).all()
     _assert_costs(g["S"], o["S"])
 
 
+@pytest.mark.parametrize("variant", [2, 3])
 @pytest.mark.parametrize("seed", range(4))
-def test_fest_plan_matches_oracle(seed):
+def test_fest_plan_matches_oracle(seed, variant):
     # light force weight: S / lambda of a few tens, as for the plain parity workload
     c = make_case(seed, cost=synth.cost_force_estimate(1e-4, base=parity_cost()))
-    g, o = _run_fest(c, _hold_plan(c))
+    g, o = _run_fest(c, _hold_plan(c), variant=variant)
     _assert_costs(g["S"], o["S"])
     assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL
     assert np.abs(g["plan"] - o["plan_next"]).max() <= PLAN_TOL
@@ -148,10 +152,11 @@ def test_fest_plan_matches_oracle(seed):
 HEAVY_MISS_BOUND = 1e-4
 
 
+@pytest.mark.parametrize("variant", [2, 3])
 @pytest.mark.parametrize("seed", range(4))
-def test_fest_plan_recorded_miss_at_heavy_weights(seed):
+def test_fest_plan_recorded_miss_at_heavy_weights(seed, variant):
     c = make_case(seed, cost=synth.cost_force_estimate(1e-3))
-    g, o = _run_fest(c, _hold_plan(c))
+    g, o = _run_fest(c, _hold_plan(c), variant=variant)
     _assert_costs(g["S"], o["S"])
     assert np.argmin(g["S"]) == np.argmin(o["S"])
     err = max(np.abs(g["ustar"] - o["ustar"]).max(), np.abs(g["plan"] - o["plan_next"]).max())
@@ -159,11 +164,12 @@ def test_fest_plan_recorded_miss_at_heavy_weights(seed):
     assert err <= HEAVY_MISS_BOUND
 
 
-def test_fest_full_size_sampled():
+@pytest.mark.parametrize("variant", [2, 3])
+def test_fest_full_size_sampled(variant):
     # K = 16384, T = 18 in the benchmark's launch shape: sampled samples one by one
     c = make_case(7, cost=synth.cost_force_estimate(), K=16384)
     plan = _hold_plan(c)
-    with gpu_controller(c) as g:
+    with gpu_controller(c, variant=variant) as g:
         g.set_plan(plan.astype(np.float32))
         g.step(c["q"], c["qd"], c["goal"], c["plane"])
         S = g.costs()
@@ -172,3 +178,26 @@ def test_fest_full_size_sampled():
         So = oracle.rollout(c["rb"], c["oc"], c["dt"], c["T"], c["sigma"], c["seed"], 0, int(k),
                             c["q"], c["qd"], c["goal"], c["plane"], plan)
         assert abs(S[k] - So) <= S_RTOL * abs(So) + S_ATOL, k
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+def test_fest_full_size_matches_oracle(variant):
+    """K = 16384, T = 18 with plane contact and the wrench-estimate cost (the
+    `--cost force_estimate` bench workload's sizes): all 16384 costs element
+    by element against the oracle's whole update, the best sample, and the
+    plan within the heavy-weight bound (S_min ~ 100 lambda here)."""
+    import os
+    c = make_case(7, cost=synth.cost_force_estimate(base=synth.cost_contact()), K=16384)
+    plan = _hold_plan(c)
+    o = oracle_step(c, plan=plan, want_noise=False, nthreads=os.cpu_count() or 8)
+    with gpu_controller(c, variant=variant) as g:
+        g.set_plan(plan.astype(np.float32))
+        tau0, nxt = g.step(c["q"], c["qd"], c["goal"], c["plane"])
+        S, us = g.costs(), g.updated_plan()
+    assert np.isfinite(o["S"]).all()
+    _assert_costs(S, o["S"])
+    assert np.argmin(S) == np.argmin(o["S"])
+    err = max(np.abs(us - o["ustar"]).max(), np.abs(nxt - o["plan_next"]).max())
+    print(f"force estimate full size, variant {variant}: max |du*| {err:.2e} N m, "
+          f"n_eff {o['stats'][2]:.1f}")
+    assert err <= HEAVY_MISS_BOUND

@@ -682,16 +682,23 @@ def test_receding_horizon_contact_loop():
 
 def test_default_kernel_choice():
     # variant 0: warp-specialised while its blocks fit on the device at once,
-    # register kernel beyond, rolled kernel for the optional cost terms
+    # register kernel beyond; with one optional cost term the warp-specialised
+    # kernel while it fits, else the rolled kernel; both terms: rolled
     for K, want in [(256, 3), (16384, 3), (65536, 1)]:
         with gpu_controller(make_case(0, K=K)) as g:
             assert g.variant() == want, K
-    with gpu_controller(make_case(0, cost=synth.cost_force_estimate())) as g:
-        assert g.variant() == 2
+    for K, want in [(256, 3), (16384, 3), (65536, 2)]:
+        with gpu_controller(make_case(0, cost=synth.cost_force_estimate(), K=K)) as g:
+            assert g.variant() == want, K
     with gpu_controller(make_case(0, cost=synth.cost_collision(2))) as g:
         assert g.variant() == 3
     with gpu_controller(make_case(0, cost=synth.cost_collision(2), K=65536)) as g:
         assert g.variant() == 2
+    both = synth.cost_force_estimate(base=synth.cost_collision(2))
+    with gpu_controller(make_case(0, cost=both)) as g:
+        assert g.variant() == 2
+    with pytest.raises(mppi.MPPIError):
+        gpu_controller(make_case(0, cost=both), variant=3)
     for v in (1, 2, 3):
         with gpu_controller(make_case(0), variant=v) as g:
             assert g.variant() == v
