@@ -22,6 +22,8 @@
 namespace mppi_dev {
 
 constexpr int NJ = 7;
+// link pairs (i, j >= i + 2) of the collision cost, by i then j
+constexpr int NJ_SELF_PAIRS = (NJ - 1) * (NJ - 2) / 2;
 
 // Link constants in the kernel's link frames (z = joint axis); the host
 // rotates the caller's description into these frames once, at create time.
@@ -55,6 +57,8 @@ struct CostK {
   float wcoll, dth_self, dth_obs;
   float lrad[NJ];                      // link capsule radii
   float seg_a[NJ], seg_ia[NJ];         // squared link segment lengths and reciprocals
+  float seg_h[NJ];                     // half link segment lengths
+  float self_b2[NJ_SELF_PAIRS];        // culling bounds of the self pairs (pair_skip_b2)
 };
 
 // Obstacle capsules read by the rollouts at every launch (device memory, so
@@ -573,7 +577,6 @@ __device__ __forceinline__ float motion_cost(const CostK& c, const float pdes[3]
   return cst;
 }
 
-// Plane contact normal force at the end-effector (0 without contact).
 // Squared distance between the segments p1 + s d1 and p2 + t d2, s, t in
 // [0, 1], for Eq. 15 by Lumelsky's method (Inf. Process. Lett. 21, 1985):
 // the closest point of the infinite lines, s clamped to [0, 1]; t follows
@@ -611,6 +614,24 @@ __device__ __forceinline__ float segment_dist2(const float p1[3], const float d1
   return dot3(g, g);
 }
 
+// Culling of a collision pair, exact: the distance of two segments is at
+// least |m_1 - m_2| - h_1 - h_2 (midpoints m, half lengths h), and the pair's
+// term of Eq. 15 is zero unless the distance is below D = th + r_1 + r_2.
+// A pair may therefore be skipped when |m_1 - m_2|^2 >= b2 =
+// ((D + h_1 + h_2)(1 + 1e-4) + 1e-5)^2 (lengths in m): the margins exceed
+// the FP32 rounding of both distances (segment_dist2 evaluates the distance
+// of two points on the segments, never below the segments' distance by more
+// than a few 1e-7 m), so a skipped pair is one whose term the full
+// evaluation also finds zero.  With D <= 0 no term is ever charged (b2 = -1:
+// always skipped).
+__host__ __device__ inline float pair_skip_b2(float th, float r1, float r2, float h1, float h2) {
+  const float D = th + r1 + r2;
+  if (!(D > 0.f)) return -1.f;
+  const float b = (D + h1 + h2) * 1.0001f + 1e-5f;
+  return b * b;
+}
+
+// Plane contact normal force at the end-effector (0 without contact).
 __device__ __forceinline__ float contact_force(const CostK& c, const float plane[4],
                                                const EEState& ee) {
   const float delta = plane[3] - dot3(plane, ee.p);

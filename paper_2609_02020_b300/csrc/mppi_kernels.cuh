@@ -448,7 +448,12 @@ __device__ __forceinline__ void backward_sweep_rolled(const RobotK& rb, const fl
 constexpr int FEAT_FEST = 1;  // C_force on the wrench estimate (Eq. 13)
 constexpr int FEAT_COLL = 2;  // C_collision (Eq. 15)
 constexpr int COLL_FLOATS_PER_THREAD = 3 * (NJ + 1);  // link capsule end points
-constexpr int OBS_SMEM_FLOATS = OBS_MAX * 9 + 8;      // block copy: obstacles, link radii
+// Block copy of the obstacles: per obstacle a xyz, b - a xyz, |b - a|^2, its
+// reciprocal (0 for a sphere), the radius, the midpoint xyz and the half
+// length; then the NJ link radii (padded to 8); then per obstacle the NJ
+// link-obstacle culling bounds (pair_skip_b2).
+constexpr int OBS_FIELDS = 13;
+constexpr int OBS_SMEM_FLOATS = OBS_MAX * OBS_FIELDS + 8 + OBS_MAX * NJ;
 
 __host__ __device__ constexpr int rolled_floats_per_thread(int feat) {
   return ROLLED_FLOATS_PER_THREAD + ((feat & FEAT_FEST) ? FEST_FLOATS_PER_THREAD : 0) +
@@ -461,9 +466,38 @@ __device__ __forceinline__ void load_point(const float* sP, int i, int tid, floa
   for (int a = 0; a < 3; ++a) x[a] = sP[(3 * i + a) * B + tid];
 }
 
-// Block copy of the obstacles: per obstacle a xyz, b - a xyz, |b - a|^2, its
-// reciprocal (0 for a sphere) and the radius; then the NJ link radii.
-constexpr int OBS_FIELDS = 9;
+// Fills the block copy of the obstacles (threads 0 .. n_obs - 1 one
+// obstacle each, threads 0 .. NJ - 1 the link radii); returns n_obs.  The
+// caller synchronises the block before use.
+__device__ __forceinline__ int load_obstacles(const ObsK* obs, const CostK& C, float* s_obs) {
+  const int n_obs = min(max(obs->n, 0), OBS_MAX);
+  if (threadIdx.x < n_obs) {
+    const float* o = obs->o[threadIdx.x];
+    float* so = s_obs + OBS_FIELDS * threadIdx.x;
+    float e = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      so[a] = o[a];
+      so[3 + a] = o[3 + a] - o[a];
+      e = fmaf(so[3 + a], so[3 + a], e);
+      so[9 + a] = 0.5f * (o[a] + o[3 + a]);
+    }
+    so[6] = e;
+    so[7] = e > 1e-12f ? 1.f / e : 0.f;
+    so[8] = o[6];
+    so[12] = 0.5f * sqrtf(e);
+    float* b2 = s_obs + OBS_FIELDS * OBS_MAX + 8 + NJ * threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < NJ; ++i) b2[i] = pair_skip_b2(C.dth_obs, C.lrad[i], o[6], C.seg_h[i], so[12]);
+  }
+  if (threadIdx.x < NJ) s_obs[OBS_FIELDS * OBS_MAX + threadIdx.x] = C.lrad[threadIdx.x];
+  return n_obs;
+}
+
+__device__ __forceinline__ float dist2_3(const float a[3], const float b[3]) {
+  const float d0 = a[0] - b[0], d1 = a[1] - b[1], d2 = a[2] - b[2];
+  return fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+}
 
 // One pair's term of Eq. 15 from the squared segment distance g2: the
 // indicator [d < th] compares g2 with (th + r1 + r2)^2 (d = sqrt(g2) - r1 -
@@ -487,43 +521,58 @@ template <int B>
 __device__ __forceinline__ float collision_cost(const CostK& C, const float* sP, int tid,
                                                 const float* s_obs, int n_obs) {
   const float* lrad = s_obs + OBS_FIELDS * OBS_MAX;
+  const float* ob2 = lrad + 8;
   float acc = 0.f;
 #pragma unroll 1
   for (int i = 0; i < NJ - 2; ++i) {
-    float pi[3], di[3];
+    float pi[3], di[3], mi[3];
     load_point<B>(sP, i, tid, pi);
     load_point<B>(sP, i + 1, tid, di);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) di[a] -= pi[a];
+    for (int a = 0; a < 3; ++a) {
+      mi[a] = 0.5f * (pi[a] + di[a]);
+      di[a] -= pi[a];
+    }
     const float ai = C.seg_a[i], iai = C.seg_ia[i], ri = lrad[i];
+    const int n0 = i * (NJ - 2) - i * (i - 1) / 2;  // index of pair (i, i + 2)
 #pragma unroll
     for (int jj = 0; jj < NJ - 2; ++jj) {
       const int j = i + 2 + jj;
       if (j < NJ) {
-        float pj[3], dj[3];
+        float pj[3], dj[3], mj[3];
         load_point<B>(sP, j, tid, pj);
         load_point<B>(sP, j + 1, tid, dj);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) dj[a] -= pj[a];
-        const float g2 = segment_dist2(pi, di, ai, iai, pj, dj, C.seg_a[j], C.seg_ia[j]);
-        acc += collision_term(C.coll, g2, ri + lrad[j], C.dth_self);
+        for (int a = 0; a < 3; ++a) {
+          mj[a] = 0.5f * (pj[a] + dj[a]);
+          dj[a] -= pj[a];
+        }
+        if (dist2_3(mi, mj) < C.self_b2[n0 + jj]) {
+          const float g2 = segment_dist2(pi, di, ai, iai, pj, dj, C.seg_a[j], C.seg_ia[j]);
+          acc += collision_term(C.coll, g2, ri + lrad[j], C.dth_self);
+        }
       }
     }
   }
 #pragma unroll 1
   for (int i = 0; i < NJ; ++i) {
-    float pi[3], di[3];
+    float pi[3], di[3], mi[3];
     load_point<B>(sP, i, tid, pi);
     load_point<B>(sP, i + 1, tid, di);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) di[a] -= pi[a];
+    for (int a = 0; a < 3; ++a) {
+      mi[a] = 0.5f * (pi[a] + di[a]);
+      di[a] -= pi[a];
+    }
     const float ai = C.seg_a[i], iai = C.seg_ia[i], ri = lrad[i];
 #pragma unroll
     for (int o = 0; o < OBS_MAX; ++o) {
       if (o < n_obs) {
         const float* ob = s_obs + OBS_FIELDS * o;
-        const float g2 = segment_dist2(pi, di, ai, iai, ob, ob + 3, ob[6], ob[7]);
-        acc += collision_term(C.coll, g2, ri + ob[8], C.dth_obs);
+        if (dist2_3(mi, ob + 9) < ob2[NJ * o + i]) {
+          const float g2 = segment_dist2(pi, di, ai, iai, ob, ob + 3, ob[6], ob[7]);
+          acc += collision_term(C.coll, g2, ri + ob[8], C.dth_obs);
+        }
       }
     }
   }
@@ -678,25 +727,7 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
   if (k_split < K)
     for (int i = threadIdx.x; i < T * NJ; i += B) s_prop[i] = prop[i];
   if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
-  int n_obs = 0;
-  if (COLL) {
-    n_obs = min(max(obs->n, 0), OBS_MAX);
-    if (threadIdx.x < n_obs) {
-      const float* o = obs->o[threadIdx.x];
-      float* so = s_obs + OBS_FIELDS * threadIdx.x;
-      float e = 0.f;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        so[a] = o[a];
-        so[3 + a] = o[3 + a] - o[a];
-        e = fmaf(so[3 + a], so[3 + a], e);
-      }
-      so[6] = e;
-      so[7] = e > 1e-12f ? 1.f / e : 0.f;
-      so[8] = o[6];
-    }
-    if (threadIdx.x < NJ) s_obs[OBS_FIELDS * OBS_MAX + threadIdx.x] = P.cost.lrad[threadIdx.x];
-  }
+  const int n_obs = COLL ? load_obstacles(obs, P.cost, s_obs) : 0;
   __syncthreads();
   const int k = blockIdx.x * B + threadIdx.x;
   float sk = 0.f;
@@ -1218,20 +1249,27 @@ template <int PART>
 __device__ __forceinline__ float ws_collision_pairs(const CostK& C, const float pts[NJ + 1][3],
                                                     const float* s_obs, int n_obs) {
   const float* lrad = s_obs + OBS_FIELDS * OBS_MAX;
+  const float* ob2 = lrad + 8;
   float acc = 0.f;
-  float d[NJ][3];
+  float d[NJ][3], mid[NJ][3];
 #pragma unroll
   for (int i = 0; i < NJ; ++i)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) d[i][a] = pts[i + 1][a] - pts[i][a];
+    for (int a = 0; a < 3; ++a) {
+      d[i][a] = pts[i + 1][a] - pts[i][a];
+      mid[i][a] = 0.5f * (pts[i][a] + pts[i + 1][a]);
+    }
   if (PART == 0) {
+    int n = 0;
 #pragma unroll
     for (int i = 0; i < NJ - 2; ++i)
 #pragma unroll
-      for (int j = i + 2; j < NJ; ++j) {
-        const float g2 = segment_dist2(pts[i], d[i], C.seg_a[i], C.seg_ia[i], pts[j], d[j],
-                                       C.seg_a[j], C.seg_ia[j]);
-        acc += collision_term(C.coll, g2, lrad[i] + lrad[j], C.dth_self);
+      for (int j = i + 2; j < NJ; ++j, ++n) {
+        if (dist2_3(mid[i], mid[j]) < C.self_b2[n]) {
+          const float g2 = segment_dist2(pts[i], d[i], C.seg_a[i], C.seg_ia[i], pts[j], d[j],
+                                         C.seg_a[j], C.seg_ia[j]);
+          acc += collision_term(C.coll, g2, lrad[i] + lrad[j], C.dth_self);
+        }
       }
   }
   constexpr int i0 = PART == 0 ? 0 : 2, i1 = PART == 0 ? 2 : NJ;
@@ -1240,9 +1278,11 @@ __device__ __forceinline__ float ws_collision_pairs(const CostK& C, const float 
 #pragma unroll 1
     for (int o = 0; o < n_obs; ++o) {
       const float* ob = s_obs + OBS_FIELDS * o;
-      const float g2 = segment_dist2(pts[i], d[i], C.seg_a[i], C.seg_ia[i], ob, ob + 3, ob[6],
-                                     ob[7]);
-      acc += collision_term(C.coll, g2, lrad[i] + ob[8], C.dth_obs);
+      if (dist2_3(mid[i], ob + 9) < ob2[NJ * o + i]) {
+        const float g2 = segment_dist2(pts[i], d[i], C.seg_a[i], C.seg_ia[i], ob, ob + 3, ob[6],
+                                       ob[7]);
+        acc += collision_term(C.coll, g2, lrad[i] + ob[8], C.dth_obs);
+      }
     }
   }
   return acc;
@@ -1411,25 +1451,7 @@ __device__ __forceinline__ void rollout_ws_block(const ProbK& P, const float* __
   float* s_in = dsm;
   float* s_obs = s_in + 32;  // COLL: obstacles (start, direction, |d|^2, 1/|d|^2, radius), radii
   if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
-  int n_obs = 0;
-  if (COLL) {
-    n_obs = min(max(obs->n, 0), OBS_MAX);
-    if (threadIdx.x < n_obs) {
-      const float* o = obs->o[threadIdx.x];
-      float* so = s_obs + OBS_FIELDS * threadIdx.x;
-      float e = 0.f;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        so[a] = o[a];
-        so[3 + a] = o[3 + a] - o[a];
-        e = fmaf(so[3 + a], so[3 + a], e);
-      }
-      so[6] = e;
-      so[7] = e > 1e-12f ? 1.f / e : 0.f;
-      so[8] = o[6];
-    }
-    if (threadIdx.x < NJ) s_obs[OBS_FIELDS * OBS_MAX + threadIdx.x] = P.cost.lrad[threadIdx.x];
-  }
+  const int n_obs = COLL ? load_obstacles(obs, P.cost, s_obs) : 0;
   __syncthreads();
   const WsSmem m = ws_carve(s_in + 32 + (COLL ? OBS_SMEM_FLOATS : 0));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

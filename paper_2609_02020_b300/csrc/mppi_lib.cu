@@ -318,7 +318,11 @@ int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, Pr
     const double a = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     k.seg_a[j] = static_cast<float>(a);
     k.seg_ia[j] = a > 1e-12 ? static_cast<float>(1.0 / a) : 0.f;
+    k.seg_h[j] = static_cast<float>(0.5 * std::sqrt(a));
   }
+  for (int i = 0, n = 0; i < 7 - 2; ++i)
+    for (int j = i + 2; j < 7; ++j, ++n)
+      k.self_b2[n] = pair_skip_b2(k.dth_self, k.lrad[i], k.lrad[j], k.seg_h[i], k.seg_h[j]);
   k.fest = c->force_estimate ? 1 : 0;
   for (int a = 0; a < 6; ++a) {
     k.wf6[a] = static_cast<float>(c->w_force6[a]);
