@@ -151,7 +151,10 @@ def test_plan_recorded_miss_at_heavy_weights(case, variant):
     g, o = run_pair(c, variant=variant)
     assert_costs(g["S"], o["S"])
     assert np.argmin(g["S"]) == np.argmin(o["S"])
-    assert max(plan_errors(g, o)) <= HEAVY_MISS_BOUND[kind]
+    err = max(plan_errors(g, o))
+    print(f"recorded miss {case} variant {variant}: max |du*| {err:.2e} N m, "
+          f"n_eff {o['stats'][2]:.2f}")
+    assert err <= HEAVY_MISS_BOUND[kind]
 
 
 @pytest.mark.parametrize("fp64", [False, True])
