@@ -55,7 +55,8 @@ L2_FLUSH_BYTES = 256 << 20  # twice the 126 MB L2
 #   compensated Euler step (Eq. 7), 7 joints x 12                         84
 #   this block's share of Eq. 4 (N_b sums: 126 x 2 / 18)                  14
 #                                                                 total 4311
-# The term-by-term derivation is in the design notes.  The executed count of
+# Each term counts the operations of the helpers in csrc/mppi_device.cuh that
+# carry it, structural zeros left out.  The executed count of
 # the warp-specialised kernel (ncu FADD + FMUL + 2 FFMA, special functions'
 # polynomials included) is kept beside it.  The optional cost terms have no
 # hand count; their lines use the executed count and say so.
