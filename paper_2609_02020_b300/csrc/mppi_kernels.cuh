@@ -1242,9 +1242,11 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
 // Warps 3 and 4 (collision cost, Eq. 15): the link points of x_s are copied
 // from the hand-off records (and the end-effector point from warp 2's slot)
 // between the forces and the step barriers, then the pairs of this warp's
-// part are charged off the critical path: part 0 the link-link pairs and
-// links 0-1 against the obstacles, part 1 links 2-6 against the obstacles.
-// Link i spans pts[i] .. pts[i + 1]; same terms as collision_cost.
+// part are charged: part 0 the 15 link-link pairs and link 0 against the
+// obstacles, part 1 links 1-6 against the obstacles (18 pairs each with three
+// obstacles; both warps must be done before the next state's forces barrier,
+// so the longer part bounds the step).  Link i spans pts[i] .. pts[i + 1];
+// same terms as collision_cost.
 template <int PART>
 __device__ __forceinline__ float ws_collision_pairs(const CostK& C, const float pts[NJ + 1][3],
                                                     const float* s_obs, int n_obs) {
@@ -1272,7 +1274,7 @@ __device__ __forceinline__ float ws_collision_pairs(const CostK& C, const float 
         }
       }
   }
-  constexpr int i0 = PART == 0 ? 0 : 2, i1 = PART == 0 ? 2 : NJ;
+  constexpr int i0 = PART == 0 ? 0 : 1, i1 = PART == 0 ? 1 : NJ;
 #pragma unroll
   for (int i = i0; i < i1; ++i) {
 #pragma unroll 1
