@@ -90,6 +90,8 @@ class Cost(C.Structure):
         ("link_radius", C.c_double * NMAX),
         ("n_obs", C.c_int),
         ("obs", C.c_double * 7 * 8),
+        ("ext_wrench", C.c_int),
+        ("f_ext", C.c_double * 6),
     ]
 
 
@@ -268,6 +270,10 @@ def make_cost(d: dict) -> Cost:
     for o in range(obs.shape[0]):
         for a in range(7):
             c.obs[o][a] = obs[o, a]
+    c.ext_wrench = int(d.get("ext_wrench", 0))
+    fe = np.asarray(d.get("f_ext", np.zeros(6)), dtype=np.float64)
+    for a in range(6):
+        c.f_ext[a] = fe[a]
     return c
 
 
@@ -330,6 +336,14 @@ def jacobian(robot: Robot, q):
     J = np.zeros((6, n))
     lib().orc_jacobian(C.byref(robot), _p(_arr(q, n)), _p(J))
     return J
+
+
+def ext_torque(robot: Robot, cost: Cost, q0):
+    """tau_ext = J(q0)^T F_ext of the cost's constant external wrench (zeros
+    when it is off)."""
+    t = np.zeros(robot.n)
+    lib().orc_ext_torque(C.byref(robot), C.byref(cost), _p(_arr(q0, robot.n)), _p(t))
+    return t
 
 
 def rnea(robot: Robot, q, qd, qdd):

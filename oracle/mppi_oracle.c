@@ -89,6 +89,14 @@ typedef struct {
   double link_radius[NMAX];
   int n_obs;
   double obs[8][7];
+  /* Eq. 5-6 as the paper states them: tau_ext = J(q)^T F_ext with F_ext the
+   * external wrench (force xyz; moment about the end-effector point xyz,
+   * world frame), "assumed to be constant over the prediction horizon": it
+   * is projected once, at the update's initial state q_0, and the same
+   * tau_ext enters every step of every rollout (in addition to the plane
+   * contact's, when that is on). */
+  int ext_wrench;
+  double f_ext[6];
 } orc_cost;
 
 /* ------------------------------------------------------------------------ */
@@ -625,6 +633,23 @@ double orc_contact(const orc_robot* rb, const orc_cost* c, const double plane[4]
   return f;
 }
 
+/* The paper's constant external torque (Eq. 5): tau_ext = J(q0)^T F_ext,
+ * with J the geometric Jacobian of the end-effector point (rows: linear
+ * velocity, angular velocity), so tau_j = J_v,j . force + J_w,j . moment.
+ * Zero when ext_wrench is off. */
+void orc_ext_torque(const orc_robot* rb, const orc_cost* c, const double* q0, double* tau_ext) {
+  int n = rb->n;
+  for (int j = 0; j < n; j++) tau_ext[j] = 0.0;
+  if (!c->ext_wrench) return;
+  double J[6 * NMAX];
+  orc_jacobian(rb, q0, J);
+  for (int j = 0; j < n; j++) {
+    double s = 0.0;
+    for (int a = 0; a < 6; a++) s += J[a * n + j] * c->f_ext[a];
+    tau_ext[j] = s;
+  }
+}
+
 /* Rotation vector of R (matrix logarithm of Eq. 11), theta in [0, pi]. */
 void orc_so3_log(const double R[3][3], double r[3]) {
   double vx = R[2][1] - R[1][2], vy = R[0][2] - R[2][0], vz = R[1][0] - R[0][1];
@@ -876,6 +901,8 @@ double orc_rollout(const orc_robot* rb, const orc_cost* c, double dt, int T, con
   memcpy(q, q0, sizeof(double) * n);
   memcpy(qd, qd0, sizeof(double) * n);
   double S = 0.0;
+  double tex0[NMAX];
+  orc_ext_torque(rb, c, q0, tex0);
   for (int t = 0; t < T; t++) {
     double z[8];
     orc_normals(seed, iter, k, (uint32_t)t, z);
@@ -887,7 +914,7 @@ double orc_rollout(const orc_robot* rb, const orc_cost* c, double dt, int T, con
     if (c->force_estimate) S += orc_force_estimate_cost(rb, c, q, v);
     for (int j = 0; j < n; j++) tex[j] = 0.0;
     if (c->contact) orc_contact(rb, c, plane, q, qd, tex);
-    for (int j = 0; j < n; j++) tau[j] = v[j] + tex[j];
+    for (int j = 0; j < n; j++) tau[j] = v[j] + tex[j] + tex0[j];
     if (orc_forward_dynamics(rb, q, qd, tau, method, qdd) != 0) return NAN;
     for (int j = 0; j < n; j++) {
       qd[j] += qdd[j] * dt;
