@@ -128,7 +128,16 @@ typedef struct mppi_robot {
  * blocks for K samples fit on the device at once, else in the rolled kernel
  * (variant 0 chooses; 2 and 3 force one; 1 is rejected).  Both together run
  * in the rolled kernel (variant 0 or 2; 1 and 3 are rejected).
- * mppi_step_static and the server take neither cost. */
+ * mppi_step_static and the server take neither cost.
+ * Constant external wrench (ext_wrench != 0; Eq. 5-6 as the paper states
+ * them): tau_ext = J(q_0)^T F_ext, with F_ext (force xyz [N]; moment about
+ * the end-effector point xyz [N m], world frame) the external wrench and J
+ * the end-effector Jacobian at the update's initial state q_0, is "constant
+ * over the prediction horizon": the same tau_ext enters M qdd + h = v +
+ * tau_ext at every step of every rollout, beside the plane contact's torque
+ * when contact is on.  F_ext starts at f_ext below and is replaced between
+ * updates by mppi_set_external_wrench[_device] (also under CUDA graphs).
+ * mppi_step_static and the server do not take it. */
 typedef struct mppi_cost {
   double w_pos[3], w_ori[3];
   double w_force, f_des, w_reg;
@@ -145,6 +154,8 @@ typedef struct mppi_cost {
   double link_radius[7];       /* link capsule radii [m], >= 0                 */
   int n_obstacles;             /* initial obstacles, 0..MPPI_OBS_MAX           */
   double obstacles[8][7];      /* capsules: a xyz, b xyz, radius [m]           */
+  int ext_wrench;              /* 1: constant tau_ext = J(q_0)^T F_ext         */
+  double f_ext[6];             /* initial F_ext: force xyz; moment xyz         */
 } mppi_cost;
 
 #define MPPI_OBS_MAX 8
@@ -277,6 +288,18 @@ MPPI_API int mppi_set_obstacles(mppi_t h, int n, const float* obs);
  * obstacles make every cost non-finite and the update keeps its plan);
  * queued on the handle's stream. */
 MPPI_API int mppi_set_obstacles_device(mppi_t h, int n, const float* d_obs);
+
+/* Replaces the external wrench F_ext of a handle created with ext_wrench
+ * (force xyz; moment about the end-effector point xyz, world frame; see
+ * mppi_cost): F, a host array of 6 finite floats, is copied in the handle's
+ * stream order and the next update projects it at its own initial state.
+ * MPPI_ERR_INVALID_ARG when the handle has no external wrench or F is not
+ * finite. */
+MPPI_API int mppi_set_external_wrench(mppi_t h, const float F[6]);
+/* The same from a device array d_F of 6 floats (not validated: a
+ * non-finite wrench makes every cost non-finite and the update keeps its
+ * plan); queued on the handle's stream. */
+MPPI_API int mppi_set_external_wrench_device(mppi_t h, const float* d_F);
 
 /* End-effector wrench estimates of Eq. 13, F = Jbar^T (v - g(q)), for n
  * pairs (q_i, v_i) of device arrays d_q, d_v [n][7] into d_F [n][6]

@@ -77,10 +77,15 @@ struct ProbK {
   float sigma[NJ];
   int T, K;
   uint32_t key0, key1;
+  const float* fext;  // device F_ext (6) of the constant external wrench, or null
 };
 
 // Per-step inputs in device memory: q, qd, goal (p, quat wxyz), plane (n, d).
 constexpr int IN_FLOATS = 25;
+// The kernels' shared-memory copy of the inputs: the IN_FLOATS inputs, then
+// (with the constant external wrench) tau_ext = J(q_0)^T F_ext.
+constexpr int IN_STAGED = 32;
+constexpr int IN_TEXT = IN_FLOATS;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller normals
@@ -629,6 +634,29 @@ __host__ __device__ inline float pair_skip_b2(float th, float r1, float r2, floa
   if (!(D > 0.f)) return -1.f;
   const float b = (D + h1 + h2) * 1.0001f + 1e-5f;
   return b * b;
+}
+
+// tau_ext = J(q0)^T F_ext for the external wrench F = (force f; moment m
+// about the end-effector point), world frame (Eq. 5, constant over the
+// horizon): with the joint axes S_j = (z_j, w_j = p_j x z_j) and the
+// wrench's moment about the origin n_O = m + p_ee x f, tau_j = z_j . n_O +
+// w_j . f.  One thread forms it for its block; not on the per-step path.
+static __device__ __noinline__ void ext_torque(const RobotK& rb, const float* q0, const float* F,
+                                               float* tau) {
+  ChainState c;
+  chain_init(rb, c);
+  float z[NJ][3], w[NJ][3];
+#pragma unroll 1
+  for (int i = 0; i < NJ; ++i) forward_link_frame(rb.L[i], q0[i], c, z[i], w[i]);
+  float de[3], p[3];
+  mv3(c.R, rb.ee, de);
+  p[0] = c.p[0] + de[0]; p[1] = c.p[1] + de[1]; p[2] = c.p[2] + de[2];
+  const float f[3] = {F[0], F[1], F[2]};
+  float nO[3];
+  cross3(p, f, nO);
+  nO[0] += F[3]; nO[1] += F[4]; nO[2] += F[5];
+#pragma unroll 1
+  for (int j = 0; j < NJ; ++j) tau[j] = dot3(z[j], nO) + dot3(w[j], f);
 }
 
 // Plane contact normal force at the end-effector (0 without contact).

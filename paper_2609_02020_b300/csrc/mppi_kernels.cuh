@@ -117,6 +117,14 @@ constexpr int OUT_STATUS = 7;   // written as an int: 0 ok, 1 no finite cost
 constexpr int OUT_STATS = 8;    // S_min, Z, n_eff, n_nonfinite
 constexpr int OUT_PLAN = 16;    // shifted plan [T][7]
 
+// Copies the inputs into the block's staged record (IN_STAGED floats) and,
+// with the constant external wrench, forms tau_ext = J(q_0)^T F_ext after
+// them (thread 0); the caller synchronises the block before use.
+__device__ __forceinline__ void stage_inputs(const ProbK& P, const float* in, float* s_in) {
+  if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
+  if (P.fext && threadIdx.x == 0) ext_torque(P.rb, in, P.fext, s_in + IN_TEXT);
+}
+
 // One rollout (sample k of T steps) of the problem P: Eq. 1-3 with Eq. 5-7
 // and the running cost of Eq. 9-14.  in: IN_FLOATS inputs and plan: [T][7]
 // nominal torques (both usually staged in shared memory); returns S_k and,
@@ -173,6 +181,10 @@ __device__ __forceinline__ float rollout_sample(const ProbK& P, const float* in,
 #pragma unroll
       for (int j = 0; j < NJ; ++j) rhs[j] = v[j] - h[j];
     }
+    if (P.fext) {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) rhs[j] += in[IN_TEXT + j];
+    }
     float qdd[NJ];
     ldlt_solve(M, rhs, qdd);
     // Eq. 7: semi-implicit Euler (compensated)
@@ -217,13 +229,13 @@ rollout_kernel(const __grid_constant__ ProbK P, const float* __restrict__ in,
                float* __restrict__ part = nullptr) {
   __shared__ float s_plan[T_MAX * NJ];
   __shared__ float s_prop[T_MAX * NJ];
-  __shared__ float s_in[IN_FLOATS];
+  __shared__ float s_in[IN_STAGED];
   const int T = P.T, K = P.K;
   const int k_split = ksplit_p ? *ksplit_p : K;
   for (int i = threadIdx.x; i < T * NJ; i += blockDim.x) s_plan[i] = plan[i];
   if (k_split < K)
     for (int i = threadIdx.x; i < T * NJ; i += blockDim.x) s_prop[i] = prop[i];
-  if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
+  stage_inputs(P, in, s_in);
   __syncthreads();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   float sk = 0.f;
@@ -652,6 +664,10 @@ __device__ __forceinline__ float rollout_sample_rolled(const ProbK& P, const flo
 #pragma unroll
       for (int j = 0; j < NJ; ++j) rhs[j] = v[j] - sh[j * B + tid];
     }
+    if (P.fext) {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) rhs[j] += in[IN_TEXT + j];
+    }
     float qdd[NJ];
     float cfest = 0.f;
     if (FEST) {
@@ -721,12 +737,12 @@ rollout_kernel_rolled(const __grid_constant__ ProbK P, const float* __restrict__
   float* s_plan = dsm;
   float* s_prop = dsm + pstride;
   float* s_in = s_prop + pstride;
-  float* s_obs = s_in + 32;
+  float* s_obs = s_in + IN_STAGED;
   float* s_work = s_obs + (COLL ? OBS_SMEM_FLOATS : 0);
   for (int i = threadIdx.x; i < T * NJ; i += B) s_plan[i] = plan[i];
   if (k_split < K)
     for (int i = threadIdx.x; i < T * NJ; i += B) s_prop[i] = prop[i];
-  if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
+  stage_inputs(P, in, s_in);
   const int n_obs = COLL ? load_obstacles(obs, P.cost, s_obs) : 0;
   __syncthreads();
   const int k = blockIdx.x * B + threadIdx.x;
@@ -1073,6 +1089,10 @@ __device__ __forceinline__ void ws_dynamics(const ProbK& P, const float* in, con
     } else {
 #pragma unroll
       for (int j = 0; j < NJ; ++j) rhs[j] = v[j * B] - m.sh[j * B + tid];
+    }
+    if (P.fext) {
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) rhs[j] += in[IN_TEXT + j];
     }
     float y[NJ], qdd[NJ];
     unit_lower_solve<NJ>(M, rhs, y);
@@ -1451,11 +1471,11 @@ __device__ __forceinline__ void rollout_ws_block(const ProbK& P, const float* __
   const int K = P.K;
   const int k_split = ksplit_p ? *ksplit_p : K;
   float* s_in = dsm;
-  float* s_obs = s_in + 32;  // COLL: obstacles (start, direction, |d|^2, 1/|d|^2, radius), radii
-  if (threadIdx.x < IN_FLOATS) s_in[threadIdx.x] = in[threadIdx.x];
+  float* s_obs = s_in + IN_STAGED;  // COLL: the block copy of the obstacles (load_obstacles)
+  stage_inputs(P, in, s_in);
   const int n_obs = COLL ? load_obstacles(obs, P.cost, s_obs) : 0;
   __syncthreads();
-  const WsSmem m = ws_carve(s_in + 32 + (COLL ? OBS_SMEM_FLOATS : 0));
+  const WsSmem m = ws_carve(s_in + IN_STAGED + (COLL ? OBS_SMEM_FLOATS : 0));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // lanes past K run sample K - 1 so that every warp meets every barrier;
   // they write nothing

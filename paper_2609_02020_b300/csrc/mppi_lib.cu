@@ -76,6 +76,7 @@ struct mppi_s {
   float* d_prop = nullptr;                // second proposal plan [T][7]
   int* d_ctl = nullptr;                   // {k_split of the next update, K}
   ObsK* d_obs = nullptr;                  // obstacle capsules of Eq. 15
+  float* d_fext = nullptr;                // F_ext of the constant external wrench (6)
   float* d_part = nullptr;                // the rollout blocks' Eq. 4 partials [nb][part_stride(T)]
   unsigned* d_done = nullptr;             // merge blocks finished (reset by the last one)
   int feat = 0;                           // FEAT_* cost terms of the rollouts
@@ -218,6 +219,7 @@ int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, Pr
     return -1;
   }
   if (c->collision < 0 || c->collision > 2) { *why = "collision must be 0, 1 or 2"; return -1; }
+  if (c->ext_wrench && !finite_all(c->f_ext, 6)) { *why = "f_ext must be finite"; return -1; }
   if (c->collision) {
     if (!std::isfinite(c->w_collision) || !std::isfinite(c->d_th_self) ||
         !std::isfinite(c->d_th_obs) || !finite_all(c->link_radius, 7)) {
@@ -329,6 +331,7 @@ int convert(const mppi_robot* rb, const mppi_cost* c, const mppi_config* cfg, Pr
     k.fdes6[a] = static_cast<float>(c->f_des6[a]);
     k.wreg6[a] = static_cast<float>(c->w_reg6[a]);
   }
+  P->fext = nullptr;  // set by mppi_create once the handle's buffer exists
   P->dt = static_cast<float>(cfg->dt);
   P->lambda = static_cast<float>(cfg->lambda);
   for (int j = 0; j < 7; ++j) P->sigma[j] = static_cast<float>(cfg->sigma[j]);
@@ -742,6 +745,14 @@ int mppi_create(const mppi_robot* robot, const mppi_cost* cost, const mppi_confi
   if ((e = cudaMalloc(&h->d_prop, plan_b)) != cudaSuccess) return bail(e, "cudaMalloc prop");
   if ((e = cudaMalloc(&h->d_ctl, 2 * sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc ctl");
   if ((e = cudaMalloc(&h->d_obs, sizeof(ObsK))) != cudaSuccess) return bail(e, "cudaMalloc obs");
+  if (cost->ext_wrench) {
+    if ((e = cudaMalloc(&h->d_fext, sizeof(float) * 8)) != cudaSuccess) return bail(e, "cudaMalloc fext");
+    float F[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int a = 0; a < 6; ++a) F[a] = static_cast<float>(cost->f_ext[a]);
+    if ((e = cudaMemcpy(h->d_fext, F, sizeof F, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(e, "fext");
+    h->P.fext = h->d_fext;
+  }
   {
     const size_t nb = (static_cast<size_t>(K) + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
     if ((e = cudaMalloc(&h->d_part, sizeof(float) * nb * part_stride(T))) != cudaSuccess)
@@ -805,6 +816,7 @@ int mppi_destroy(mppi_t h) {
   cudaFree(h->d_prop);
   cudaFree(h->d_ctl);
   cudaFree(h->d_obs);
+  cudaFree(h->d_fext);
   cudaFree(h->d_part);
   cudaFree(h->d_done);
   cudaFree(h->d_out);
@@ -1109,6 +1121,29 @@ int mppi_set_obstacles_device(mppi_t h, int n, const float* d_obs) {
                                 cudaMemcpyDeviceToDevice, h->stream));
   set_int_kernel<<<1, 32, 0, h->stream>>>(&h->d_obs->n, n);
   CUDA_TRY(h, cudaGetLastError());
+  return MPPI_OK;
+}
+
+int mppi_set_external_wrench(mppi_t h, const float F[6]) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (!h->d_fext) return fail(h, MPPI_ERR_INVALID_ARG, "the handle has no external wrench");
+  if (!F) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  float img[6];
+  for (int a = 0; a < 6; ++a) {
+    if (!std::isfinite(F[a])) return fail(h, MPPI_ERR_INVALID_ARG, "F_ext must be finite");
+    img[a] = F[a];
+  }
+  // pageable source: the call returns once the image has been staged
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_fext, img, sizeof img, cudaMemcpyHostToDevice, h->stream));
+  return MPPI_OK;
+}
+
+int mppi_set_external_wrench_device(mppi_t h, const float* d_F) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (!h->d_fext) return fail(h, MPPI_ERR_INVALID_ARG, "the handle has no external wrench");
+  if (!d_F) return fail(h, MPPI_ERR_INVALID_ARG, "null argument");
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_fext, d_F, sizeof(float) * 6, cudaMemcpyDeviceToDevice,
+                              h->stream));
   return MPPI_OK;
 }
 

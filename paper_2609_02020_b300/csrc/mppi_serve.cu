@@ -814,9 +814,10 @@ int mppi_server_add_problem(mppi_server_t s, const mppi_robot* robot, const mppi
   Problem p;
   std::string why;
   if (mppi_convert_params(robot, cost, cfg, &p.P, &why) != 0) return sfail(s, MPPI_ERR_INVALID_ARG, why);
-  if (p.P.cost.fest || p.P.cost.coll)
+  if (p.P.cost.fest || p.P.cost.coll || cost->ext_wrench)
     return sfail(s, MPPI_ERR_INVALID_ARG,
-                 "the server takes neither the wrench-estimate nor the collision cost");
+                 "the server takes neither the wrench-estimate nor the collision cost nor the "
+                 "constant external wrench");
   p.K = cfg->K;
   p.T = cfg->T;
   if (scratch_bytes(p.K, p.T) > s->pool.size)

@@ -156,9 +156,10 @@ int mppi_step_static(const mppi_robot* robot, const mppi_cost* cost, const mppi_
   ProbK P;
   std::string why;
   if (mppi_convert_params(robot, cost, cfg, &P, &why) != 0) return fail(MPPI_ERR_INVALID_ARG, why);
-  if (P.cost.fest || P.cost.coll)
+  if (P.cost.fest || P.cost.coll || cost->ext_wrench)
     return fail(MPPI_ERR_INVALID_ARG,
-                "mppi_step_static takes neither the wrench-estimate nor the collision cost");
+                "mppi_step_static takes neither the wrench-estimate nor the collision cost nor "
+                "the constant external wrench");
   StaticScratch* sc = nullptr;
   int rc = scratch_for_current_device(&sc);
   if (rc != MPPI_OK) return rc;

@@ -82,6 +82,8 @@ class Cost(C.Structure):
         ("link_radius", C.c_double * NJ),
         ("n_obstacles", C.c_int),
         ("obstacles", C.c_double * 7 * OBS_MAX),
+        ("ext_wrench", C.c_int),
+        ("f_ext", C.c_double * 6),
     ]
 
 
@@ -134,6 +136,7 @@ EXPORTS = [
     "mppi_simulate_device", "mppi_set_plan_device", "mppi_get_plan_device",
     "mppi_get_updated_plan_device", "mppi_set_proposal_device", "mppi_gravity_torque",
     "mppi_force_estimate_device", "mppi_set_obstacles", "mppi_set_obstacles_device",
+    "mppi_set_external_wrench", "mppi_set_external_wrench_device",
     "mppi_get_variant", "mppi_measure_fp32_peak", "mppi_get_correction_device",
     # include/mppi_serve.h
     "mppi_pool_create", "mppi_pool_destroy", "mppi_pool_alloc", "mppi_pool_free",
@@ -200,6 +203,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_get_variant": ([H, C.POINTER(C.c_int)], C.c_int),
         "mppi_measure_fp32_peak": ([C.POINTER(C.c_double)], C.c_int),
         "mppi_set_obstacles_device": ([H, C.c_int, vp], C.c_int),
+        "mppi_set_external_wrench": ([H, fp], C.c_int),
+        "mppi_set_external_wrench_device": ([H, vp], C.c_int),
         "mppi_pool_create": ([C.c_size_t, C.POINTER(C.c_void_p)], C.c_int),
         "mppi_pool_destroy": ([H], C.c_int),
         "mppi_pool_alloc": ([H, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
@@ -316,6 +321,10 @@ def cost_struct(d: dict) -> Cost:
     for o in range(obs.shape[0]):
         for a in range(7):
             c.obstacles[o][a] = obs[o, a]
+    c.ext_wrench = int(d.get("ext_wrench", 0))
+    fe = np.asarray(d.get("f_ext", np.zeros(6)), dtype=np.float64).reshape(6)
+    for a in range(6):
+        c.f_ext[a] = fe[a]
     return c
 
 
@@ -477,6 +486,15 @@ class MPPI:
     def set_obstacles_device(self, d_obs):
         """The same from a device tensor [n][7] (stream-ordered)."""
         self._check(self.lib.mppi_set_obstacles_device(self.h, int(d_obs.shape[0]), _dptr(d_obs)))
+
+    def set_external_wrench(self, F):
+        """Replaces F_ext of the constant external wrench (force xyz; moment
+        about the end-effector point xyz, world frame), stream-ordered."""
+        self._check(self.lib.mppi_set_external_wrench(self.h, _fp(_f32(F, 6))))
+
+    def set_external_wrench_device(self, d_F):
+        """The same from a device tensor of 6 floats (stream-ordered)."""
+        self._check(self.lib.mppi_set_external_wrench_device(self.h, _dptr(d_F)))
 
     def force_estimate_device(self, d_q, d_v, d_F):
         """Wrench estimates F = Jbar^T (v - g(q)) (Eq. 13): d_q, d_v [n][7] ->
