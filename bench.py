@@ -461,13 +461,14 @@ def run_ours(args, rank, world):
                                   "L2 flushed before each"},
             "update_hz": 1e3 / mean_ms,
             "kernels_ms": {kname: ms_roll, "merge_kernel": ms_upd},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 25 * 4,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 26 * 4,
                     "d2h_bytes_per_step": (16 + T * 7) * 4, "calls": int(e2e_ms.size),
                     "p50_ms": float(np.percentile(e2e_ms, 50)),
                     "p99_ms": float(np.percentile(e2e_ms, 99)),
                     "api": "mppi_step (host buffers, CUDA graph replay: H2D copy of the "
-                           "inputs, two kernels, the merge kernel writing tau0, status and "
-                           "plan into pinned host memory), host clock per call"},
+                           "inputs and a sequence word, two kernels, the merge kernel writing "
+                           "tau0, status, plan and last the sequence word into pinned host "
+                           "memory, which the host polls), host clock per call"},
             "roofline": roof,
             "clocks": clocks,
             "gpu_launches": launches,

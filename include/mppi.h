@@ -197,9 +197,13 @@ MPPI_API int mppi_destroy(mppi_t h);
 /* One MPPI update from host memory: copies (q, qd, goal, plane) to the
  * device, runs the rollouts and the update, and returns tau0 = u*_0 (7
  * floats) and, when plan_out is not NULL, the shifted plan [T][7] that the
- * next update samples around.  The update kernel writes its output record
+ * next update samples around.  The merge kernel writes its output record
  * straight into the handle's pinned host buffer (no separate device-to-host
- * copy).  Blocks until the result is in host memory.
+ * copy), a sequence word last.  Blocks until the result is in host memory:
+ * the calling thread polls that word (it does not sleep), and a stream that
+ * ends or fails without it is synchronised and its error returned; the
+ * stream may still be retiring the update's last instructions when the call
+ * returns (later calls on the handle are ordered after it).
  * Returns MPPI_ERR_NONFINITE (plan unchanged, iter unchanged) when no sample
  * has a finite cost. */
 MPPI_API int mppi_step(mppi_t h, const float q[7], const float qd[7], const float goal[7],

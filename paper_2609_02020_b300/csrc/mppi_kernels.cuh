@@ -115,6 +115,7 @@ __device__ __forceinline__ void block_partial(const float* s_S, float* s_w, int 
 constexpr int OUT_TAU0 = 0;
 constexpr int OUT_STATUS = 7;   // written as an int: 0 ok, 1 no finite cost
 constexpr int OUT_STATS = 8;    // S_min, Z, n_eff, n_nonfinite
+constexpr int OUT_SEQ = 12;     // host steps: the step's sequence word, written last
 constexpr int OUT_PLAN = 16;    // shifted plan [T][7]
 
 // Copies the inputs into the block's staged record (IN_STAGED floats) and,
@@ -1887,7 +1888,11 @@ __device__ __forceinline__ Lse<Acc> lse_shfl(const Lse<Acc>& a, int o) {
 // Launched as a programmatic dependent of the rollouts.  When this update
 // has a second proposal (k_split < K), the last block (done counter) resets
 // the counter and, through ctl_reset (= ksplit_p's {k_split, K}), consumes
-// the proposal (k_split := K).  Acc: the type of the sums over blocks.
+// the proposal (k_split := K).  With seq_in (host steps, whose output record
+// is mapped host memory) every block fences its record entries to system
+// scope before the count and the last block then writes *seq_in to the
+// record's OUT_SEQ word, after which the host may read the whole record.
+// Acc: the type of the sums over blocks.
 constexpr int MERGE_THREADS = 256;
 
 template <typename Acc>
@@ -1897,7 +1902,7 @@ merge_kernel(int K, int T, float lambda, int nb, int pstride, const float* part,
              float* __restrict__ plan_next, float* __restrict__ out,
              unsigned long long* __restrict__ iter_p, const float* __restrict__ prop,
              const int* ksplit_p, float* __restrict__ tau_dst, float* __restrict__ plan_dst,
-             unsigned* done, int* ctl_reset) {
+             unsigned* done, int* ctl_reset, const unsigned* seq_in) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   __shared__ Lse<Acc> sm[MERGE_THREADS / 32];
   __shared__ float sm_bad[MERGE_THREADS / 32];
@@ -1947,13 +1952,6 @@ merge_kernel(int K, int T, float lambda, int nb, int pstride, const float* part,
     acc = lse_merge(acc, sm[i], inv_l);
     bad += sm_bad[i];
   }
-  // with a second proposal in this update, the last block to finish resets
-  // the counter and consumes it; every block read k_split above, and the
-  // acquire-release count orders those reads before the reset
-  if (ctl_reset && k_split < K && atomic_add_acq_rel(done, 1u) == gridDim.x - 1) {
-    *done = 0u;
-    ctl_reset[0] = ctl_reset[1];
-  }
   const bool ok = isfinite(acc.m);
   float us = u;
   if (ok) {
@@ -1968,6 +1966,22 @@ merge_kernel(int K, int T, float lambda, int nb, int pstride, const float* part,
     if (out) write_stats(out, ok, acc.m, static_cast<double>(acc.z), static_cast<double>(acc.z2),
                          static_cast<double>(bad));
     if (iter_p && ok) *iter_p += 1ull;
+  }
+  // the last block to finish resets the counter; with a second proposal in
+  // this update it consumes it (every block read k_split above, and the
+  // acquire-release count orders those reads before the reset), and in a
+  // host step it writes the completion word after every block's entries
+  const bool second = ctl_reset && k_split < K;
+  if (second || seq_in) {
+    if (seq_in) __threadfence_system();
+    if (atomic_add_acq_rel(done, 1u) == gridDim.x - 1) {
+      *done = 0u;
+      if (second) ctl_reset[0] = ctl_reset[1];
+      if (seq_in) {
+        __threadfence_system();
+        reinterpret_cast<volatile unsigned*>(out)[OUT_SEQ] = *seq_in;
+      }
+    }
   }
 }
 

@@ -3,6 +3,7 @@
 // ownership, kernel launches and CUDA-graph replay of one update.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -86,6 +87,7 @@ struct mppi_s {
   float* h_out = nullptr;                 // pinned, mapped: host steps write it directly
   float* h_out_dev = nullptr;             // h_out as the device sees it
   bool out_on_host = false;               // the last update's record is in h_out, not d_out
+  unsigned host_seq = 0;                  // sequence word of the last host step
   int cur = 0;  // index of the current nominal plan
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   std::string err;
@@ -488,7 +490,7 @@ cudaError_t launch_update(mppi_s* h, const float* S, const float* noise, const f
 // record at `out` and iter += 1; the last block consumes a second proposal.
 cudaError_t launch_merge(mppi_s* h, const float* plan, float* ustar, float* plan_next, float* out,
                          unsigned long long* iter, float* tau_dst = nullptr,
-                         float* plan_dst = nullptr) {
+                         float* plan_dst = nullptr, const unsigned* seq_in = nullptr) {
   // programmatic dependent launch: the merge blocks may start as the rollout
   // kernel's retire and wait (griddepcontrol.wait) for its results, which
   // hides the launch gap between the two kernels
@@ -511,11 +513,11 @@ cudaError_t launch_merge(mppi_s* h, const float* plan, float* ustar, float* plan
     return cudaLaunchKernelEx(&lc, merge_kernel<double>, K, T, lambda, nb, ps, part, plan, ustar,
                               plan_next, out, iter, static_cast<const float*>(h->d_prop),
                               static_cast<const int*>(h->d_ctl), tau_dst, plan_dst, h->d_done,
-                              h->d_ctl);
+                              h->d_ctl, seq_in);
   return cudaLaunchKernelEx(&lc, merge_kernel<float>, K, T, lambda, nb, ps, part, plan, ustar,
                             plan_next, out, iter, static_cast<const float*>(h->d_prop),
                             static_cast<const int*>(h->d_ctl), tau_dst, plan_dst, h->d_done,
-                            h->d_ctl);
+                            h->d_ctl, seq_in);
 }
 
 // the whole update on device buffers: rollouts from the inputs at `in`
@@ -524,12 +526,13 @@ cudaError_t launch_merge(mppi_s* h, const float* plan, float* ustar, float* plan
 // `out` (default d_out); the merge's last block consumes a second proposal
 // set for this update (k_split := K)
 cudaError_t enqueue_update(mppi_s* h, int cur, const float* in = nullptr, float* tau_dst = nullptr,
-                           float* plan_dst = nullptr, float* out = nullptr) {
+                           float* plan_dst = nullptr, float* out = nullptr,
+                           const unsigned* seq_in = nullptr) {
   cudaError_t e = launch_rollout(h, in ? in : h->d_in, h->d_plan[cur], h->d_S, h->d_noise,
                                  h->d_part);
   if (e != cudaSuccess) return e;
   return launch_merge(h, h->d_plan[cur], h->d_ustar, h->d_plan[cur ^ 1], out ? out : h->d_out,
-                      h->d_iter, tau_dst, plan_dst);
+                      h->d_iter, tau_dst, plan_dst, seq_in);
 }
 
 __global__ void set_int_kernel(int* dst, int v) {
@@ -539,13 +542,15 @@ __global__ void set_int_kernel(int* dst, int v) {
 
 // host-buffer step: H2D inputs, update, D2H outputs (captured once per parity)
 cudaError_t enqueue_host_step(mppi_s* h, int cur) {
-  cudaError_t e = cudaMemcpyAsync(h->d_in, h->h_in, sizeof(float) * IN_FLOATS,
+  // the inputs and, after them, the step's sequence word (104 B)
+  cudaError_t e = cudaMemcpyAsync(h->d_in, h->h_in, sizeof(float) * (IN_FLOATS + 1),
                                   cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return e;
-  // the update kernel writes the output record straight into pinned host
+  // the merge kernel writes the output record straight into pinned host
   // memory (tau0, status, stats, shifted plan: 568 B at T = 18), so no
-  // device-to-host copy follows it
-  return enqueue_update(h, cur, nullptr, nullptr, nullptr, h->h_out_dev);
+  // device-to-host copy follows it, and the sequence word last
+  return enqueue_update(h, cur, nullptr, nullptr, nullptr, h->h_out_dev,
+                        reinterpret_cast<const unsigned*>(h->d_in + IN_FLOATS));
 }
 
 void destroy_graphs(mppi_s* h) {
@@ -841,6 +846,8 @@ int mppi_step(mppi_t h, const float q[7], const float qd[7], const float goal[7]
   std::memcpy(h->h_in + 7, qd, 7 * sizeof(float));
   std::memcpy(h->h_in + 14, goal, 7 * sizeof(float));
   std::memcpy(h->h_in + 21, plane, 4 * sizeof(float));
+  const unsigned seq = ++h->host_seq;
+  std::memcpy(h->h_in + IN_FLOATS, &seq, sizeof seq);
   const int cur = h->cur;
   if (h->use_graph) {
     if (!h->graph[cur]) {
@@ -861,7 +868,17 @@ int mppi_step(mppi_t h, const float q[7], const float qd[7], const float goal[7]
   } else {
     CUDA_TRY(h, enqueue_host_step(h, cur));
   }
-  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  // the record is complete once its sequence word reads this step's: poll
+  // it (about 2.5 us sooner than a stream synchronisation); a stream that
+  // finished or failed without it ends the poll, and the synchronisation
+  // then reports the error
+  {
+    const volatile unsigned* word = reinterpret_cast<const volatile unsigned*>(h->h_out + OUT_SEQ);
+    for (unsigned n = 1; *word != seq; ++n)
+      if ((n & 4095u) == 0 && cudaStreamQuery(h->stream) != cudaErrorNotReady) break;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    if (*word != seq) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
   h->cur = cur ^ 1;  // the update wrote the next plan into the other buffer
   h->out_on_host = true;
   rc = read_status(h);
