@@ -186,3 +186,14 @@ def test_long_horizon_shared_memory_opt_in():
     tau_g = oracle.rnea(c["rb"], c["q"], np.zeros(7), np.zeros(7))
     g, o = _run(c, plan=f32(np.tile(tau_g, (c["T"], 1))))
     _assert_costs(g["S"], o["S"])
+
+
+@pytest.mark.parametrize("variant", [3, 2])
+@pytest.mark.parametrize("K,T", [(1, 18), (33, 2), (77, 5), (1000, 1)])
+def test_hinge_ragged_sizes(K, T, variant):
+    """Ragged K against the 32-sample blocks (on the warp-specialised kernel
+    the lanes past K replay sample K - 1 through all five warps) and short T;
+    both collision warps' pair sets and the culled pairs included."""
+    c = _case(1, 2, K=K, T=T)
+    g, o = _run(c, variant=variant)
+    _assert_costs(g["S"], o["S"])

@@ -124,3 +124,13 @@ def test_calls_that_do_not_take_it_refuse_it():
     bad = dict(cost, f_ext=np.array([0, 0, np.inf, 0, 0, 0]))
     with pytest.raises(mppi.MPPIError):
         gpu_controller(make_case(0, cost=bad, K=64, T=4))
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("K,T", [(1, 18), (33, 2), (77, 5)])
+def test_ragged_sizes(K, T, variant):
+    c = make_case(2, cost=_with_wrench(parity_cost(), _wrench(2)), K=K, T=T)
+    g = _step(c, variant=variant)
+    o = oracle_step(c)
+    _assert_costs(g["S"], o["S"])
+    assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL

@@ -201,3 +201,18 @@ def test_fest_full_size_matches_oracle(variant):
     print(f"force estimate full size, variant {variant}: max |du*| {err:.2e} N m, "
           f"n_eff {o['stats'][2]:.1f}")
     assert err <= HEAVY_MISS_BOUND
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("K,T", [(1, 18), (33, 2), (77, 5), (1000, 1)])
+def test_fest_ragged_sizes(K, T, variant):
+    """Ragged K against the 32-sample blocks (the warp-specialised kernel's
+    lanes past K replay sample K - 1 through its four warps) and short T:
+    every cost and the best sample.  Around the gravity-holding plan these
+    costs are 280-9000 lambda with the weights on one or two samples, the
+    heavy-weight regime where the plan bar is a recorded miss, so the plan is
+    left to the tests above."""
+    c = make_case(3, cost=synth.cost_force_estimate(1e-4, base=parity_cost()), K=K, T=T)
+    g, o = _run_fest(c, _hold_plan(c), variant=variant)
+    _assert_costs(g["S"], o["S"])
+    assert np.argmin(g["S"]) == np.argmin(o["S"])
