@@ -71,7 +71,7 @@ FLOP_EXECUTED_PER_ROLLOUT_STEP = {("contact", "rollout_kernel_ws"): 4970.2,
 # launch.
 # Only kernels captured since their last change are listed; the others
 # report null.
-ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel_ws"): 61184,
+ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel_ws"): 64640,
                                     ("force_estimate", "rollout_kernel_ws_fest"): 73728,
                                     ("force_estimate", "rollout_kernel_rolled"): 67840,
                                     ("collision", "rollout_kernel_ws"): 127616}
