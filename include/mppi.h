@@ -174,7 +174,8 @@ typedef struct mppi_config {
   int variant;      /* rollout kernel: 0 default, 1 links unrolled in registers,
                        2 link loops rolled through shared memory, 3 three
                        warps per 32 samples (kinematic chain / link forces and
-                       costs / link forces and noise)                        */
+                       costs / link forces and noise; one more warp for the
+                       wrench estimate, two more for the collision cost)    */
 } mppi_config;
 
 #define MPPI_T_MAX 256
