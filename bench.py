@@ -624,13 +624,20 @@ def run_sweep(args, rank, world):
                     d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, plane), device="cuda")
                     d_tau = torch.zeros(7, device="cuda")
                     d_plan = torch.zeros(T, 7, device="cuda")
+                    # every update starts from the same state and the zero plan
+                    # (outside the timed events): repeated warm-started updates of
+                    # one fixed state are no closed loop, and over thousands of
+                    # them the plan can drift until no rollout stays finite
+                    zero_plan = np.zeros((T, 7), np.float32)
                     for _ in range(max(args.warmup, 3)):
+                        ctl.set_plan(zero_plan)
                         ctl.step_device(d_in, d_tau, d_plan)
                     st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
                     en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
                     torch.cuda.synchronize()
                     a = clk.mark()
                     for i in range(steps):
+                        ctl.set_plan(zero_plan)
                         flush.zero_()
                         st[i].record(stream)
                         ctl.step_device(d_in, d_tau, d_plan)
