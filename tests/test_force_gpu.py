@@ -216,3 +216,14 @@ def test_fest_ragged_sizes(K, T, variant):
     g, o = _run_fest(c, _hold_plan(c), variant=variant)
     _assert_costs(g["S"], o["S"])
     assert np.argmin(g["S"]) == np.argmin(o["S"])
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+def test_fest_longest_horizon(variant):
+    # T = 256 (MPPI_T_MAX) at dt = 1 ms: the warp-specialised kernel's shared
+    # memory does not grow with T, the rolled kernel's does (opt-in above 48 KB)
+    c = make_case(5, cost=synth.cost_force_estimate(1e-4, base=parity_cost()), K=64, T=256,
+                  dt=0.001)
+    g, o = _run_fest(c, _hold_plan(c), variant=variant)
+    _assert_costs(g["S"], o["S"])
+    assert np.argmin(g["S"]) == np.argmin(o["S"])
