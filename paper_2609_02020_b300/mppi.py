@@ -420,17 +420,23 @@ class MPPI:
         self._check(self.lib.mppi_step_device(self.h, _dptr(d_in), _dptr(d_tau0), _dptr(d_plan)))
 
     def sync(self) -> int:
+        """mppi_sync: waits for the handle's stream; the last update's status."""
         return self.lib.mppi_sync(self.h)
 
     def rollout_device(self, d_in, d_S, d_noise=None):
+        """mppi_rollout_device: the rollouts alone (costs, and the noise when
+        d_noise is given) from the inputs at d_in; queued on the stream."""
         self._check(self.lib.mppi_rollout_device(self.h, _dptr(d_in), _dptr(d_S), _dptr(d_noise)))
 
     def update_device(self, d_S, d_noise, d_plan, d_ustar, d_plan_next):
+        """mppi_update_device: Eq. 4 and the shift from caller-supplied costs and
+        noise; queued on the stream."""
         self._check(self.lib.mppi_update_device(self.h, _dptr(d_S), _dptr(d_noise), _dptr(d_plan),
                                                 _dptr(d_ustar), _dptr(d_plan_next)))
 
     # -- inspection / state -------------------------------------------------
     def costs(self) -> np.ndarray:
+        """The last update's K costs S_k (Eq. 3)."""
         S = np.zeros(self.K, dtype=np.float32)
         self._check(self.lib.mppi_get_costs(self.h, _fp(S)))
         return S
@@ -442,27 +448,33 @@ class MPPI:
         return n
 
     def updated_plan(self) -> np.ndarray:
+        """The last update's u* [T][7] before the shift (Eq. 4b)."""
         u = np.zeros((self.T, NJ), dtype=np.float32)
         self._check(self.lib.mppi_get_updated_plan(self.h, _fp(u)))
         return u
 
     def stats(self) -> np.ndarray:
+        """S_min, Z, n_eff and the non-finite count of the last update."""
         s = np.zeros(4, dtype=np.float64)
         self._check(self.lib.mppi_get_stats(self.h, s.ctypes.data_as(C.POINTER(C.c_double))))
         return s
 
     def set_plan(self, u):
+        """Sets the warm start [T][7] the next update samples around."""
         self._check(self.lib.mppi_set_plan(self.h, _fp(_f32(u, self.T * NJ))))
 
     def get_plan(self) -> np.ndarray:
+        """The warm start [T][7] the next update samples around."""
         u = np.zeros((self.T, NJ), dtype=np.float32)
         self._check(self.lib.mppi_get_plan(self.h, _fp(u)))
         return u
 
     def set_iter(self, it: int):
+        """Sets the update counter (the Philox counter's iteration word)."""
         self._check(self.lib.mppi_set_iter(self.h, int(it)))
 
     def get_iter(self) -> int:
+        """The update counter: successful updates so far (or as set)."""
         v = C.c_uint64()
         self._check(self.lib.mppi_get_iter(self.h, C.byref(v)))
         return int(v.value)
