@@ -743,3 +743,15 @@ def test_status_and_stats_follow_the_last_update_path():
         assert g.stats()[3] == c["K"]
         g.step(c["q"], c["qd"], c["goal"], c["plane"])
         assert g.sync() == 0 and g.stats()[3] == 0
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_longest_horizon_full_update(variant):
+    """T = 256 (MPPI_T_MAX) at dt = 1 ms with K = 4096 and the parity
+    weights: every cost, every noise value and the plan against the
+    oracle's whole update (the warm start's 1792 plan entries, one merge
+    block each), on the default (warp-specialised), register and rolled
+    kernels."""
+    c = make_case(2, cost=parity_cost(), K=4096, T=256, dt=0.001)
+    o = oracle_step(c, nthreads=os.cpu_count() or 8)
+    assert_full_update(c, o, variant)
