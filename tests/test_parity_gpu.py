@@ -755,3 +755,16 @@ def test_longest_horizon_full_update(variant):
     c = make_case(2, cost=parity_cost(), K=4096, T=256, dt=0.001)
     o = oracle_step(c, nthreads=os.cpu_count() or 8)
     assert_full_update(c, o, variant)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_per_joint_sigma_with_a_zero(variant):
+    """Sigma of Eq. 2 per joint, one of them zero (that joint is not
+    perturbed: its u* equals its warm start exactly)."""
+    sig = np.array([1.0, 2.5, 0.0, 3.0, 0.5, 2.0, 4.0])
+    c = make_case(1, cost=parity_cost(), sigma=sig)
+    g, o = run_pair(c, variant=variant)
+    assert_costs(g["S"], o["S"])
+    assert_plan(g, o)
+    assert np.all(g["noise"].reshape(c["T"], 7, c["K"])[:, 2, :] == 0.0)
+    assert np.all(g["ustar"][:, 2] == 0.0)
