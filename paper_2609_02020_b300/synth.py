@@ -30,7 +30,7 @@ ROD_RADIUS = 0.04
 BASE_HEIGHT = 0.1
 
 # purpose tags so that robot, state, goal and plan streams never overlap
-_ROBOT, _STATE, _GOAL, _PLAN, _BATCH = 1, 2, 3, 4, 5
+_ROBOT, _STATE, _GOAL, _PLAN, _BATCH, _GENERAL = 1, 2, 3, 4, 5, 6
 
 
 def _rng(seed: int, purpose: int) -> np.random.Generator:
@@ -74,6 +74,32 @@ def arm(seed: int = 0, armature: float = 0.1, damping: float = 0.1) -> dict:
         gravity=np.array([0.0, 0.0, -9.81]),
         length=length,
     )
+
+
+def arm_general(seed: int = 0, armature: float = 0.1, damping: float = 0.1) -> dict:
+    """The seeded arm with general geometry: each joint's fixed rotation is a
+    random roll-pitch-yaw, its axis a random unit vector in its own frame,
+    the joint offsets, centres of mass and end-effector point leave the
+    link axis, and the link inertias carry products of inertia (the rod's
+    principal inertia turned by a random rotation)."""
+    a = arm(seed, armature, damping)
+    g = _rng(seed, _GENERAL)
+    n = N_JOINTS
+    a["joint_rpy"] = g.uniform(-np.pi, np.pi, (n, 3))
+    ax = g.normal(0.0, 1.0, (n, 3))
+    a["axis"] = ax / np.linalg.norm(ax, axis=1, keepdims=True)
+    a["joint_xyz"] = a["joint_xyz"] + np.concatenate(
+        [np.zeros((1, 3)), g.uniform(-0.05, 0.05, (n - 1, 3))])
+    a["com"] = a["com"] + g.uniform(-0.03, 0.03, (n, 3))
+    a["ee_xyz"] = a["ee_xyz"] + g.uniform(-0.03, 0.03, 3)
+    inertia = np.zeros((n, 6))
+    for i in range(n):
+        d = a["inertia"][i]
+        Q, _ = np.linalg.qr(g.normal(0.0, 1.0, (3, 3)))
+        I = Q @ np.diag(d[:3]) @ Q.T
+        inertia[i] = [I[0, 0], I[1, 1], I[2, 2], I[0, 1], I[0, 2], I[1, 2]]
+    a["inertia"] = inertia
+    return a
 
 
 def state(seed: int, robot: dict) -> tuple[np.ndarray, np.ndarray]:

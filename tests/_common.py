@@ -33,8 +33,8 @@ def parity_cost(scale: float = 0.05) -> dict:
 
 def make_case(seed: int, *, contact: bool = False, cost: dict | None = None, K: int = 256,
               T: int = 18, dt: float = 0.01, lam: float = 1.0, sigma=2.0, armature: float = 0.1,
-              penetration: float = 0.02) -> dict:
-    arm = synth.arm(seed, armature=armature)
+              penetration: float = 0.02, general: bool = False) -> dict:
+    arm = (synth.arm_general if general else synth.arm)(seed, armature=armature)
     q, qd = synth.state(1000 + seed, arm)
     goal = synth.goal(1000 + seed, arm)
     if cost is None:
