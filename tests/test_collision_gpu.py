@@ -197,3 +197,14 @@ def test_hinge_ragged_sizes(K, T, variant):
     c = _case(1, 2, K=K, T=T)
     g, o = _run(c, variant=variant)
     _assert_costs(g["S"], o["S"])
+
+
+@pytest.mark.parametrize("variant", [3, 2])
+def test_hinge_general_geometry(variant):
+    # off-axis joint offsets: the link capsules' rigid lengths come from the
+    # general joint positions (synth.arm_general)
+    c0 = make_case(1, general=True)
+    obs = f32(synth.obstacles_near(oracle.link_points(c0["rb"], c0["q"]), 1, 3))
+    c = make_case(1, cost=synth.cost_collision(2, w=10.0, obstacles=obs), general=True)
+    g, o = _run(c, variant=variant)
+    _assert_costs(g["S"], o["S"])

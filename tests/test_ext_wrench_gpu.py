@@ -134,3 +134,12 @@ def test_ragged_sizes(K, T, variant):
     o = oracle_step(c)
     _assert_costs(g["S"], o["S"])
     assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_general_geometry(variant):
+    c = make_case(0, cost=_with_wrench(parity_cost(), _wrench(0)), general=True)
+    g = _step(c, variant=variant)
+    o = oracle_step(c)
+    _assert_costs(g["S"], o["S"])
+    assert np.abs(g["ustar"] - o["ustar"]).max() <= PLAN_TOL

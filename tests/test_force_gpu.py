@@ -227,3 +227,15 @@ def test_fest_longest_horizon(variant):
     g, o = _run_fest(c, _hold_plan(c), variant=variant)
     _assert_costs(g["S"], o["S"])
     assert np.argmin(g["S"]) == np.argmin(o["S"])
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("seed", range(2))
+def test_fest_general_geometry(seed, variant):
+    # oblique axes and products of inertia (synth.arm_general): the estimate's
+    # Jacobian, g(q) and factors of M in the kernels' link frames
+    c = make_case(seed, cost=synth.cost_force_estimate(base=synth.cost_contact()), general=True)
+    g, o = _run_fest(c, _hold_plan(c), variant=variant)
+    assert np.isfinite(o["S"]).all()
+    _assert_costs(g["S"], o["S"])
+    assert np.argmin(g["S"]) == np.argmin(o["S"])
