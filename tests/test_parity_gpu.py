@@ -825,3 +825,15 @@ def test_general_geometry_matches_oracle(seed, variant):
     else:
         assert np.argmin(g["S"]) == np.argmin(o["S"])
         assert max(plan_errors(g, o)) <= HEAVY_MISS_BOUND["c22"]
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_tilted_gravity(variant):
+    """A base mounted on a wall: gravity along a tilted direction (the
+    kernels take the world gravity vector, not an axis)."""
+    c = make_case(2, cost=parity_cost())
+    c["arm"]["gravity"] = np.array([4.0, -3.0, -8.0])
+    c["rb"] = oracle.make_robot(c["arm"])
+    g, o = run_pair(c, variant=variant)
+    assert_costs(g["S"], o["S"])
+    assert_plan(g, o)
