@@ -81,11 +81,16 @@ def test_each_result_same_alone_and_in_the_mix(variant):
         assert np.abs(plan - p_ref).max() <= tol
 
 
-def test_served_problem_matches_oracle():
-    cases = [make_case(s, cost=parity_cost(), K=K, T=T) for s, K, T in
-             [(0, 700, 18), (1, 256, 9), (2, 1500, 25)]]
-    with mppi.Server(pool_bytes=256 << 20, max_problems=8, max_batch=8, lanes=1, variant=2,
-                     rollout_block=32) as srv:
+@pytest.mark.parametrize("variant", [2, 3])
+def test_served_problem_matches_oracle(variant):
+    """Three problems of uneven K and T served in one batch, one of them on an
+    arm of general geometry (synth.arm_general), on the rolled and the
+    warp-specialised serving kernels: tau0 and the shifted plan against the
+    oracle's update."""
+    cases = [make_case(s, cost=parity_cost(), K=K, T=T, general=gen) for s, K, T, gen in
+             [(0, 700, 18, False), (1, 256, 9, False), (2, 1500, 25, True)]]
+    with mppi.Server(pool_bytes=256 << 20, max_problems=8, max_batch=8, lanes=1,
+                     variant=variant, rollout_block=32) as srv:
         ids = register(srv, cases)
         res = [srv.wait(srv.submit(i, inputs(c))) for i, c in zip(ids, cases)]
         plans = [srv.get_plan(i) for i in ids]
