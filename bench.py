@@ -348,6 +348,7 @@ def run_ours(args, rank, world):
     # wave, else the register kernel, or the rolled one with an optional cost
     kname = {1: "rollout_kernel", 2: "rollout_kernel_rolled",
              3: "rollout_kernel_ws_fest" if args.cost == "force_estimate"
+             else "rollout_kernel_ws_small" if args.cost == "contact" and K <= 8192
              else "rollout_kernel_ws"}[ctl.variant()]
     plane = synth.plane_through(float(pose[2]))
     d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, plane), device="cuda")

@@ -1521,6 +1521,21 @@ rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
                                              part);
 }
 
+// The same for fewer samples: under an occupancy bound of four blocks per SM
+// ptxas gives the kernel 122 registers instead of 95 (the same arithmetic,
+// bit for bit), which is faster while few blocks share an SM and slower at
+// four (see WS_SMALL_K_MAX).
+template <bool STORE_NOISE>
+__global__ void __launch_bounds__(ws_threads(false, false), 4)
+rollout_kernel_ws_small(const __grid_constant__ ProbK P, const float* __restrict__ in,
+                        const unsigned long long* __restrict__ iter_p,
+                        const float* __restrict__ plan, float* __restrict__ S,
+                        float* __restrict__ noise, const float* __restrict__ prop,
+                        const int* __restrict__ ksplit_p, float* __restrict__ part) {
+  rollout_ws_block<STORE_NOISE, false, false>(P, in, iter_p, plan, S, noise, prop, ksplit_p,
+                                              nullptr, part);
+}
+
 // The same with the wrench-estimate warp: four 128-thread blocks per SM (the
 // shared-memory limit) need at most 128 registers per thread.
 template <bool STORE_NOISE>

@@ -32,6 +32,15 @@ using namespace mppi_dev;
 // The rolled kernel carries every optional cost term; the warp-specialised
 // kernel the collision cost or the wrench-estimate cost alone.  With one of
 // those (coll, fest) the alternative is the rolled kernel.
+#ifndef WS_SMALL_K_MAX
+// Up to this K the plain warp-specialised rollout runs as
+// rollout_kernel_ws_small.  Rollout at T = 18 on B300 (us), the default
+// instantiation against the small one: K = 512-2048: 62.5-64.0 against
+// 60.2-61.5; 4096: 64.5 against 62.6; 8192: 68.2 against 67.5; 12288: 84.4
+// for both; 16384: 86.6 against 87.7.
+#define WS_SMALL_K_MAX 8192
+#endif
+
 static int default_variant(int K, bool coll, bool fest) {
   const int other = (coll || fest) ? 2 : 1;
   int dev = 0, sms = 0, per_sm = 0;
@@ -401,6 +410,11 @@ cudaError_t prepare_rollout(mppi_s* h) {
   if (h->variant == 2) return prepare_rolled<0>(h->P.T);
   if (h->variant == 3) {
     const size_t smem = ws_smem_bytes();
+    for (auto f : {rollout_kernel_ws_small<true>, rollout_kernel_ws_small<false>}) {
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem));
+      if (e != cudaSuccess) return e;
+    }
     cudaError_t e = cudaFuncSetAttribute(rollout_kernel_ws<true, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
@@ -453,6 +467,15 @@ cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float*
   if (h->variant == 3) {
     const int wgrid = (h->P.K + WS_B - 1) / WS_B;
     const size_t smem = ws_smem_bytes();
+    if (h->P.K <= WS_SMALL_K_MAX) {
+      if (noise)
+        rollout_kernel_ws_small<true><<<wgrid, WS_THREADS, smem, h->stream>>>(
+            h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, part);
+      else
+        rollout_kernel_ws_small<false><<<wgrid, WS_THREADS, smem, h->stream>>>(
+            h->P, in, h->d_iter, plan, S, nullptr, h->d_prop, h->d_ctl, nullptr);
+      return cudaGetLastError();
+    }
     if (noise)
       rollout_kernel_ws<true, false><<<wgrid, WS_THREADS, smem, h->stream>>>(
           h->P, in, h->d_iter, plan, S, noise, h->d_prop, h->d_ctl, nullptr, part);
