@@ -77,6 +77,18 @@ MPPI_API int mppi_mlp_train_step(mppi_mlp_t m, const float* d_x, const float* d_
  * Needs n_in = 21 + 7T and n_out = 7T, at most 3 hidden layers and widths
  * <= 256 (MPPI_ERR_INVALID_ARG otherwise). */
 MPPI_API int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain);
+/* mppi_mlp_propose followed by mppi_step_device(h, d_in, d_tau0, d_plan) in
+ * one call: the update runs with the proposal it installs.  The two are
+ * queued back to back, and on the plain warp-specialised rollout kernel
+ * (variant 3 without the optional costs) the update's blocks whose samples
+ * all lie below n_plain start while the proposal is still being formed
+ * (programmatic dependent launch); the other blocks wait for it.  The
+ * result is the same, bit for bit, as the two calls made one after the
+ * other.  Errors as for the two calls, the message of either in
+ * mppi_last_error(NULL); nothing is queued when the proposal's arguments
+ * are rejected. */
+MPPI_API int mppi_mlp_propose_step_device(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain,
+                                          float* d_tau0, float* d_plan);
 /* The timeout path of the bounded device waits: one mbarrier wait that
  * nothing completes, given up after `cycles` SM clock cycles (1 ..
  * about 2e9, the limit of the GEMMs' own waits) through the same helper and

@@ -28,6 +28,13 @@ __device__ __forceinline__ void allow_dependent_launch() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Wait for the completion of the grid this one was launched as a
+// programmatic dependent of, and for its memory operations (no-op for a
+// grid launched without that attribute).
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // atomicAdd with acquire-release semantics at GPU scope
 __device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned* p, unsigned v) {
   unsigned old;
@@ -1230,7 +1237,9 @@ __device__ __forceinline__ void ws_draw(const ProbK& P, const float* plan, uint6
 template <bool STORE_NOISE, bool COLL, bool FEST>
 __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const float* plan,
                                          uint64_t iter, int k, bool live,
-                                         float* __restrict__ noise, const WsSmem& m, int tid) {
+                                         float* __restrict__ noise, const WsSmem& m, int tid,
+                                         const float* prop = nullptr,
+                                         const int* ksplit_p = nullptr, bool defer = false) {
   constexpr int NA = ws_threads(COLL, FEST);
   constexpr int B = WS_B;
   const int T = P.T;
@@ -1254,7 +1263,15 @@ __device__ __forceinline__ void ws_noise(const ProbK& P, const float* in, const 
     bar_sync(BAR_FORCES, NA);
     ws_backward_rows(P.rb, m, WS_ROWS2, tid);
     bar_arrive(BAR_MROWS, 3 * B);
-    if (s == 0) ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, 0, tid);
+    if (s == 0) {
+      if (defer) {
+        // the proposal kernel this grid overlaps: its plan and split are
+        // needed from the first draw on
+        grid_dependency_wait();
+        if (k >= (ksplit_p ? *ksplit_p : P.K)) plan = prop;
+      }
+      ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, 0, tid);
+    }
     bar_arrive(BAR_STEP, NA);
     if (s + 1 < T) ws_draw<STORE_NOISE>(P, plan, iter, k, live, noise, m, s + 1, tid);
   }
@@ -1466,11 +1483,27 @@ __device__ __forceinline__ void rollout_ws_block(const ProbK& P, const float* __
                                                  const float* __restrict__ prop,
                                                  const int* __restrict__ ksplit_p,
                                                  const ObsK* __restrict__ obs,
-                                                 float* __restrict__ part) {
+                                                 float* __restrict__ part, int kwait = -1) {
   extern __shared__ float4 dsm4[];
   float* dsm = reinterpret_cast<float*>(dsm4);
   const int K = P.K;
-  const int k_split = ksplit_p ? *ksplit_p : K;
+  // kwait >= 0: this grid is the programmatic dependent of a proposal kernel
+  // that may still be writing prop and *ksplit_p (kwait there unless its
+  // wait gave up).  A block whose samples all lie below kwait rolls out
+  // around plan either way and does not wait.  In the others (defer) warp 2
+  // waits for that grid's completion just before its first draw, the state
+  // phases of step 0 having run meanwhile, and every thread reads the split
+  // after the rollout.  The last block always defers, so that this grid
+  // completes after the proposal kernel and the merge, which waits for this
+  // grid, finds its writes done.
+  int k_split = K;
+  bool defer = false;
+  if (kwait < 0)
+    k_split = ksplit_p ? *ksplit_p : K;
+  else if ((blockIdx.x + 1) * WS_B <= kwait && blockIdx.x + 1 < gridDim.x)
+    k_split = kwait;
+  else
+    defer = true;
   float* s_in = dsm;
   float* s_obs = s_in + IN_STAGED;  // COLL: the block copy of the obstacles (load_obstacles)
   stage_inputs(P, in, s_in);
@@ -1491,13 +1524,17 @@ __device__ __forceinline__ void rollout_ws_block(const ProbK& P, const float* __
     if (live) S[k] = Sk;
     s_S[lane] = Sk;
   } else if (warp == 2) {
-    ws_noise<STORE_NOISE, COLL, FEST>(P, s_in, k < k_split ? plan : prop, *iter_p, k, live, noise,
-                                      m, lane);
+    ws_noise<STORE_NOISE, COLL, FEST>(P, s_in, defer || k < k_split ? plan : prop, *iter_p, k,
+                                      live, noise, m, lane, prop, ksplit_p, defer);
   } else if (COLL) {
     if (warp == 3) ws_collision<0>(P, m, s_obs, n_obs, lane);
     else ws_collision<1>(P, m, s_obs, n_obs, lane);
   } else if (FEST) {
     ws_estimate(P, m, lane);
+  }
+  if (defer) {
+    grid_dependency_wait();
+    k_split = ksplit_p ? *ksplit_p : K;
   }
   if (STORE_NOISE && part) {
     const int k0 = blockIdx.x * WS_B;
@@ -1516,9 +1553,10 @@ rollout_kernel_ws(const __grid_constant__ ProbK P, const float* __restrict__ in,
                   float* __restrict__ S, float* __restrict__ noise,
                   const float* __restrict__ prop = nullptr,
                   const int* __restrict__ ksplit_p = nullptr,
-                  const ObsK* __restrict__ obs = nullptr, float* __restrict__ part = nullptr) {
+                  const ObsK* __restrict__ obs = nullptr, float* __restrict__ part = nullptr,
+                  int kwait = -1) {
   rollout_ws_block<STORE_NOISE, COLL, false>(P, in, iter_p, plan, S, noise, prop, ksplit_p, obs,
-                                             part);
+                                             part, kwait);
 }
 
 // The same for fewer samples: under an occupancy bound of four blocks per SM
@@ -1531,9 +1569,10 @@ rollout_kernel_ws_small(const __grid_constant__ ProbK P, const float* __restrict
                         const unsigned long long* __restrict__ iter_p,
                         const float* __restrict__ plan, float* __restrict__ S,
                         float* __restrict__ noise, const float* __restrict__ prop,
-                        const int* __restrict__ ksplit_p, float* __restrict__ part) {
+                        const int* __restrict__ ksplit_p, float* __restrict__ part,
+                        int kwait = -1) {
   rollout_ws_block<STORE_NOISE, false, false>(P, in, iter_p, plan, S, noise, prop, ksplit_p,
-                                              nullptr, part);
+                                              nullptr, part, kwait);
 }
 
 // The same with the wrench-estimate warp: four 128-thread blocks per SM (the

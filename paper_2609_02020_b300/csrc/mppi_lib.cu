@@ -425,10 +425,31 @@ cudaError_t prepare_rollout(mppi_s* h) {
   return cudaSuccess;
 }
 
+// Launch configuration of a programmatic dependent launch on the handle's
+// stream: the grid may start while the previous kernel still runs and waits
+// (griddepcontrol.wait) before it reads what that kernel writes.
+struct PdlLaunch {
+  cudaLaunchAttribute at[1];
+  cudaLaunchConfig_t lc;
+  PdlLaunch(dim3 grid, dim3 block, size_t smem, cudaStream_t st) : at{}, lc{} {
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+  }
+};
+
 // part non-null (with noise): every rollout block also leaves its Eq. 4
-// partials there for merge_kernel
+// partials there for merge_kernel.  kwait >= 0: a proposal kernel that
+// installs a second proposal with k_split = kwait immediately precedes on
+// the stream; the plain warp-specialised kernel then overlaps it (blocks
+// below kwait do not wait for it), the other kernels wait for it as usual.
 cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float* S, float* noise,
-                           float* part = nullptr) {
+                           float* part = nullptr, int kwait = -1) {
   if (!noise) part = nullptr;
   const int grid = (h->P.K + ROLLOUT_BLOCK - 1) / ROLLOUT_BLOCK;
   if (h->feat == FEAT_COLL && h->variant == 3) {
@@ -467,6 +488,23 @@ cudaError_t launch_rollout(mppi_s* h, const float* in, const float* plan, float*
   if (h->variant == 3) {
     const int wgrid = (h->P.K + WS_B - 1) / WS_B;
     const size_t smem = ws_smem_bytes();
+    if (kwait >= 0) {
+      PdlLaunch L(dim3(wgrid), dim3(WS_THREADS), smem, h->stream);
+      const unsigned long long* iter = h->d_iter;
+      const float* prop = h->d_prop;
+      const int* ctl = h->d_ctl;
+      float* pt = noise ? part : nullptr;
+      if (h->P.K <= WS_SMALL_K_MAX)
+        return noise ? cudaLaunchKernelEx(&L.lc, rollout_kernel_ws_small<true>, h->P, in, iter,
+                                          plan, S, noise, prop, ctl, pt, kwait)
+                     : cudaLaunchKernelEx(&L.lc, rollout_kernel_ws_small<false>, h->P, in, iter,
+                                          plan, S, noise, prop, ctl, pt, kwait);
+      const ObsK* no_obs = nullptr;
+      return noise ? cudaLaunchKernelEx(&L.lc, rollout_kernel_ws<true, false>, h->P, in, iter,
+                                        plan, S, noise, prop, ctl, no_obs, pt, kwait)
+                   : cudaLaunchKernelEx(&L.lc, rollout_kernel_ws<false, false>, h->P, in, iter,
+                                        plan, S, noise, prop, ctl, no_obs, pt, kwait);
+    }
     if (h->P.K <= WS_SMALL_K_MAX) {
       if (noise)
         rollout_kernel_ws_small<true><<<wgrid, WS_THREADS, smem, h->stream>>>(
@@ -550,9 +588,9 @@ cudaError_t launch_merge(mppi_s* h, const float* plan, float* ustar, float* plan
 // set for this update (k_split := K)
 cudaError_t enqueue_update(mppi_s* h, int cur, const float* in = nullptr, float* tau_dst = nullptr,
                            float* plan_dst = nullptr, float* out = nullptr,
-                           const unsigned* seq_in = nullptr) {
+                           const unsigned* seq_in = nullptr, int kwait = -1) {
   cudaError_t e = launch_rollout(h, in ? in : h->d_in, h->d_plan[cur], h->d_S, h->d_noise,
-                                 h->d_part);
+                                 h->d_part, kwait);
   if (e != cudaSuccess) return e;
   return launch_merge(h, h->d_plan[cur], h->d_ustar, h->d_plan[cur ^ 1], out ? out : h->d_out,
                       h->d_iter, tau_dst, plan_dst, seq_in);
@@ -917,6 +955,21 @@ int mppi_step_device(mppi_t h, const float* d_in, float* d_tau0, float* d_plan) 
   // straight into the caller's buffers: two kernels and one 4-byte copy
   const int cur = h->cur;
   CUDA_TRY(h, enqueue_update(h, cur, d_in, d_tau0, d_plan));
+  h->cur = cur ^ 1;
+  h->out_on_host = false;
+  return MPPI_OK;
+}
+
+// mppi_step_device queued directly behind a proposal kernel that installs
+// a second proposal with k_split = n_plain (the learned proposal's fused
+// call): the rollouts may overlap that kernel.
+int mppi_internal_step_after_proposal(mppi_t h, const float* d_in, float* d_tau0, float* d_plan,
+                                      int n_plain) {
+  if (!h) return fail(nullptr, MPPI_ERR_INVALID_ARG, "null handle");
+  if (!d_in) return fail(h, MPPI_ERR_INVALID_ARG, "null d_in");
+  if (n_plain < 0 || n_plain > h->P.K) return fail(h, MPPI_ERR_INVALID_ARG, "n_plain must be in 0..K");
+  const int cur = h->cur;
+  CUDA_TRY(h, enqueue_update(h, cur, d_in, d_tau0, d_plan, nullptr, nullptr, n_plain));
   h->cur = cur ^ 1;
   h->out_on_host = false;
   return MPPI_OK;

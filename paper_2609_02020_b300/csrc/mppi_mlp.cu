@@ -36,6 +36,8 @@ cudaStream_t mppi_internal_stream(mppi_t h);
 float* mppi_internal_prop(mppi_t h);
 int mppi_internal_K(mppi_t h);
 int* mppi_internal_ctl(mppi_t h);
+extern "C" int mppi_internal_step_after_proposal(mppi_t h, const float* d_in, float* d_tau0,
+                                                 float* d_plan, int n_plain);
 
 namespace {
 
@@ -256,6 +258,9 @@ propose_kernel(const ProposeArgs a) {
   __shared__ float act[2][MAXW];
   __shared__ __align__(8) uint64_t bar[2];  // one per activation buffer
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // an update queued behind this kernel as its programmatic dependent may
+  // start now: its blocks that need the proposal wait for this grid
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   uint32_t rank;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
   // every weight fragment of this lane, all layers, before any arithmetic
@@ -539,6 +544,8 @@ int check_err(mppi_mlp_s* m) {
   return MPPI_OK;
 }
 
+int enqueue_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain);
+
 }  // namespace
 
 extern "C" {
@@ -784,6 +791,23 @@ int mppi_mlp_train_step(mppi_mlp_t m, const float* d_x, const float* d_y, int n,
 }
 
 int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain) {
+  return enqueue_propose(m, h, d_in, n_plain);
+}
+
+int mppi_mlp_propose_step_device(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain,
+                                 float* d_tau0, float* d_plan) {
+  int rc = enqueue_propose(m, h, d_in, n_plain);
+  if (rc != MPPI_OK) return rc;
+  rc = mppi_internal_step_after_proposal(h, d_in, d_tau0, d_plan, n_plain);
+  if (rc != MPPI_OK) mppi_set_thread_error(mppi_last_error(h));
+  return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+int enqueue_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain) {
   if (!m || !h || !d_in) return fail(MPPI_ERR_INVALID_ARG, "null argument");
   const int T = mppi_internal_T(h);
   if (n_plain < 0 || n_plain > mppi_internal_K(h)) return fail(MPPI_ERR_INVALID_ARG, "n_plain must be in 0..K");
@@ -821,4 +845,4 @@ int mppi_mlp_propose(mppi_mlp_t m, mppi_t h, const float* d_in, int n_plain) {
   return e == cudaSuccess ? MPPI_OK : fail(MPPI_ERR_CUDA, cudaGetErrorString(e));
 }
 
-}  // extern "C"
+}  // namespace

@@ -215,8 +215,7 @@ class LearnedMPPI:
         self.n_plain = int(round(K * plain_frac))
 
     def step_device(self, d_in, d_tau):
-        self.net.propose(self.ctl, d_in, self.n_plain)
-        self.ctl.step_device(d_in, d_tau, None)
+        self.net.propose_step_device(self.ctl, d_in, self.n_plain, d_tau)
 
     def reset(self, plan0):
         self.ctl.set_plan(plan0)

@@ -150,6 +150,7 @@ EXPORTS = [
     "mppi_mlp_set_params", "mppi_mlp_set_normalization", "mppi_mlp_fit_normalization",
     "mppi_mlp_forward",
     "mppi_mlp_loss_grad", "mppi_mlp_train_step", "mppi_mlp_propose", "mppi_mlp_check_wait",
+    "mppi_mlp_propose_step_device",
 ]
 
 _lib = None
@@ -239,6 +240,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "mppi_mlp_loss_grad": ([H, vp, vp, C.c_int, fp, fp], C.c_int),
         "mppi_mlp_train_step": ([H, vp, vp, C.c_int, C.c_float, fp], C.c_int),
         "mppi_mlp_propose": ([H, H, vp, C.c_int], C.c_int),
+        "mppi_mlp_propose_step_device": ([H, H, vp, C.c_int, vp, vp], C.c_int),
         "mppi_mlp_check_wait": ([H, C.c_longlong], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -838,6 +840,13 @@ class MLP:
         """Install the network's plan as ctl's second proposal for its next
         update, keeping n_plain samples around ctl's warm start."""
         self._check(self.lib.mppi_mlp_propose(self.h, ctl.h, _dptr(d_in), int(n_plain)))
+
+    def propose_step_device(self, ctl: "MPPI", d_in, n_plain: int = 0, d_tau0=None, d_plan=None):
+        """propose(ctl, d_in, n_plain) and ctl.step_device(d_in, d_tau0, d_plan)
+        in one call, the update's plain blocks overlapping the proposal
+        (queued; see MPPI.sync())."""
+        self._check(self.lib.mppi_mlp_propose_step_device(self.h, ctl.h, _dptr(d_in), int(n_plain),
+                                                          _dptr(d_tau0), _dptr(d_plan)))
 
     def check_wait(self, cycles: int) -> int:
         """Status of one bounded device wait that nothing completes

@@ -133,6 +133,67 @@ def test_propose_installs_the_network_plan_as_second_proposal():
         assert np.allclose(a, b, rtol=1e-4, atol=1e-4)
 
 
+@pytest.mark.parametrize("variant", [0, 2])
+@pytest.mark.parametrize("K,n_plain", [(512, 200), (2048, 0), (2048, 1000), (2048, 2048),
+                                       (16384, 8192), (16384, 5001)])
+def test_fused_propose_step_matches_the_two_calls(K, n_plain, variant):
+    """propose_step_device gives, bit for bit, the updates of propose followed
+    by step_device: tau0, the shifted plan, u* and the costs over three
+    warm-started updates.  Variant 0 is the warp-specialised kernel (the
+    small-K and the default instantiation), whose plain blocks overlap the
+    proposal; the rolled kernel (variant 2) waits for it as usual."""
+    import torch
+    arm = synth.arm(0)
+    T = 18
+    m = net(seed=5)
+    g = np.random.default_rng(K + n_plain)
+    plan0 = g.normal(0, 3, (T, 7)).astype(np.float32)
+    states = [synth.state(1100 + i, arm) for i in range(3)]
+    goal = synth.goal(1100, arm)
+    res = []
+    for fused in (False, True):
+        ctl = mppi.MPPI(arm, synth.cost_contact(), dt=0.01, T=T, K=K, lam=1.0, sigma=2.0,
+                        seed=3, variant=variant)
+        assert variant == 2 or ctl.variant() == 3
+        ctl.set_plan(plan0)
+        out = []
+        for q, qd in states:
+            d_in = torch.tensor(mppi.pack_inputs(q, qd, goal), device="cuda")
+            d_tau = torch.zeros(7, device="cuda")
+            if fused:
+                m.propose_step_device(ctl, d_in, n_plain, d_tau)
+            else:
+                m.propose(ctl, d_in, n_plain)
+                ctl.step_device(d_in, d_tau)
+            assert ctl.sync() == mppi.OK
+            out.append((d_tau.cpu().numpy(), ctl.get_plan(), ctl.updated_plan(), ctl.costs()))
+        res.append(out)
+        ctl.close()
+    for a_step, b_step in zip(*res):
+        for a, b in zip(a_step, b_step):
+            assert np.array_equal(a, b)
+
+
+def test_fused_propose_step_rejects_bad_arguments():
+    import torch
+    arm = synth.arm(0)
+    m = net()
+    ctl = mppi.MPPI(arm, synth.cost_free_space(), dt=0.01, T=18, K=256, lam=1.0, sigma=2.0, seed=1)
+    try:
+        d_in = torch.zeros(25, device="cuda")
+        for bad in (-1, 257):
+            with pytest.raises(mppi.MPPIError) as e:
+                m.propose_step_device(ctl, d_in, bad)
+            assert e.value.code == mppi.ERR_INVALID_ARG
+        with pytest.raises(mppi.MPPIError) as e:
+            m.propose_step_device(ctl, None, 0)
+        assert e.value.code == mppi.ERR_INVALID_ARG
+        assert ctl.get_iter() == 0  # nothing was queued
+    finally:
+        ctl.close()
+        m.close()
+
+
 def test_bounded_wait_reports_timeout():
     # one mbarrier wait that nothing completes, given up after about 1 ms of
     # SM clock through the GEMMs' wait helper and error flag: the status is
