@@ -64,17 +64,17 @@ FLOP_PER_ROLLOUT_STEP = {"contact": 4311.0}
 FLOP_EXECUTED_PER_ROLLOUT_STEP = {("contact", "rollout_kernel_ws"): 4970.2,
                                   ("force_estimate", "rollout_kernel_ws_fest"): 6159.1,
                                   ("force_estimate", "rollout_kernel_rolled"): 6167.6,
-                                  ("collision", "rollout_kernel_ws"): 6527.2}
+                                  ("collision", "rollout_kernel_ws"): 6500.2}
 # DRAM read + write bytes of one rollout launch at K=16384, T=18 per (cost,
 # kernel) (ncu dram__bytes_{read,write}.sum, mean of two launches).  The
 # 8.3 MB of stored noise stays in L2 and is not written back inside the
 # launch.
 # Only kernels captured since their last change are listed; the others
 # report null.
-ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel_ws"): 64640,
-                                    ("force_estimate", "rollout_kernel_ws_fest"): 73728,
+ROLLOUT_TRAFFIC_BYTES_PER_LAUNCH = {("contact", "rollout_kernel_ws"): 65024,
+                                    ("force_estimate", "rollout_kernel_ws_fest"): 72832,
                                     ("force_estimate", "rollout_kernel_rolled"): 67840,
-                                    ("collision", "rollout_kernel_ws"): 127616}
+                                    ("collision", "rollout_kernel_ws"): 131072}
 COSTS = ("contact", "force_estimate", "collision")
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
