@@ -115,6 +115,9 @@ def parse():
     ap.add_argument("--on-policy-pairs", type=int, default=100_000,
                     help="learned mode: pairs per on-policy round")
     ap.add_argument("--episodes", type=int, default=12, help="learned mode: eval episodes")
+    ap.add_argument("--plain-fracs", default="0.5",
+                    help="learned mode: comma-separated shares of the samples kept around the "
+                         "plain warm start, one set of learned rows each")
     ap.add_argument("--rates", default="2000,5000,10000,20000,100000",
                     help="serve mode: arrival rates [updates/s]")
     ap.add_argument("--seconds", type=float, default=2.0, help="serve mode: seconds per rate")
@@ -784,14 +787,15 @@ def run_learned(args, rank, world):
     for name, K, mk in (
             [("plain", K, lambda K: learned.PlainMPPI(prob, K, seed=5, stream=s))
              for K in (16384, 512, 2048, 4096, args.label_k)] +
-            [("learned", K, lambda K: learned.LearnedMPPI(prob, net, K, seed=5, stream=s,
-                                                           plain_frac=0.5))
-             for K in (512, 2048, 4096)]):
+            [("learned", K, lambda K, f=float(f): learned.LearnedMPPI(prob, net, K, seed=5,
+                                                                      stream=s, plain_frac=f))
+             for f in args.plain_fracs.split(",") for K in (512, 2048, 4096)]):
         c = mk(K)
         r = learned.evaluate(prob, c, episodes=args.episodes, steps=1000, seed=1, stream=s)
+        frac = c.n_plain / K if name == "learned" else 1.0
         c.close()
         r.pop("tracking_cost_per_episode")
-        rows.append({"controller": name, "K": K, **r})
+        rows.append({"controller": name, "K": K, "plain_frac": frac, **r})
     if rank == 0:
         print(json.dumps({
             "mode": "learned",
