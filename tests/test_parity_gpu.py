@@ -129,24 +129,24 @@ def test_contact_plan_matches_oracle(seed, variant):
 
 
 # Recorded miss of the 1e-5 N m plan bar.  At these weights S_k is 300-1000
-# lambda (free space, SURVEY c22 weights) or 1e3-1e5 lambda (contact), and the
+# lambda (free space, the heavy parity weights) or 1e3-1e5 lambda (contact), and the
 # weights of Eq. 4a are spread over a few samples (n_eff of 1.5-7).  A cost
 # error dS moves u* by about sigma dS / lambda through the weights, and FP32
 # cannot make dS smaller than one ulp of S_k (6e-8 S_k, 2e-5 to 6e-5 lambda
 # here) even with exact arithmetic; the measured cost errors are 1e-7 to 8e-6
 # relative, well inside the 1e-4 cost bar.  Measured max |du*| (N m):
-# c22 weights, seeds 0-5: 5e-7 to 5.6e-5; contact seed 4 (n_eff 1.5, the two
+# heavy weights, seeds 0-5: 5e-7 to 5.6e-5; contact seed 4 (n_eff 1.5, the two
 # best samples 1.4 lambda apart): 2.7e-3; contact at K = 4,194,304, T = 2
 # (n_eff 1.009, S_min 2169 lambda): 1.5e-4.  The bounds below guard those sizes.
-HEAVY_MISS_BOUND = {"c22": 1e-4, "contact": 5e-3}
+HEAVY_MISS_BOUND = {"heavy": 1e-4, "contact": 5e-3}
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3])
-@pytest.mark.parametrize("case", ["c22-0", "c22-1", "c22-2", "c22-3", "c22-4", "c22-5",
+@pytest.mark.parametrize("case", ["heavy-0", "heavy-1", "heavy-2", "heavy-3", "heavy-4", "heavy-5",
                                   "contact-4"])
 def test_plan_recorded_miss_at_heavy_weights(case, variant):
     kind, seed = case.split("-")
-    c = (make_case(int(seed), cost=parity_cost(1.0)) if kind == "c22"
+    c = (make_case(int(seed), cost=parity_cost(1.0)) if kind == "heavy"
          else make_case(int(seed), contact=True))
     g, o = run_pair(c, variant=variant)
     assert_costs(g["S"], o["S"])
@@ -771,7 +771,7 @@ def test_per_joint_sigma_with_a_zero(variant):
 
 
 # Recorded miss of the 1e-4 cost bar for the bare rigid-body model (armature
-# a = 0 of Eq. 8, no joint damping).  Without the armature of reading r1 the
+# a = 0 of Eq. 8, no joint damping).  Without the workloads' rotor armature the
 # seeded arm's mass matrix has condition numbers of 900-3900 at the start
 # states (24-55 with a = 0.1), and an FP32 LDL^T solve then loses about
 # cond(M) u (u = 6e-8) of relative accuracy in qdd at every step.  Measured
@@ -824,7 +824,7 @@ def test_general_geometry_matches_oracle(seed, variant):
         assert_plan(g, o)
     else:
         assert np.argmin(g["S"]) == np.argmin(o["S"])
-        assert max(plan_errors(g, o)) <= HEAVY_MISS_BOUND["c22"]
+        assert max(plan_errors(g, o)) <= HEAVY_MISS_BOUND["heavy"]
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3])

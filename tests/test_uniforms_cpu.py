@@ -1,4 +1,4 @@
-"""The FP32 form of the noise's uniforms (reading c20), restated on the CPU
+"""The FP32 form of the noise's uniforms (Box-Muller inputs in (0, 1)), restated on the CPU
 with IEEE single-precision numpy arithmetic (round to nearest even, as the
 kernels' explicitly rounded intrinsics).
 
