@@ -174,6 +174,37 @@ def test_fused_propose_step_matches_the_two_calls(K, n_plain, variant):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("cost", ["force_estimate", "collision"])
+def test_fused_propose_step_with_the_optional_costs(cost):
+    """With the wrench-estimate or collision cost the warp-specialised rollout
+    waits for the proposal kernel as usual; the one call still gives the two
+    calls' update bit for bit."""
+    import torch
+    arm = synth.arm(1)
+    T, K, n_plain = 18, 2048, 1000
+    c = (synth.cost_force_estimate() if cost == "force_estimate" else
+         synth.cost_collision(obstacles=[[0.3, 0.0, 0.5, 0.3, 0.15, 0.55, 0.05],
+                                         [0.0, 0.35, 0.4, 0.1, 0.35, 0.4, 0.04]]))
+    m = net(seed=6)
+    q, qd = synth.state(1200, arm)
+    d_in = torch.tensor(mppi.pack_inputs(q, qd, synth.goal(1200, arm)), device="cuda")
+    res = []
+    for fused in (False, True):
+        ctl = mppi.MPPI(arm, c, dt=0.01, T=T, K=K, lam=1.0, sigma=2.0, seed=2)
+        assert ctl.variant() == 3
+        d_tau = torch.zeros(7, device="cuda")
+        if fused:
+            m.propose_step_device(ctl, d_in, n_plain, d_tau)
+        else:
+            m.propose(ctl, d_in, n_plain)
+            ctl.step_device(d_in, d_tau)
+        assert ctl.sync() == mppi.OK
+        res.append((d_tau.cpu().numpy(), ctl.get_plan(), ctl.costs()))
+        ctl.close()
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+
+
 def test_fused_propose_step_rejects_bad_arguments():
     import torch
     arm = synth.arm(0)
