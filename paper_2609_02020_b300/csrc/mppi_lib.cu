@@ -37,7 +37,8 @@ using namespace mppi_dev;
 // rollout_kernel_ws_small.  Rollout at T = 18 on B300 (us), the default
 // instantiation against the small one: K = 512-2048: 62.5-64.0 against
 // 60.2-61.5; 4096: 64.5 against 62.6; 8192: 68.2 against 67.5; 12288: 84.4
-// for both; 16384: 86.6 against 87.7.
+// for both; 16384: 86.6 against 87.7 (on another box both within 1 % at
+// every K).
 #define WS_SMALL_K_MAX 8192
 #endif
 
