@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--K", type=int, default=K_DEFAULT)
     ap.add_argument("--T", type=int, default=T_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="update mode: skip the learned-proposal latency sub-object")
     ap.add_argument("--no-serve", action="store_true",
                     help="update mode: leave out the compact serving measurement")
     ap.add_argument("--budget-s", type=float, default=120.0,
@@ -480,12 +482,61 @@ def run_ours(args, rank, world):
     ctl.close()
     if not args.no_serve:
         line["serve"] = serve_summary(rank)
+    if not args.no_learned:
+        line["learned_latency"] = learned_latency_summary()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(K, T, cost_name=args.cost)
     print(json.dumps(line), flush=True)
 
 
 LAT_UPDATES, LAT_WARMUP, LAT_SECONDS = 1000, 50, 1.2
+
+
+def learned_latency_summary(K_learned=2048, K_plain=16384):
+    """Update latency of the learned-proposal form beside plain MPPI, for the
+    update line: device time per update (CUDA events on the controller's
+    stream, LAT_UPDATES after LAT_WARMUP, L2 not flushed), on the closed-loop
+    study's task and network shape.  The network is untrained here: its
+    weights do not change the time; the tracking comparison, which needs the
+    trained network, is `--mode learned`."""
+    import torch
+    from paper_2609_02020_b300 import learned, mppi
+    prob = learned.tracking_problem(0)
+    s = torch.cuda.Stream()
+    net = mppi.MLP(21 + 7 * prob.T, 256, 3, 7 * prob.T, max_batch=256, seed=0, stream=s)
+    out = {"task": "the closed-loop study's (learned.tracking_problem), untrained network "
+                   "147-3x256-126, half of the learned form's samples around the plain warm start",
+           "updates": LAT_UPDATES}
+    forms = (("plain", K_plain, None), ("learned_one_call", K_learned, True),
+             ("learned_two_calls", K_learned, False))
+    for name, K, one_call in forms:
+        ctl = prob.controller(K, seed=5, stream=s)
+        q, qd, goal = prob.episode_start(123, ctl)
+        ctl.set_plan(prob.hold_plan(ctl, q))
+        d_in = torch.tensor(mppi.pack_inputs(q, qd, goal, prob.plane), device="cuda")
+        d_tau = torch.zeros(7, device="cuda")
+        n_plain = K // 2
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(LAT_UPDATES)]
+        for i in range(LAT_WARMUP + LAT_UPDATES):
+            if i >= LAT_WARMUP:
+                ev[i - LAT_WARMUP][0].record(s)
+            if one_call is None:
+                ctl.step_device(d_in, d_tau)
+            elif one_call:
+                net.propose_step_device(ctl, d_in, n_plain, d_tau)
+            else:
+                net.propose(ctl, d_in, n_plain)
+                ctl.step_device(d_in, d_tau)
+            if i >= LAT_WARMUP:
+                ev[i - LAT_WARMUP][1].record(s)
+        s.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        out[name] = {"K": K, "p50_ms": float(np.percentile(ms, 50)),
+                     "p99_ms": float(np.percentile(ms, 99)), "status": ctl.sync()}
+        ctl.close()
+    net.close()
+    return out
 
 
 def latency_loop(ctl, d_in, d_tau, d_plan, flush, stream, barrier, clk, spans):
